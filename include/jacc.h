@@ -1,0 +1,225 @@
+/*
+ * jacc.h - C ABI of the GB300 runtime-specialised affine stencil library
+ * (libjacc.so).
+ *
+ * The library covers the data-parallel hot path that the JACC OpenACC runtime
+ * (Matsumura, Garcia De Gonzalo, Pena, HiPC 2021, arXiv 2110.14340) speeds up:
+ * runtime analysis of the array regions an affine loop nest touches, kernels
+ * specialised with runtime values and cached, and iterative stencil sweeps
+ * with a fused convergence reduction, run as CUDA-graph-captured loops.  Two
+ * additions have no counterpart in the paper: batched persistent launches over
+ * many uneven grids, and an autotuner plus a small learned cost model that
+ * picks tile configurations.
+ *
+ * Conventions for every entry point:
+ *  - Returns a jacc_status; JACC_OK is 0 and every error is negative.  The
+ *    library never aborts or exits.  jacc_last_error() gives a message for the
+ *    last failing call on the calling thread.
+ *  - Device pointers are caller-owned CUDA device memory (for instance torch
+ *    tensors); the library never frees them.  Host pointers are read during
+ *    the call only, unless stated.
+ *  - `stream` is a cudaStream_t passed as uintptr_t (0 = legacy default stream).
+ *    Device work is enqueued asynchronously on it unless stated.
+ *  - Arrays are row-major with x the fastest axis: a 2D grid is [ny][nx], a 3D
+ *    grid [nz][ny][nx].
+ */
+#ifndef JACC_H
+#define JACC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+typedef int32_t jacc_status;
+#define JACC_OK 0
+#define JACC_ERR_INVALID_ARG (-1)   /* bad pointer, size, enum, aliasing */
+#define JACC_ERR_OUT_OF_BOUNDS (-2) /* a touched region leaves the array  */
+#define JACC_ERR_OVERFLOW (-3)      /* int64 overflow in index arithmetic */
+#define JACC_ERR_CUDA (-4)          /* a CUDA runtime call failed         */
+#define JACC_ERR_COMPILE (-5)       /* NVRTC or module load failed        */
+#define JACC_ERR_TIMEOUT (-6)       /* a bounded device wait gave up      */
+#define JACC_ERR_UNSUPPORTED (-7)   /* valid request the library lacks    */
+#define JACC_ERR_NOMEM (-8)         /* host or device allocation failed   */
+
+/* Message for the last non-OK status returned on this thread ("" if none).
+ * The pointer stays valid until the next jacc call on the same thread. */
+const char* jacc_last_error(void);
+/* Library version string, e.g. "jacc-gb300 1.0 (sm_103a)". */
+const char* jacc_version(void);
+
+/* ---------------------------------------------------------- region analysis
+ * The runtime tracks which index ranges of each array a kernel reads and
+ * writes (data ranges linked to pointers, paper §3.2.1; per-array lower/upper
+ * write bounds, §4.1).  References to one array are merged to the widest range
+ * (§4.1); reads and writes are kept separate (§4.1, aliasing rule).
+ *
+ * A nest is rectangular: loop k runs i_k = lo, lo+step, ... while i_k <= hi
+ * (step > 0) or while i_k >= hi (step < 0); step == 0 is JACC_ERR_INVALID_ARG.
+ * nloops == 0 means a single iteration.  A reference's subscript d is the
+ * affine form off[d] + sum_k coef[d][k] * i_k.  For every array the result
+ * holds the per-dimension index hulls [lo, hi] of the reads and of the writes
+ * and the exact min/max of the flattened row-major element offset
+ * (stride[ndim-1] = 1, stride[d] = stride[d+1] * extent[d+1]).  Hulls are
+ * exact: each bound is attained by some iteration.  An empty nest (some loop
+ * with no iteration) touches nothing (has_read = has_write = 0).
+ *
+ * Errors: JACC_ERR_INVALID_ARG for NULL arrays with a non-zero count, a count
+ * outside [0, JACC_MAX_*], ndim outside [1, JACC_MAX_DIMS], a negative extent,
+ * an array_id out of range or a reference whose ndim differs from its
+ * array's; JACC_ERR_OVERFLOW when a coefficient times a loop endpoint, a
+ * stride, a flattened coefficient or offset, or a final bound leaves int64
+ * (`out` is then unspecified); JACC_ERR_OUT_OF_BOUNDS when some hull leaves
+ * [0, extent-1] (`out` is still fully written).  Pure host code, reentrant,
+ * no CUDA call. */
+#define JACC_MAX_DIMS 8
+#define JACC_MAX_LOOPS 8
+
+typedef struct { int64_t lo, hi, step; } jacc_loop;
+
+typedef struct {
+  int32_t array_id;                          /* index into the arrays[] argument */
+  int32_t ndim;                              /* must equal arrays[array_id].ndim */
+  int32_t is_write;                          /* 0 = read, non-zero = write       */
+  int32_t reserved;                          /* set to 0                         */
+  int64_t coef[JACC_MAX_DIMS][JACC_MAX_LOOPS]; /* coef[d][k]                     */
+  int64_t off[JACC_MAX_DIMS];
+} jacc_ref;
+
+typedef struct {
+  int32_t ndim;
+  int32_t reserved;
+  int64_t extent[JACC_MAX_DIMS];
+} jacc_array;
+
+typedef struct {
+  int32_t has_read, has_write;
+  int64_t rlo[JACC_MAX_DIMS], rhi[JACC_MAX_DIMS]; /* read hull per dimension  */
+  int64_t wlo[JACC_MAX_DIMS], whi[JACC_MAX_DIMS]; /* write hull per dimension */
+  int64_t rlin_lo, rlin_hi, wlin_lo, wlin_hi;     /* flattened offset extremes */
+} jacc_region;
+
+jacc_status jacc_region_analyze(int32_t nloops, const jacc_loop* loops, int32_t nrefs, const jacc_ref* refs,
+                                int32_t narrays, const jacc_array* arrays, jacc_region* out /* [narrays] */);
+
+/* ---------------------------------------------------------- specialisation
+ * A kernel descriptor names one stencil sweep.  jacc_specialize returns a
+ * handle to a compiled kernel plus its launch configuration, from a cache
+ * keyed on the full descriptor (paper §3.1: code compiled once is reused;
+ * §3.2.2: runtime-invariant parameters are substituted by constants and
+ * non-aliasing pointers are declared restrict).
+ *
+ * Stencils (interior points; Dirichlet boundary points are copied unchanged):
+ *   JACC_STENCIL_5PT  (2D): v = ((u[y-1][x] + u[y+1][x]) + (u[y][x-1] + u[y][x+1])) / 4
+ *   JACC_STENCIL_7PT  (3D): v = u + r * (sum of the 6 face neighbours - 6 u),  r = coeffs[0]
+ *   JACC_STENCIL_27PT (3D): v = w0*centre + wf*faces + we*edges + wc*corners,
+ *                           (w0, wf, we, wc) = coeffs[0..3]
+ * Fused reduction written per sweep into resid_dev[k] (FP64):
+ *   5PT and 7PT : max over interior points of |v - u| (the change made by
+ *                 the sweep);
+ *   27PT        : the sum of the output field (every materialised sweep).
+ *
+ * dtype JACC_F64 stores FP64.  Its arithmetic (arith):
+ *   JACC_ARITH_AUTO    exact 64-bit fixed-point integer arithmetic when the
+ *                      stencil is a convex combination (5PT always; 7PT with
+ *                      0 < r <= 1/6; 27PT with non-negative weights summing to
+ *                      at most 1 + 2^-20) and the input is finite; native
+ *                      FP64 otherwise.  Results are the exact stencil value
+ *                      rounded once to FP64.
+ *   JACC_ARITH_NATIVE  FP64 instructions throughout.
+ * dtype JACC_F32 stores and computes FP32 (arith is ignored).
+ *
+ * tile_id selects one of JACC_NUM_TILES tile configurations (see
+ * jacc_tile_info), or -1 to let the library choose (the autotuner's cached
+ * pick for this shape if one exists, else a default).
+ *
+ * flags: JACC_SPEC_JIT compiles a variant with the extents and coefficients
+ * folded in as constants (NVRTC, sm_103a; cached in memory and, if the
+ * environment variable JACC_CACHE_DIR names a directory, on disk).  Without
+ * it the handle uses a precompiled kernel that takes them as arguments.
+ *
+ * tblock (27PT only): temporal-blocking depth T >= 1.  Each launch then
+ * performs T sweeps; jacc_sweep accounts for this.
+ *
+ * The handle is owned by the library and stays valid until jacc_release or
+ * jacc_shutdown.  Identical descriptors share one compiled kernel. */
+#define JACC_STENCIL_5PT 5
+#define JACC_STENCIL_7PT 7
+#define JACC_STENCIL_27PT 27
+#define JACC_F32 32
+#define JACC_F64 64
+#define JACC_DIRICHLET 0
+#define JACC_PERIODIC 1
+#define JACC_ARITH_AUTO 0
+#define JACC_ARITH_NATIVE 1
+#define JACC_SPEC_JIT 1u
+#define JACC_NUM_TILES 24
+
+typedef struct {
+  int32_t stencil;   /* JACC_STENCIL_*                                 */
+  int32_t dtype;     /* JACC_F32 or JACC_F64                           */
+  int32_t boundary;  /* JACC_DIRICHLET (5PT, 7PT) or JACC_PERIODIC (27PT) */
+  int32_t tile_id;   /* 0..JACC_NUM_TILES-1, or -1                     */
+  int64_t nx, ny, nz;/* extents; nz = 1 for 5PT; each >= 3             */
+  double coeffs[4];  /* see above                                      */
+  int32_t arith;     /* JACC_ARITH_*                                   */
+  uint32_t flags;    /* JACC_SPEC_*                                    */
+  int32_t tblock;    /* 27PT temporal-blocking depth (0 or 1 = none)   */
+  int32_t reserved;  /* set to 0                                       */
+} jacc_kernel_desc;
+
+typedef struct jacc_kernel_s* jacc_kernel;
+
+typedef struct {
+  int32_t tile_id;
+  int32_t jit;          /* 1 if constants are folded (NVRTC variant)     */
+  int32_t fixed_point;  /* 1 if FP64 arithmetic runs in 64-bit fixed point */
+  int32_t tblock;
+  int32_t block[3];     /* CUDA block shape                               */
+  int32_t grid[3];      /* CUDA grid shape                                */
+  double compile_ms;    /* NVRTC + load time of this variant (0 if cached) */
+} jacc_kernel_info_t;
+
+jacc_status jacc_specialize(const jacc_kernel_desc* desc, jacc_kernel* out);
+jacc_status jacc_kernel_info(jacc_kernel k, jacc_kernel_info_t* out);
+jacc_status jacc_release(jacc_kernel k);
+
+/* Tile configuration `tile_id`: threads (bx, by) per CTA, elements per thread
+ * in x (vec: 1 or a 16-byte vector), and the march length zc (planes per CTA
+ * in 3D, rows per thread in 2D).  Host only. */
+typedef struct { int32_t bx, by, vec16, zc; } jacc_tile;
+jacc_status jacc_tile_info(int32_t tile_id, jacc_tile* out);
+
+/* ------------------------------------------------------------------ launch
+ * jacc_launch: one sweep from u_in to u_out (each nx*ny*nz elements of the
+ * descriptor's dtype, 16-byte aligned).  u_in and u_out must not overlap
+ * (they are restrict in the kernel): overlap is JACC_ERR_INVALID_ARG.
+ * resid_dev (nullable) receives the sweep's reduction (one double, device
+ * memory).  For 27PT with tblock T > 1 one launch performs T sweeps.
+ * Asynchronous on `stream`. */
+jacc_status jacc_launch(jacc_kernel k, const void* u_in, void* u_out, double* resid_dev, uintptr_t stream);
+
+/* jacc_sweep: nsweeps ping-pong sweeps u0 -> u1 -> u0 ... (nsweeps >= 1; for
+ * 27PT a multiple of tblock).  resid_dev (nullable, device, nsweeps doubles)
+ * receives resid_dev[k] for sweep k; for 27PT with temporal blocking only
+ * sweeps that end a block are materialised and the others get NaN.
+ * flags: JACC_SWEEP_GRAPH captures the whole loop as one CUDA graph, cached
+ * by (kernel, u0, u1, nsweeps, resid_dev) and replayed on later calls; the
+ * graph is dropped by jacc_release.  Without it the launches are issued one
+ * by one.  *final_buf (host) is set to 0 if the last sweep wrote u0, 1 if u1.
+ * Asynchronous on `stream`. */
+#define JACC_SWEEP_GRAPH 1u
+jacc_status jacc_sweep(jacc_kernel k, void* u0, void* u1, int32_t nsweeps, double* resid_dev, uint32_t flags,
+                       uintptr_t stream, int32_t* final_buf);
+
+/* Release every cached kernel, graph and library allocation.  Handles become
+ * invalid.  Safe to call more than once. */
+jacc_status jacc_shutdown(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* JACC_H */

@@ -294,6 +294,43 @@ int orc_box27_run(int64_t nx, int64_t ny, int64_t nz, const float w[4], float* u
   return (nsweeps % 2 == 0) ? 0 : 1;
 }
 
+/* The same definition with FP64 storage and arithmetic. */
+void orc_box27_sweep_f64(int64_t nx, int64_t ny, int64_t nz, const double w[4], const double* u, double* v) {
+  for (int64_t z = 0; z < nz; ++z)
+    for (int64_t y = 0; y < ny; ++y)
+      for (int64_t x = 0; x < nx; ++x) {
+        double cls[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int dz = -1; dz <= 1; ++dz)
+          for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+              int64_t zz = (z + dz + nz) % nz;
+              int64_t yy = (y + dy + ny) % ny;
+              int64_t xx = (x + dx + nx) % nx;
+              int k = (dz != 0) + (dy != 0) + (dx != 0);
+              cls[k] = cls[k] + u[(zz * ny + yy) * nx + xx];
+            }
+        double acc = w[0] * cls[0];
+        acc = acc + w[1] * cls[1];
+        acc = acc + w[2] * cls[2];
+        acc = acc + w[3] * cls[3];
+        v[(z * ny + y) * nx + x] = acc;
+      }
+}
+
+int orc_box27_run_f64(int64_t nx, int64_t ny, int64_t nz, const double w[4], double* u0, double* u1, int32_t nsweeps,
+                      double* sums) {
+  double* a = u0;
+  double* b = u1;
+  for (int32_t k = 0; k < nsweeps; ++k) {
+    orc_box27_sweep_f64(nx, ny, nz, w, a, b);
+    if (sums) sums[k] = orc_sum_f64(b, nx * ny * nz);
+    double* t = a;
+    a = b;
+    b = t;
+  }
+  return (nsweeps % 2 == 0) ? 0 : 1;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Reductions (FP64 accumulation).  The runtime must synchronise after a      */
 /* reduction (§3.2.1); the reduction itself is the plain definition.          */

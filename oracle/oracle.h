@@ -73,6 +73,10 @@ int orc_heat3d_run(int64_t nx, int64_t ny, int64_t nz, double r, double* u0, dou
 /* 3D 27-point periodic stencil, FP32 storage and arithmetic; weights by class
  * (centre, face, edge, corner).  One sweep over every point. */
 void orc_box27_sweep(int64_t nx, int64_t ny, int64_t nz, const float w[4], const float* u, float* v);
+/* The same 27-point stencil in FP64 storage and arithmetic. */
+void orc_box27_sweep_f64(int64_t nx, int64_t ny, int64_t nz, const double w[4], const double* u, double* v);
+int orc_box27_run_f64(int64_t nx, int64_t ny, int64_t nz, const double w[4], double* u0, double* u1, int32_t nsweeps,
+                      double* sums);
 /* nsweeps ping-pong sweeps; if sums != NULL, sums[k] = FP64 sum of the field
  * after sweep k (k = 0..nsweeps-1).  Returns the parity of the final buffer. */
 int orc_box27_run(int64_t nx, int64_t ny, int64_t nz, const float w[4], float* u0, float* u1, int32_t nsweeps,

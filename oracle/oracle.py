@@ -60,6 +60,10 @@ def lib():
         L.orc_box27_sweep.argtypes = [C.c_int64, C.c_int64, C.c_int64, P, P, P]
         L.orc_box27_run.restype = C.c_int
         L.orc_box27_run.argtypes = [C.c_int64, C.c_int64, C.c_int64, P, P, P, C.c_int32, P]
+        L.orc_box27_sweep_f64.restype = None
+        L.orc_box27_sweep_f64.argtypes = [C.c_int64, C.c_int64, C.c_int64, P, P, P]
+        L.orc_box27_run_f64.restype = C.c_int
+        L.orc_box27_run_f64.argtypes = [C.c_int64, C.c_int64, C.c_int64, P, P, P, C.c_int32, P]
         L.orc_maxabs_diff.restype = C.c_double
         L.orc_maxabs_diff.argtypes = [P, P, C.c_int64]
         L.orc_sum_f64.restype = C.c_double
@@ -188,6 +192,16 @@ def box27_run(u, w, nsweeps, with_sums=True):
     sums = np.zeros(max(1, nsweeps), dtype=np.float64)
     par = lib().orc_box27_run(nx, ny, nz, _ptr(w), _ptr(a), _ptr(b), nsweeps,
                               _ptr(sums) if with_sums else None)
+    return (a if par == 0 else b), sums[:nsweeps]
+
+
+def box27_run_f64(u, w, nsweeps):
+    a = _c(u, np.float64).copy()
+    b = np.empty_like(a)
+    w = _c(w, np.float64)
+    nz, ny, nx = a.shape
+    sums = np.zeros(max(1, nsweeps), dtype=np.float64)
+    par = lib().orc_box27_run_f64(nx, ny, nz, _ptr(w), _ptr(a), _ptr(b), nsweeps, _ptr(sums))
     return (a if par == 0 else b), sums[:nsweeps]
 
 

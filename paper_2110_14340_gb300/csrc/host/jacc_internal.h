@@ -1,0 +1,75 @@
+// jacc_internal.h - shared declarations of the host runtime (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../../include/jacc.h"
+#include "../kernels/jacc_params.h"
+
+namespace jacc {
+
+// Records `msg` as the calling thread's last error and returns `st`.
+jacc_status fail(jacc_status st, const std::string& msg);
+jacc_status ok();
+// Wraps a CUDA runtime status: JACC_OK or JACC_ERR_CUDA with the CUDA message.
+jacc_status cuda_check(cudaError_t e, const char* what);
+
+struct TileCfg {
+  int bx, by, vec16, zc;
+};
+const TileCfg& tile_cfg(int id);
+
+// One cached sweep graph.
+struct SweepGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  u64* scratch = nullptr;  // max-abs word of this graph (device)
+};
+
+using GraphKey = std::tuple<const void*, const void*, int32_t, const double*>;
+
+// A specialised kernel (the object behind a jacc_kernel handle).
+struct Kernel {
+  jacc_kernel_desc desc{};
+  std::string key;
+  JParams params{};
+  int tile = 0;
+  int elem = 8;                 // bytes per element
+  int vec = 1;                  // elements per thread in x
+  bool jit = false;
+  double compile_ms = 0.0;
+  const void* func = nullptr;   // kernel entry (host stub or cudaKernel_t)
+  cudaLibrary_t lib = nullptr;  // NVRTC module, if jit
+  dim3 grid, block;
+  int tblock = 1;
+  int refcount = 0;
+  u64* scratch = nullptr;       // max-abs word for direct launches (device)
+  std::map<GraphKey, SweepGraph> graphs;
+};
+
+// Launch one sweep of `k` (no validation).  maxword may be null.
+cudaError_t launch_sweep_kernel(const Kernel& k, const void* u, void* v, double* resid, const u64* maxword,
+                                cudaStream_t s);
+// Enqueue the max-abs pre-pass of `n` doubles into maxword (zeroing it first).
+cudaError_t launch_maxabs(const double* u, long long n, u64* maxword, cudaStream_t s);
+cudaError_t launch_fill_skipped(double* resid, int n, int T, cudaStream_t s);
+
+// NVRTC: compile `src` (plus jacc_params.h) for sm_103a, load it, return
+// kernel `name`.  Uses the on-disk cache under $JACC_CACHE_DIR if set.
+jacc_status jit_compile(const std::string& src, const char* name, cudaLibrary_t* lib, const void** func,
+                        double* ms);
+// The device-code text embedded at build time.
+const char* device_source();
+const char* params_source();
+
+std::mutex& global_mutex();
+
+}  // namespace jacc

@@ -1,0 +1,456 @@
+// runtime.cpp - specialisation cache, launches and graph-captured sweeps.
+//
+// jacc_specialize follows the paper's kernel cache and specialisation
+// (§3.1: code compiled once is cached and reused; §3.2.2: runtime-invariant
+// parameters are substituted by constants, non-conflicting pointers are
+// restrict).  Descriptors are canonicalised into a byte key; identical keys
+// share one Kernel object with a reference count.  Without JACC_SPEC_JIT the
+// kernel is one of the precompiled instantiations (extents and coefficients
+// as arguments); with it, NVRTC compiles the same template with them folded.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "../kernels/tiles.h"
+#include "jacc_internal.h"
+
+extern "C" const void* const jacc_tab_5_64[JACC_NTILES];
+extern "C" const void* const jacc_tab_5_32[JACC_NTILES];
+extern "C" const void* const jacc_tab_7_64[JACC_NTILES];
+extern "C" const void* const jacc_tab_7_32[JACC_NTILES];
+extern "C" const void* const jacc_tab_27_64[JACC_NTILES];
+extern "C" const void* const jacc_tab_27_32[JACC_NTILES];
+
+namespace jacc {
+
+static const TileCfg kTiles[JACC_NTILES] = {
+#define JACC_TILE_ROW(id, BX, BY, VEC, ZC) {BX, BY, VEC, ZC},
+    JACC_TILE_LIST(JACC_TILE_ROW)
+#undef JACC_TILE_ROW
+};
+
+const TileCfg& tile_cfg(int id) { return kTiles[id]; }
+
+static std::map<std::string, Kernel*>& cache() {
+  static std::map<std::string, Kernel*> c;
+  return c;
+}
+
+// d = m * 2^-k with m odd (d > 0 finite).  Returns false if d is not of
+// that form with k in [0, 62].
+static bool dyadic(double d, uint64_t* m, int* k) {
+  if (!(d > 0.0) || !std::isfinite(d)) return false;
+  int e = 0;
+  double f = std::frexp(d, &e);  // d = f 2^e, f in [0.5, 1)
+  uint64_t mm = static_cast<uint64_t>(std::ldexp(f, 53));
+  int kk = 53 - e;
+  while ((mm & 1u) == 0 && kk > 0) {
+    mm >>= 1;
+    --kk;
+  }
+  if ((mm & 1u) == 0 || kk > 62 || kk < 0) return false;
+  *m = mm;
+  *k = kk;
+  return true;
+}
+
+static const void* table_entry(int stencil, int dtype, int tile) {
+  const void* const* t = nullptr;
+  if (stencil == 5) t = dtype == 64 ? jacc_tab_5_64 : jacc_tab_5_32;
+  if (stencil == 7) t = dtype == 64 ? jacc_tab_7_64 : jacc_tab_7_32;
+  if (stencil == 27) t = dtype == 64 ? jacc_tab_27_64 : jacc_tab_27_32;
+  return t ? t[tile] : nullptr;
+}
+
+// Fills the fixed-point fields of p.  Returns the chosen path.
+static int plan_fixed(const jacc_kernel_desc& d, JParams& p) {
+  p.fpath = JACC_FP_NONE;
+  if (d.dtype != JACC_F64 || d.arith != JACC_ARITH_AUTO) return p.fpath;
+  if (d.stencil == JACC_STENCIL_5PT) {
+    p.fpath = JACC_FP_JACOBI;
+    p.fk = 2;
+  } else if (d.stencil == JACC_STENCIL_7PT) {
+    const double r = d.coeffs[0];
+    if (r == 0.0) {
+      p.fpath = JACC_FP_SMALL;
+      p.fa = 1;
+      p.fb = 0;
+      p.fk = 0;
+    } else if (r > 0.0 && r <= 1.0 / 6.0) {
+      uint64_t m;
+      int k;
+      if (dyadic(r, &m, &k)) {
+        if (k <= 5) {
+          p.fpath = JACC_FP_SMALL;
+          p.fb = static_cast<i64>(m);
+          p.fa = (static_cast<i64>(1) << k) - 6 * static_cast<i64>(m);
+          p.fk = k;
+        } else {
+          p.fpath = JACC_FP_WIDE;
+          p.fw0 = static_cast<i64>(m);
+          p.fk = k;
+        }
+      }
+    }
+  } else if (d.stencil == JACC_STENCIL_27PT) {
+    const double* w = d.coeffs;
+    for (int j = 0; j < 4; ++j)
+      if (!(w[j] >= 0.0) || !std::isfinite(w[j])) return p.fpath;
+    const double W = w[0] + 6.0 * w[1] + 12.0 * w[2] + 8.0 * w[3];
+    if (!(W <= 1.0 + std::ldexp(1.0, -20))) return p.fpath;
+    uint64_t m[4] = {0, 0, 0, 0};
+    int k[4] = {0, 0, 0, 0};
+    int K = 0;
+    for (int j = 0; j < 4; ++j) {
+      if (w[j] == 0.0) continue;
+      if (!dyadic(w[j], &m[j], &k[j])) return p.fpath;
+      K = k[j] > K ? k[j] : K;
+    }
+    if (K > 62) return p.fpath;
+    i64 f[4];
+    for (int j = 0; j < 4; ++j) {
+      if (w[j] == 0.0) {
+        f[j] = 0;
+        continue;
+      }
+      const int sh = K - k[j];
+      if (sh >= 64 || (m[j] >> (63 - sh)) != 0) return p.fpath;  // factor must stay below 2^63
+      f[j] = static_cast<i64>(m[j] << sh);
+    }
+    p.fpath = JACC_FP_WIDE;
+    p.fw0 = f[0];
+    p.fw1 = f[1];
+    p.fw2 = f[2];
+    p.fw3 = f[3];
+    p.fk = K;
+  }
+  return p.fpath;
+}
+
+static jacc_status validate(const jacc_kernel_desc& d) {
+  if (d.stencil != 5 && d.stencil != 7 && d.stencil != 27) return fail(JACC_ERR_INVALID_ARG, "unknown stencil");
+  if (d.dtype != JACC_F32 && d.dtype != JACC_F64) return fail(JACC_ERR_INVALID_ARG, "dtype must be 32 or 64");
+  if (d.tile_id < -1 || d.tile_id >= JACC_NTILES) return fail(JACC_ERR_INVALID_ARG, "tile_id out of range");
+  if (d.arith != JACC_ARITH_AUTO && d.arith != JACC_ARITH_NATIVE) return fail(JACC_ERR_INVALID_ARG, "bad arith");
+  if (d.flags & ~JACC_SPEC_JIT) return fail(JACC_ERR_INVALID_ARG, "unknown specialisation flags");
+  if (d.nx < 3 || d.ny < 3 || d.nz < 1) return fail(JACC_ERR_INVALID_ARG, "extents must be >= 3");
+  if (d.stencil == 5) {
+    if (d.nz != 1) return fail(JACC_ERR_INVALID_ARG, "5-point stencil is 2D: nz must be 1");
+    if (d.boundary != JACC_DIRICHLET) return fail(JACC_ERR_UNSUPPORTED, "5-point stencil supports Dirichlet only");
+  } else {
+    if (d.nz < 3) return fail(JACC_ERR_INVALID_ARG, "3D stencil: nz must be >= 3");
+  }
+  if (d.stencil == 7 && d.boundary != JACC_DIRICHLET) return fail(JACC_ERR_UNSUPPORTED, "7-point: Dirichlet only");
+  if (d.stencil == 27 && d.boundary != JACC_PERIODIC) return fail(JACC_ERR_UNSUPPORTED, "27-point: periodic only");
+  if (d.tblock < 0) return fail(JACC_ERR_INVALID_ARG, "tblock < 0");
+  if (d.tblock > 1) return fail(JACC_ERR_UNSUPPORTED, "temporal blocking is not available in this build");
+  for (int j = 0; j < 4; ++j)
+    if (!std::isfinite(d.coeffs[j])) return fail(JACC_ERR_INVALID_ARG, "non-finite coefficient");
+  const double n = static_cast<double>(d.nx) * static_cast<double>(d.ny) * static_cast<double>(d.nz);
+  if (n > 9.0e18) return fail(JACC_ERR_OVERFLOW, "element count overflows int64");
+  return ok();
+}
+
+static int default_tile(const jacc_kernel_desc& d) {
+  const int V = d.dtype == 64 ? 2 : 4;
+  const bool vec_ok = (d.nx % V) == 0;
+  if (d.stencil == 5) return vec_ok ? 5 : 4;
+  return vec_ok ? 15 : 14;
+}
+
+static bool tile_valid(const jacc_kernel_desc& d, int t) {
+  const TileCfg& c = kTiles[t];
+  const int V = c.vec16 ? (d.dtype == 64 ? 2 : 4) : 1;
+  if (d.nx % V) return false;
+  // grid-dimension limits
+  const int64_t gy = d.stencil == 5 ? (d.ny + c.by * (c.zc / 4) - 1) / (c.by * (c.zc / 4)) : (d.ny + c.by - 1) / c.by;
+  const int64_t gz = d.stencil == 5 ? 1 : (d.nz + c.zc - 1) / c.zc;
+  const int64_t gx = (d.nx + c.bx * V - 1) / (c.bx * V);
+  return gx < (1ll << 31) && gy <= 65535 && gz <= 65535;
+}
+
+static std::string key_of(const jacc_kernel_desc& d, int tile) {
+  jacc_kernel_desc c = d;
+  c.tile_id = tile;
+  c.reserved = 0;
+  if (c.tblock == 0) c.tblock = 1;
+  return std::string(reinterpret_cast<const char*>(&c), sizeof(c));
+}
+
+// The NVRTC source of a folded variant: the device text plus a struct whose
+// static constexpr members replace JParams.
+static std::string jit_source(const Kernel& k) {
+  const JParams& p = k.params;
+  const TileCfg& c = kTiles[k.tile];
+  char buf[2048];
+  const char* T = k.desc.dtype == 64 ? "double" : "float";
+  const char* entry = k.desc.stencil == 5 ? "jacobi2d_entry" : (k.desc.stencil == 7 ? "heat3d_entry" : "box27_entry");
+  const int zc = k.desc.stencil == 5 ? c.zc / 4 : c.zc;
+  std::snprintf(buf, sizeof(buf),
+                "\nstruct JFold {\n"
+                "  static constexpr i64 nx = %lldll, ny = %lldll, nz = %lldll;\n"
+                "  static constexpr double c0 = %a, c1 = %a, c2 = %a, c3 = %a;\n"
+                "  static constexpr i64 fa = %lldll, fb = %lldll;\n"
+                "  static constexpr i64 fw0 = %lldll, fw1 = %lldll, fw2 = %lldll, fw3 = %lldll;\n"
+                "  static constexpr int fk = %d, fpath = %d;\n"
+                "};\n"
+                "extern \"C\" __global__ void __launch_bounds__(%d) jacc_jit(const %s* __restrict__ u, "
+                "%s* __restrict__ v, JParams, double* resid, const u64* maxword) {\n"
+                "  const JFold f{};\n"
+                "  %s<%s, %d, %d, %d, %d>(u, v, f, resid, maxword);\n"
+                "}\n",
+                (long long)p.nx, (long long)p.ny, (long long)p.nz, p.c0, p.c1, p.c2, p.c3, (long long)p.fa,
+                (long long)p.fb, (long long)p.fw0, (long long)p.fw1, (long long)p.fw2, (long long)p.fw3, p.fk, p.fpath,
+                c.bx * c.by, T, T, entry, T, c.bx, c.by, k.vec, zc);
+  return std::string(device_source()) + buf;
+}
+
+static void free_kernel(Kernel* k) {
+  for (auto& g : k->graphs) {
+    if (g.second.exec) cudaGraphExecDestroy(g.second.exec);
+    if (g.second.graph) cudaGraphDestroy(g.second.graph);
+    if (g.second.scratch) cudaFree(g.second.scratch);
+  }
+  k->graphs.clear();
+  if (k->scratch) cudaFree(k->scratch);
+  if (k->lib) cudaLibraryUnload(k->lib);
+  delete k;
+}
+
+}  // namespace jacc
+
+using namespace jacc;
+
+extern "C" jacc_status jacc_tile_info(int32_t tile_id, jacc_tile* out) {
+  if (tile_id < 0 || tile_id >= JACC_NTILES || !out) return fail(JACC_ERR_INVALID_ARG, "bad tile_id or NULL out");
+  const TileCfg& c = kTiles[tile_id];
+  out->bx = c.bx;
+  out->by = c.by;
+  out->vec16 = c.vec16;
+  out->zc = c.zc;
+  return ok();
+}
+
+extern "C" jacc_status jacc_specialize(const jacc_kernel_desc* desc, jacc_kernel* out) {
+  if (!desc || !out) return fail(JACC_ERR_INVALID_ARG, "NULL descriptor or output");
+  jacc_status st = validate(*desc);
+  if (st) return st;
+  int tile = desc->tile_id >= 0 ? desc->tile_id : default_tile(*desc);
+  if (!tile_valid(*desc, tile))
+    return fail(JACC_ERR_INVALID_ARG, "tile " + std::to_string(tile) + " does not fit this shape (x vector width)");
+  const std::string key = key_of(*desc, tile);
+  std::lock_guard<std::mutex> lock(global_mutex());
+  auto it = cache().find(key);
+  if (it != cache().end()) {
+    it->second->refcount++;
+    *out = reinterpret_cast<jacc_kernel>(it->second);
+    return ok();
+  }
+  std::unique_ptr<Kernel> k(new Kernel());
+  k->desc = *desc;
+  k->desc.tile_id = tile;
+  k->key = key;
+  k->tile = tile;
+  k->elem = desc->dtype / 8;
+  const TileCfg& c = kTiles[tile];
+  k->vec = c.vec16 ? 16 / k->elem : 1;
+  JParams& p = k->params;
+  p.nx = desc->nx;
+  p.ny = desc->ny;
+  p.nz = desc->nz;
+  p.c0 = desc->coeffs[0];
+  p.c1 = desc->coeffs[1];
+  p.c2 = desc->coeffs[2];
+  p.c3 = desc->coeffs[3];
+  plan_fixed(*desc, p);
+  k->block = dim3(c.bx, c.by, 1);
+  const int64_t tx = static_cast<int64_t>(c.bx) * k->vec;
+  if (desc->stencil == 5) {
+    const int64_t ty = static_cast<int64_t>(c.by) * (c.zc / 4);
+    k->grid = dim3(static_cast<unsigned>((desc->nx + tx - 1) / tx), static_cast<unsigned>((desc->ny + ty - 1) / ty), 1);
+  } else {
+    k->grid = dim3(static_cast<unsigned>((desc->nx + tx - 1) / tx), static_cast<unsigned>((desc->ny + c.by - 1) / c.by),
+                   static_cast<unsigned>((desc->nz + c.zc - 1) / c.zc));
+  }
+  if (desc->flags & JACC_SPEC_JIT) {
+    st = jit_compile(jit_source(*k), "jacc_jit", &k->lib, &k->func, &k->compile_ms);
+    if (st) return st;
+    k->jit = true;
+  } else {
+    k->func = table_entry(desc->stencil, desc->dtype, tile);
+    if (!k->func) return fail(JACC_ERR_UNSUPPORTED, "no precompiled kernel for this descriptor");
+  }
+  if (desc->dtype == 64 && p.fpath != JACC_FP_NONE) {
+    st = cuda_check(cudaMalloc(reinterpret_cast<void**>(&k->scratch), 256), "cudaMalloc(scratch)");
+    if (st) {
+      if (k->lib) cudaLibraryUnload(k->lib);
+      return st;
+    }
+  }
+  k->refcount = 1;
+  Kernel* raw = k.release();
+  cache()[key] = raw;
+  *out = reinterpret_cast<jacc_kernel>(raw);
+  return ok();
+}
+
+extern "C" jacc_status jacc_kernel_info(jacc_kernel h, jacc_kernel_info_t* out) {
+  if (!h || !out) return fail(JACC_ERR_INVALID_ARG, "NULL handle or output");
+  const Kernel& k = *reinterpret_cast<Kernel*>(h);
+  out->tile_id = k.tile;
+  out->jit = k.jit ? 1 : 0;
+  out->fixed_point = k.params.fpath != JACC_FP_NONE ? 1 : 0;
+  out->tblock = k.tblock;
+  out->block[0] = static_cast<int32_t>(k.block.x);
+  out->block[1] = static_cast<int32_t>(k.block.y);
+  out->block[2] = static_cast<int32_t>(k.block.z);
+  out->grid[0] = static_cast<int32_t>(k.grid.x);
+  out->grid[1] = static_cast<int32_t>(k.grid.y);
+  out->grid[2] = static_cast<int32_t>(k.grid.z);
+  out->compile_ms = k.compile_ms;
+  return ok();
+}
+
+extern "C" jacc_status jacc_release(jacc_kernel h) {
+  if (!h) return fail(JACC_ERR_INVALID_ARG, "NULL handle");
+  std::lock_guard<std::mutex> lock(global_mutex());
+  Kernel* k = reinterpret_cast<Kernel*>(h);
+  auto it = cache().find(k->key);
+  if (it == cache().end() || it->second != k) return fail(JACC_ERR_INVALID_ARG, "unknown or released handle");
+  if (--k->refcount > 0) return ok();
+  cache().erase(it);
+  free_kernel(k);
+  return ok();
+}
+
+extern "C" jacc_status jacc_shutdown(void) {
+  std::lock_guard<std::mutex> lock(global_mutex());
+  for (auto& e : cache()) free_kernel(e.second);
+  cache().clear();
+  return ok();
+}
+
+// ---------------------------------------------------------------- launches
+
+namespace jacc {
+
+cudaError_t launch_sweep_kernel(const Kernel& k, const void* u, void* v, double* resid, const u64* maxword,
+                                cudaStream_t s) {
+  JParams p = k.params;
+  const void* args[] = {&u, &v, &p, &resid, &maxword};
+  return cudaLaunchKernel(k.func, k.grid, k.block, const_cast<void**>(args), 0, s);
+}
+
+}  // namespace jacc
+
+static jacc_status check_buffers(const Kernel& k, const void* a, const void* b) {
+  if (!a || !b) return fail(JACC_ERR_INVALID_ARG, "NULL field pointer");
+  if ((reinterpret_cast<uintptr_t>(a) % 16) || (reinterpret_cast<uintptr_t>(b) % 16))
+    return fail(JACC_ERR_INVALID_ARG, "field pointers must be 16-byte aligned");
+  const uintptr_t bytes = static_cast<uintptr_t>(k.desc.nx * k.desc.ny * k.desc.nz) * k.elem;
+  const uintptr_t pa = reinterpret_cast<uintptr_t>(a), pb = reinterpret_cast<uintptr_t>(b);
+  if (pa < pb + bytes && pb < pa + bytes) return fail(JACC_ERR_INVALID_ARG, "input and output fields overlap");
+  return ok();
+}
+
+// Enqueue one sweep with its pre-pass (fixed point) and residual zeroing.
+static jacc_status enqueue_one(const Kernel& k, const void* u, void* v, double* resid, u64* scratch, cudaStream_t s) {
+  const u64* mw = nullptr;
+  if (k.params.fpath != JACC_FP_NONE && k.desc.dtype == 64) {
+    jacc_status st = cuda_check(launch_maxabs(static_cast<const double*>(u), k.desc.nx * k.desc.ny * k.desc.nz,
+                                              scratch, s),
+                                "max-abs pre-pass");
+    if (st) return st;
+    mw = scratch;
+  }
+  if (resid) {
+    jacc_status st = cuda_check(cudaMemsetAsync(resid, 0, sizeof(double), s), "cudaMemsetAsync(resid)");
+    if (st) return st;
+  }
+  return cuda_check(launch_sweep_kernel(k, u, v, resid, mw, s), "stencil launch");
+}
+
+extern "C" jacc_status jacc_launch(jacc_kernel h, const void* u_in, void* u_out, double* resid_dev, uintptr_t stream) {
+  if (!h) return fail(JACC_ERR_INVALID_ARG, "NULL handle");
+  const Kernel& k = *reinterpret_cast<Kernel*>(h);
+  jacc_status st = check_buffers(k, u_in, u_out);
+  if (st) return st;
+  return enqueue_one(k, u_in, u_out, resid_dev, k.scratch, reinterpret_cast<cudaStream_t>(stream));
+}
+
+// The full sweep sequence on stream s.
+static jacc_status enqueue_sweeps(const Kernel& k, void* u0, void* u1, int32_t n, double* resid, u64* scratch,
+                                  cudaStream_t s) {
+  const u64* mw = nullptr;
+  if (k.params.fpath != JACC_FP_NONE && k.desc.dtype == 64) {
+    jacc_status st = cuda_check(
+        launch_maxabs(static_cast<const double*>(u0), k.desc.nx * k.desc.ny * k.desc.nz, scratch, s), "max-abs pre-pass");
+    if (st) return st;
+    mw = scratch;
+  }
+  if (resid) {
+    jacc_status st = cuda_check(cudaMemsetAsync(resid, 0, sizeof(double) * static_cast<size_t>(n), s), "memset resid");
+    if (st) return st;
+  }
+  for (int32_t i = 0; i < n; ++i) {
+    const void* src = (i % 2 == 0) ? u0 : u1;
+    void* dst = (i % 2 == 0) ? u1 : u0;
+    jacc_status st = cuda_check(launch_sweep_kernel(k, src, dst, resid ? resid + i : nullptr, mw, s), "stencil launch");
+    if (st) return st;
+  }
+  return ok();
+}
+
+extern "C" jacc_status jacc_sweep(jacc_kernel h, void* u0, void* u1, int32_t nsweeps, double* resid_dev, uint32_t flags,
+                                  uintptr_t stream, int32_t* final_buf) {
+  if (!h) return fail(JACC_ERR_INVALID_ARG, "NULL handle");
+  if (nsweeps < 1) return fail(JACC_ERR_INVALID_ARG, "nsweeps must be >= 1");
+  if (flags & ~JACC_SWEEP_GRAPH) return fail(JACC_ERR_INVALID_ARG, "unknown sweep flags");
+  Kernel& k = *reinterpret_cast<Kernel*>(h);
+  jacc_status st = check_buffers(k, u0, u1);
+  if (st) return st;
+  if (k.desc.stencil == 27 && k.params.fpath != JACC_FP_NONE) {
+    // the fixed-point scale is taken once from u0; values may grow by W per sweep
+    const double W = k.desc.coeffs[0] + 6 * k.desc.coeffs[1] + 12 * k.desc.coeffs[2] + 8 * k.desc.coeffs[3];
+    if (std::pow(W, static_cast<double>(nsweeps)) > 4.0)
+      return fail(JACC_ERR_UNSUPPORTED, "weight sum too far above 1 for this many fixed-point sweeps");
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (final_buf) *final_buf = nsweeps % 2;
+  if (!(flags & JACC_SWEEP_GRAPH)) return enqueue_sweeps(k, u0, u1, nsweeps, resid_dev, k.scratch, s);
+
+  std::lock_guard<std::mutex> lock(global_mutex());
+  const GraphKey gk{u0, u1, nsweeps, resid_dev};
+  auto it = k.graphs.find(gk);
+  if (it == k.graphs.end()) {
+    SweepGraph g;
+    if (k.params.fpath != JACC_FP_NONE && k.desc.dtype == 64) {
+      st = cuda_check(cudaMalloc(reinterpret_cast<void**>(&g.scratch), 256), "cudaMalloc(graph scratch)");
+      if (st) return st;
+    }
+    cudaStream_t cap = nullptr;
+    st = cuda_check(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "cudaStreamCreate");
+    if (!st) st = cuda_check(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+    if (!st) {
+      jacc_status est = enqueue_sweeps(k, u0, u1, nsweeps, resid_dev, g.scratch, cap);
+      cudaGraph_t graph = nullptr;
+      cudaError_t ce = cudaStreamEndCapture(cap, &graph);
+      if (est) st = est;
+      else st = cuda_check(ce, "cudaStreamEndCapture");
+      g.graph = graph;
+      if (!st) st = cuda_check(cudaGraphInstantiate(&g.exec, g.graph, 0), "cudaGraphInstantiate");
+    }
+    if (cap) cudaStreamDestroy(cap);
+    if (st) {
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+      if (g.graph) cudaGraphDestroy(g.graph);
+      if (g.scratch) cudaFree(g.scratch);
+      return st;
+    }
+    it = k.graphs.emplace(gk, g).first;
+  }
+  return cuda_check(cudaGraphLaunch(it->second.exec, s), "cudaGraphLaunch");
+}

@@ -1,0 +1,25 @@
+// aux.cu - non-template helper kernels (max-abs pre-pass, NaN fill) and their launchers.
+#define JACC_AUX_KERNELS
+#include "jacc_device.cuh"
+
+#include <cuda_runtime.h>
+
+namespace jacc {
+
+cudaError_t launch_maxabs(const double* u, long long n, u64* maxword, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(maxword, 0, sizeof(u64), s);
+  if (e != cudaSuccess) return e;
+  long long pairs = n / 2;
+  long long blocks = (pairs + 255) / 256;
+  if (blocks < 1) blocks = 1;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  jacc_k_maxabs<<<(unsigned)blocks, 256, 0, s>>>(u, n, maxword);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_skipped(double* resid, int n, int T, cudaStream_t s) {
+  jacc_k_fill_skipped<<<(n + 255) / 256, 256, 0, s>>>(resid, n, T);
+  return cudaGetLastError();
+}
+
+}  // namespace jacc

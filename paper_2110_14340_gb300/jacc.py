@@ -1,0 +1,249 @@
+"""Python binding of libjacc.so (ctypes).  Argument marshalling only.
+
+Every computation happens in the library's CUDA kernels; this module turns
+torch tensors into device pointers and Python values into the C structs of
+include/jacc.h.  If the library is missing, `lib()` raises: there is no
+fallback path.
+"""
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libjacc.so")
+
+MAX_DIMS = 8
+MAX_LOOPS = 8
+NUM_TILES = 24
+
+OK = 0
+ERR_INVALID_ARG, ERR_OUT_OF_BOUNDS, ERR_OVERFLOW, ERR_CUDA = -1, -2, -3, -4
+ERR_COMPILE, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_NOMEM = -5, -6, -7, -8
+STATUS_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OUT_OF_BOUNDS", -3: "OVERFLOW", -4: "CUDA", -5: "COMPILE",
+                -6: "TIMEOUT", -7: "UNSUPPORTED", -8: "NOMEM"}
+
+STENCIL_5PT, STENCIL_7PT, STENCIL_27PT = 5, 7, 27
+F32, F64 = 32, 64
+DIRICHLET, PERIODIC = 0, 1
+ARITH_AUTO, ARITH_NATIVE = 0, 1
+SPEC_JIT = 1
+SWEEP_GRAPH = 1
+
+
+class JaccError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"jacc status {status} ({STATUS_NAMES.get(status, '?')}): {msg}")
+        self.status = status
+
+
+class Loop(C.Structure):
+    _fields_ = [("lo", C.c_int64), ("hi", C.c_int64), ("step", C.c_int64)]
+
+
+class Ref(C.Structure):
+    _fields_ = [("array_id", C.c_int32), ("ndim", C.c_int32), ("is_write", C.c_int32), ("reserved", C.c_int32),
+                ("coef", (C.c_int64 * MAX_LOOPS) * MAX_DIMS), ("off", C.c_int64 * MAX_DIMS)]
+
+
+class Array(C.Structure):
+    _fields_ = [("ndim", C.c_int32), ("reserved", C.c_int32), ("extent", C.c_int64 * MAX_DIMS)]
+
+
+class Region(C.Structure):
+    _fields_ = [("has_read", C.c_int32), ("has_write", C.c_int32),
+                ("rlo", C.c_int64 * MAX_DIMS), ("rhi", C.c_int64 * MAX_DIMS),
+                ("wlo", C.c_int64 * MAX_DIMS), ("whi", C.c_int64 * MAX_DIMS),
+                ("rlin_lo", C.c_int64), ("rlin_hi", C.c_int64), ("wlin_lo", C.c_int64), ("wlin_hi", C.c_int64)]
+
+
+class KernelDesc(C.Structure):
+    _fields_ = [("stencil", C.c_int32), ("dtype", C.c_int32), ("boundary", C.c_int32), ("tile_id", C.c_int32),
+                ("nx", C.c_int64), ("ny", C.c_int64), ("nz", C.c_int64), ("coeffs", C.c_double * 4),
+                ("arith", C.c_int32), ("flags", C.c_uint32), ("tblock", C.c_int32), ("reserved", C.c_int32)]
+
+
+class KernelInfo(C.Structure):
+    _fields_ = [("tile_id", C.c_int32), ("jit", C.c_int32), ("fixed_point", C.c_int32), ("tblock", C.c_int32),
+                ("block", C.c_int32 * 3), ("grid", C.c_int32 * 3), ("compile_ms", C.c_double)]
+
+
+class Tile(C.Structure):
+    _fields_ = [("bx", C.c_int32), ("by", C.c_int32), ("vec16", C.c_int32), ("zc", C.c_int32)]
+
+
+# Every symbol include/jacc.h declares, with its argument and result types.
+P = C.c_void_p
+SIGNATURES = {
+    "jacc_last_error": ([], C.c_char_p),
+    "jacc_version": ([], C.c_char_p),
+    "jacc_region_analyze": ([C.c_int32, P, C.c_int32, P, C.c_int32, P, P], C.c_int32),
+    "jacc_specialize": ([P, P], C.c_int32),
+    "jacc_kernel_info": ([P, P], C.c_int32),
+    "jacc_release": ([P], C.c_int32),
+    "jacc_tile_info": ([C.c_int32, P], C.c_int32),
+    "jacc_launch": ([P, P, P, P, C.c_size_t], C.c_int32),
+    "jacc_sweep": ([P, P, P, C.c_int32, P, C.c_uint32, C.c_size_t, P], C.c_int32),
+    "jacc_shutdown": ([], C.c_int32),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libjacc.so (built by paper_2110_14340_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libjacc.so not built ({LIB_PATH}); run paper_2110_14340_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, (args, res) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(st):
+    if st != OK:
+        raise JaccError(st, lib().jacc_last_error().decode())
+
+
+def version():
+    return lib().jacc_version().decode()
+
+
+# ----------------------------------------------------------------------------- region analysis
+
+def region_analyze(loops, refs, arrays):
+    """Same argument format as the oracle's region_analyze; returns (status, [dict per array])."""
+    L = (Loop * max(1, len(loops)))()
+    for k, (lo, hi, st) in enumerate(loops):
+        L[k].lo, L[k].hi, L[k].step = lo, hi, st
+    R = (Ref * max(1, len(refs)))()
+    for r, ref in enumerate(refs):
+        R[r].array_id = ref["array"]
+        R[r].ndim = len(ref["off"])
+        R[r].is_write = 1 if ref.get("write") else 0
+        for d, row in enumerate(ref["coef"]):
+            for k, c in enumerate(row):
+                R[r].coef[d][k] = c
+        for d, o in enumerate(ref["off"]):
+            R[r].off[d] = o
+    A = (Array * max(1, len(arrays)))()
+    for a, ext in enumerate(arrays):
+        A[a].ndim = len(ext)
+        for d, e in enumerate(ext):
+            A[a].extent[d] = e
+    O = (Region * max(1, len(arrays)))()
+    st = lib().jacc_region_analyze(len(loops), C.cast(L, P), len(refs), C.cast(R, P), len(arrays), C.cast(A, P),
+                                   C.cast(O, P))
+    out = []
+    for a, ext in enumerate(arrays):
+        nd = len(ext)
+        o = O[a]
+        out.append(dict(has_read=bool(o.has_read), has_write=bool(o.has_write),
+                        rlo=list(o.rlo[:nd]), rhi=list(o.rhi[:nd]), wlo=list(o.wlo[:nd]), whi=list(o.whi[:nd]),
+                        rlin=(o.rlin_lo, o.rlin_hi), wlin=(o.wlin_lo, o.wlin_hi)))
+    return st, out
+
+
+# ----------------------------------------------------------------------------- kernels
+
+def tile_info(tile_id):
+    t = Tile()
+    _check(lib().jacc_tile_info(tile_id, C.byref(t)))
+    return dict(bx=t.bx, by=t.by, vec16=bool(t.vec16), zc=t.zc)
+
+
+class Kernel:
+    """A specialised stencil kernel (owns one reference to the library handle)."""
+
+    def __init__(self, stencil, dtype, nx, ny, nz=1, coeffs=(0.0, 0.0, 0.0, 0.0), tile_id=-1, jit=False,
+                 arith=ARITH_AUTO, boundary=None, tblock=0):
+        d = KernelDesc()
+        d.stencil = stencil
+        d.dtype = dtype
+        d.boundary = (PERIODIC if stencil == STENCIL_27PT else DIRICHLET) if boundary is None else boundary
+        d.tile_id = tile_id
+        d.nx, d.ny, d.nz = nx, ny, nz
+        cs = list(coeffs) + [0.0] * (4 - len(coeffs))
+        for j in range(4):
+            d.coeffs[j] = float(cs[j])
+        d.arith = arith
+        d.flags = SPEC_JIT if jit else 0
+        d.tblock = tblock
+        h = C.c_void_p()
+        _check(lib().jacc_specialize(C.byref(d), C.byref(h)))
+        self.handle = h
+        self.desc = d
+        self.shape = (ny, nx) if stencil == STENCIL_5PT else (nz, ny, nx)
+
+    def info(self):
+        i = KernelInfo()
+        _check(lib().jacc_kernel_info(self.handle, C.byref(i)))
+        return dict(tile_id=i.tile_id, jit=bool(i.jit), fixed_point=bool(i.fixed_point), tblock=i.tblock,
+                    block=tuple(i.block), grid=tuple(i.grid), compile_ms=i.compile_ms)
+
+    def release(self):
+        if self.handle:
+            _check(lib().jacc_release(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            if self.handle and _lib is not None:
+                _lib.jacc_release(self.handle)
+        except Exception:
+            pass
+
+
+def specialize(*args, **kw):
+    return Kernel(*args, **kw)
+
+
+def _field(k, t, name):
+    import torch
+    want = torch.float64 if k.desc.dtype == F64 else torch.float32
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != want or not t.is_contiguous() or tuple(t.shape) != k.shape:
+        raise ValueError(f"{name} must be a contiguous {want} tensor of shape {k.shape}")
+    return t.data_ptr()
+
+
+def _resid(r):
+    import torch
+    if r is None:
+        return None
+    if not isinstance(r, torch.Tensor) or not r.is_cuda or r.dtype != torch.float64 or not r.is_contiguous():
+        raise ValueError("resid must be a contiguous CUDA float64 tensor")
+    return r.data_ptr()
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream
+
+
+def launch(k, u_in, u_out, resid=None, stream=None):
+    """One sweep u_in -> u_out; resid (1 double) receives the reduction."""
+    if resid is not None and resid.numel() < 1:
+        raise ValueError("resid needs one element")
+    _check(lib().jacc_launch(k.handle, _field(k, u_in, "u_in"), _field(k, u_out, "u_out"), _resid(resid),
+                             _stream(stream)))
+
+
+def sweep(k, u0, u1, nsweeps, resid=None, graph=True, stream=None):
+    """nsweeps ping-pong sweeps; returns 0 if the result is in u0, 1 if in u1."""
+    if resid is not None and resid.numel() < nsweeps:
+        raise ValueError("resid needs nsweeps elements")
+    fb = C.c_int32(-1)
+    _check(lib().jacc_sweep(k.handle, _field(k, u0, "u0"), _field(k, u1, "u1"), nsweeps, _resid(resid),
+                            SWEEP_GRAPH if graph else 0, _stream(stream), C.byref(fb)))
+    return fb.value
+
+
+def shutdown():
+    if _lib is not None:
+        _check(_lib.jacc_shutdown())

@@ -1,0 +1,91 @@
+"""Host-side checks of the C ABI (CPU only: no kernel is launched).
+
+The library loads without a GPU, exports every function include/jacc.h
+declares, and its region analyser (pure host code) matches the oracle
+bit-exactly on the same nests the oracle is pinned on.
+"""
+import os
+import random
+import re
+
+import pytest
+
+from paper_2110_14340_gb300 import jacc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2110_14340_gb300 import build
+    build.build()
+    return jacc.lib()
+
+
+def declared_functions():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", f)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(jacc_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert "jacc_region_analyze" in names and "jacc_sweep" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) <= set(jacc.SIGNATURES), set(names) - set(jacc.SIGNATURES)
+
+
+def test_version_and_tiles(lib):
+    assert "sm_103a" in jacc.version()
+    seen = set()
+    for t in range(jacc.NUM_TILES):
+        info = jacc.tile_info(t)
+        seen.add((info["bx"], info["by"], info["vec16"], info["zc"]))
+    assert len(seen) == jacc.NUM_TILES
+    with pytest.raises(jacc.JaccError):
+        jacc.tile_info(24)
+
+
+def test_specialize_rejects_bad_descriptors_on_host(lib):
+    # validation happens before any CUDA call
+    with pytest.raises(jacc.JaccError) as e:
+        jacc.Kernel(6, jacc.F64, 10, 10, 10)
+    assert e.value.status == jacc.ERR_INVALID_ARG
+    with pytest.raises(jacc.JaccError) as e:
+        jacc.Kernel(jacc.STENCIL_5PT, jacc.F64, 10, 10, 4)
+    assert e.value.status == jacc.ERR_INVALID_ARG
+    with pytest.raises(jacc.JaccError) as e:
+        jacc.Kernel(jacc.STENCIL_7PT, jacc.F64, 2, 10, 10)
+    assert e.value.status == jacc.ERR_INVALID_ARG
+    with pytest.raises(jacc.JaccError) as e:
+        jacc.Kernel(jacc.STENCIL_7PT, jacc.F64, 11, 10, 10, tile_id=1)  # 16-byte vectors need even nx
+    assert e.value.status == jacc.ERR_INVALID_ARG
+    with pytest.raises(jacc.JaccError) as e:
+        jacc.Kernel(jacc.STENCIL_27PT, jacc.F32, 10, 10, 10, boundary=jacc.DIRICHLET)
+    assert e.value.status == jacc.ERR_UNSUPPORTED
+
+
+def test_region_analysis_matches_oracle_bit_exactly(lib, orc):
+    from tests.test_oracle_region import five_point_nest, listing5_nest, random_nest
+    cases = [five_point_nest(256), five_point_nest(7), listing5_nest()]
+    rng = random.Random(14340)
+    cases += [random_nest(rng) for _ in range(2000)]
+    # overflow and error cases
+    INT64_MAX = (1 << 63) - 1
+    cases += [([(0, 4, 1)], [dict(array=0, coef=[[1 << 62]], off=[0])], [[4]]),
+              ([(0, 1, 1), (0, 1, 1)], [dict(array=0, coef=[[INT64_MAX, INT64_MAX]], off=[0])], [[4]]),
+              ([(0, 0, 1)], [dict(array=0, coef=[[0], [0], [0]], off=[0, 0, 0])], [[2, 1 << 40, 1 << 40]]),
+              ([(0, 3, 0)], [dict(array=0, coef=[[1]], off=[0])], [[4]]),
+              ([(10, 2, -3)], [dict(array=0, coef=[[1]], off=[0])], [[11]]),
+              ([(0, 9, 1), (5, 4, 1)], [dict(array=0, write=True, coef=[[1, 0]], off=[0])], [[10]])]
+    for loops, refs, arrays in cases:
+        st_o, out_o = orc.region_analyze(loops, refs, arrays)
+        st_j, out_j = jacc.region_analyze(loops, refs, arrays)
+        assert st_o == st_j, (loops, refs, arrays)
+        if st_o in (0, -2):
+            assert out_o == out_j, (loops, refs, arrays)

@@ -1,0 +1,257 @@
+"""GPU parity: every stencil kernel through the C ABI against the CPU oracle.
+
+Sizes span several tiles in every axis with ragged tails; every one of the 24
+tile configurations is exercised.  Tolerances (normwise: max |g - o| / max |o|):
+1e-12 for FP64 fields and residuals, 1e-5 for FP32 fields.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2110_14340_gb300 import inputs, jacc
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 1e-5
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2110_14340_gb300 import build
+    build.build()
+    jacc.lib()
+    yield
+    torch.cuda.synchronize()
+
+
+def run(k, u, nsweeps, graph=True):
+    t = torch.float64 if k.desc.dtype == 64 else torch.float32
+    a = torch.from_numpy(np.ascontiguousarray(u)).to(DEV, t)
+    b = torch.zeros_like(a)
+    res = torch.full((nsweeps,), -1.0, dtype=torch.float64, device=DEV)
+    fb = jacc.sweep(k, a, b, nsweeps, res, graph=graph)
+    torch.cuda.synchronize()
+    return (a if fb == 0 else b).cpu().numpy(), res.cpu().numpy()
+
+
+def nerr(g, o):
+    return float(np.max(np.abs(g.astype(np.float64) - o.astype(np.float64))) / max(np.max(np.abs(o)), 1e-300))
+
+
+# ----------------------------------------------------------------------------- 5-point Jacobi
+
+@pytest.mark.parametrize("tile", range(24))
+def test_jacobi2d_f64_all_tiles(orc, tile):
+    ny, nx = 150, 266  # ragged against every tile in both axes
+    u = inputs.jacobi2d_field(nx, ny, seed=1)
+    k = jacc.Kernel(jacc.STENCIL_5PT, jacc.F64, nx, ny, 1, tile_id=tile)
+    assert k.info()["fixed_point"]
+    g, gr = run(k, u, 7)
+    o, orr = orc.jacobi2d_run(u, 7)
+    assert nerr(g, o) <= TOL64
+    assert np.max(np.abs(gr - orr)) <= TOL64 * np.max(np.abs(o))
+
+
+@pytest.mark.parametrize("tile", [0, 4, 8, 16, 22])
+def test_jacobi2d_f64_odd_width_native_and_fixed(orc, tile):
+    ny, nx = 37, 101
+    u = inputs.jacobi2d_field(nx, ny, seed=7)
+    o, orr = orc.jacobi2d_run(u, 5)
+    for arith in (jacc.ARITH_AUTO, jacc.ARITH_NATIVE):
+        k = jacc.Kernel(jacc.STENCIL_5PT, jacc.F64, nx, ny, 1, tile_id=tile, arith=arith)
+        g, gr = run(k, u, 5)
+        assert nerr(g, o) <= TOL64
+        assert np.max(np.abs(gr - orr)) <= TOL64 * np.max(np.abs(o))
+
+
+@pytest.mark.parametrize("tile", [1, 5, 13, 23])
+def test_jacobi2d_f32(orc, tile):
+    ny, nx = 90, 300
+    u = inputs.jacobi2d_field(nx, ny, seed=11)
+    k = jacc.Kernel(jacc.STENCIL_5PT, jacc.F32, nx, ny, 1, tile_id=tile)
+    g, gr = run(k, u.astype(np.float32), 6)
+    o, orr = orc.jacobi2d_run(u.astype(np.float32).astype(np.float64), 6)
+    assert nerr(g, o) <= TOL32
+    assert np.max(np.abs(gr - orr)) <= TOL32 * np.max(np.abs(o))
+
+
+def test_jacobi2d_affine_fixed_point_bit_exact():
+    ny, nx = 45, 130
+    y, x = np.mgrid[0:ny, 0:nx]
+    u = 3.0 * x - 2.0 * y + 7.0
+    k = jacc.Kernel(jacc.STENCIL_5PT, jacc.F64, nx, ny, 1)
+    g, gr = run(k, u, 9)
+    assert np.array_equal(g, u) and np.all(gr == 0.0)
+
+
+def test_jacobi2d_full_size_256_100_sweeps(orc):
+    # the 256 x 256, 100-sweep configuration, element by element
+    u = inputs.jacobi2d_field(256, 256, seed=1)
+    k = jacc.Kernel(jacc.STENCIL_5PT, jacc.F64, 256, 256, 1)
+    g, gr = run(k, u, 100)
+    o, orr = orc.jacobi2d_run(u, 100)
+    assert nerr(g, o) <= TOL64
+    assert np.max(np.abs(gr - orr)) <= TOL64
+    assert np.all(gr[1:] <= gr[:-1] + 1e-15)
+
+
+# ----------------------------------------------------------------------------- 7-point heat
+
+@pytest.mark.parametrize("tile", range(24))
+def test_heat3d_f64_all_tiles(orc, tile):
+    nz, ny, nx = 37, 21, 134
+    u = inputs.heat3d_field(nx, seed=2, ny=ny, nz=nz)
+    k = jacc.Kernel(jacc.STENCIL_7PT, jacc.F64, nx, ny, nz, coeffs=(0.125,), tile_id=tile)
+    assert k.info()["fixed_point"]
+    g, gr = run(k, u, 5)
+    o, orr = orc.heat3d_run(u, 0.125, 5)
+    assert nerr(g, o) <= TOL64
+    assert np.max(np.abs(gr - orr)) <= TOL64 * np.max(np.abs(o))
+
+
+@pytest.mark.parametrize("r,fixed", [(0.1, True), (1.0 / 16, True), (1.0 / 6, True), (0.2, False), (0.0, True)])
+def test_heat3d_coefficient_paths(orc, r, fixed):
+    nz, ny, nx = 19, 23, 66
+    rng = np.random.default_rng(3)
+    u = rng.uniform(-2.0, 3.0, (nz, ny, nx))
+    k = jacc.Kernel(jacc.STENCIL_7PT, jacc.F64, nx, ny, nz, coeffs=(r,))
+    assert k.info()["fixed_point"] == fixed
+    g, gr = run(k, u, 4)
+    o, orr = orc.heat3d_run(u, r, 4)
+    assert nerr(g, o) <= TOL64
+    assert np.max(np.abs(gr - orr)) <= TOL64 * np.max(np.abs(o))
+
+
+def test_heat3d_native_path_and_nonfinite_input(orc):
+    nz, ny, nx = 12, 14, 40
+    u = inputs.heat3d_field(nx, ny=ny, nz=nz, seed=5)
+    o, orr = orc.heat3d_run(u, 0.125, 3)
+    k = jacc.Kernel(jacc.STENCIL_7PT, jacc.F64, nx, ny, nz, coeffs=(0.125,), arith=jacc.ARITH_NATIVE)
+    g, gr = run(k, u, 3)
+    assert nerr(g, o) <= TOL64 and np.max(np.abs(gr - orr)) <= TOL64
+    # a NaN in the input routes the sweep to the native path: NaN propagates like IEEE FP64
+    u2 = u.copy()
+    u2[5, 6, 7] = np.nan
+    k2 = jacc.Kernel(jacc.STENCIL_7PT, jacc.F64, nx, ny, nz, coeffs=(0.125,))
+    g2, _ = run(k2, u2, 1)
+    o2, _ = orc.heat3d_sweep(u2, 0.125)
+    assert np.array_equal(np.isnan(g2), np.isnan(o2))
+    m = ~np.isnan(o2)
+    assert nerr(g2[m], o2[m]) <= TOL64
+
+
+@pytest.mark.parametrize("tile", [3, 9, 15, 21])
+def test_heat3d_f32(orc, tile):
+    nz, ny, nx = 20, 18, 136
+    u = inputs.heat3d_field(nx, ny=ny, nz=nz, seed=2).astype(np.float32)
+    k = jacc.Kernel(jacc.STENCIL_7PT, jacc.F32, nx, ny, nz, coeffs=(0.125,), tile_id=tile)
+    g, gr = run(k, u, 4)
+    o, orr = orc.heat3d_run(u.astype(np.float64), 0.125, 4)
+    assert nerr(g, o) <= TOL32
+
+
+# ----------------------------------------------------------------------------- 27-point periodic box
+
+W = inputs.box27_weights()
+
+
+@pytest.mark.parametrize("tile", range(24))
+def test_box27_f32_all_tiles(orc, tile):
+    nz, ny, nx = 35, 11, 140
+    u = inputs.box27_field(nx, ny, nz, seed=6)
+    k = jacc.Kernel(jacc.STENCIL_27PT, jacc.F32, nx, ny, nz, coeffs=tuple(float(w) for w in W), tile_id=tile)
+    g, gs = run(k, u, 4)
+    o, osum = orc.box27_run(u, W, 4)
+    assert nerr(g, o) <= TOL32
+    A = float(np.sum(np.abs(o.astype(np.float64))))
+    assert np.max(np.abs(gs - osum)) <= 1e-6 * A
+
+
+@pytest.mark.parametrize("tile", [0, 7, 13, 23])
+def test_box27_f64(orc, tile):
+    nz, ny, nx = 18, 13, 70
+    u = inputs.box27_field(nx, ny, nz, seed=9).astype(np.float64)
+    w64 = W.astype(np.float64)
+    k = jacc.Kernel(jacc.STENCIL_27PT, jacc.F64, nx, ny, nz, coeffs=tuple(w64), tile_id=tile)
+    assert k.info()["fixed_point"]
+    g, gs = run(k, u, 3)
+    o, sums = orc.box27_run_f64(u, w64, 3)
+    assert nerr(g, o) <= TOL64
+    assert np.max(np.abs(gs - np.array(sums))) <= 1e-12 * float(np.sum(np.abs(o)))
+
+
+def test_box27_impulse_response_exact():
+    nz, ny, nx = 6, 7, 8
+    u = np.zeros((nz, ny, nx), dtype=np.float32)
+    u[0, 0, 0] = 1.0
+    k = jacc.Kernel(jacc.STENCIL_27PT, jacc.F32, nx, ny, nz, coeffs=tuple(float(w) for w in W), tile_id=0)
+    g, _ = run(k, u, 1)
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                assert g[dz % nz, dy % ny, dx % nx] == W[(dz != 0) + (dy != 0) + (dx != 0)]
+    assert np.count_nonzero(g) == 27
+
+
+# ----------------------------------------------------------------------------- specialisation and graphs
+
+@pytest.mark.parametrize("stencil,dtype,shape,coeffs", [
+    (5, 64, (1, 70, 134), ()), (7, 64, (21, 22, 70), (0.125,)), (7, 64, (21, 22, 70), (0.1,)),
+    (27, 32, (12, 13, 64), tuple(float(w) for w in W)), (7, 32, (21, 22, 72), (0.125,))])
+def test_jit_variant_matches_generic(stencil, dtype, shape, coeffs):
+    nz, ny, nx = shape
+    rng = np.random.default_rng(1)
+    u = rng.uniform(0, 1, (ny, nx) if stencil == 5 else shape)
+    if dtype == 32:
+        u = u.astype(np.float32)
+    kg = jacc.Kernel(stencil, dtype, nx, ny, nz, coeffs=coeffs)
+    kj = jacc.Kernel(stencil, dtype, nx, ny, nz, coeffs=coeffs, jit=True)
+    assert kj.info()["jit"] and not kg.info()["jit"]
+    g1, r1 = run(kg, u, 3)
+    g2, r2 = run(kj, u, 3)
+    if dtype == 64:
+        assert np.array_equal(g1, g2) and np.array_equal(r1, r2)  # integer arithmetic: bit-identical
+    else:
+        assert nerr(g2, g1) <= TOL32
+
+
+def test_graph_and_eager_sweeps_agree_and_cache():
+    nz, ny, nx = 16, 16, 64
+    u = inputs.heat3d_field(nx, ny=ny, nz=nz, seed=3)
+    k = jacc.Kernel(jacc.STENCIL_7PT, jacc.F64, nx, ny, nz, coeffs=(0.125,))
+    k2 = jacc.Kernel(jacc.STENCIL_7PT, jacc.F64, nx, ny, nz, coeffs=(0.125,))
+    assert k.handle.value == k2.handle.value  # cache hit shares the compiled kernel
+    g1, r1 = run(k, u, 6, graph=True)
+    g2, r2 = run(k, u, 6, graph=False)
+    assert np.array_equal(g1, g2) and np.array_equal(r1, r2)
+    # replay of the cached graph on the same buffers
+    a = torch.from_numpy(u).to(DEV)
+    b = torch.zeros_like(a)
+    res = torch.zeros(6, dtype=torch.float64, device=DEV)
+    for _ in range(3):
+        a.copy_(torch.from_numpy(u))
+        fb = jacc.sweep(k, a, b, 6, res)
+    torch.cuda.synchronize()
+    assert np.array_equal((a if fb == 0 else b).cpu().numpy(), g1)
+
+
+def test_launch_single_sweep_and_errors(orc):
+    nz, ny, nx = 10, 12, 34
+    u = inputs.heat3d_field(nx, ny=ny, nz=nz, seed=4)
+    k = jacc.Kernel(jacc.STENCIL_7PT, jacc.F64, nx, ny, nz, coeffs=(0.125,))
+    a = torch.from_numpy(u).to(DEV)
+    b = torch.empty_like(a)
+    r = torch.zeros(1, dtype=torch.float64, device=DEV)
+    jacc.launch(k, a, b, r)
+    torch.cuda.synchronize()
+    o, orr = orc.heat3d_sweep(u, 0.125)
+    assert nerr(b.cpu().numpy(), o) <= TOL64 and abs(r.item() - orr) <= TOL64
+    with pytest.raises(jacc.JaccError) as e:
+        jacc.launch(k, a, a, r)  # in-place is aliasing
+    assert e.value.status == jacc.ERR_INVALID_ARG
+    with pytest.raises(ValueError):
+        jacc.launch(k, a.float(), b)
+    with pytest.raises(jacc.JaccError):
+        jacc.sweep(k, a, b, 0)

@@ -188,3 +188,23 @@ def test_sums_and_maxabs(orc):
         assert abs(orc.sum_f32(f) - math.fsum(f.astype(np.float64))) <= bound + 1e-300
         b = rng.uniform(-1, 1, n)
         assert orc.maxabs_diff(a, b) == (float(np.max(np.abs(a - b))) if n else 0.0)
+
+
+def test_box27_f64_pins(orc):
+    # FP64 variant: impulse response is the weights exactly; the plane-wave symbol holds to FP64 rounding.
+    w = np.array([6 / 11, 1 / 22, 1 / 88, 1 / 176])
+    nz, ny, nx = 10, 12, 16
+    u = np.zeros((nz, ny, nx))
+    u[1, 2, 3] = 1.0
+    v, _ = orc.box27_run_f64(u, w, 1)
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                assert v[1 + dz, 2 + dy, 3 + dx] == w[(dz != 0) + (dy != 0) + (dx != 0)]
+    assert np.count_nonzero(v) == 27
+    z, y, x = np.mgrid[0:nz, 0:ny, 0:nx]
+    ph = 2 * np.pi * (3 * x / nx + 2 * y / ny + 1 * z / nz)
+    cx, cy, cz = (math.cos(2 * math.pi * k / n) for k, n in ((3, nx), (2, ny), (1, nz)))
+    sym = w[0] + 2 * w[1] * (cx + cy + cz) + 4 * w[2] * (cx * cy + cx * cz + cy * cz) + 8 * w[3] * cx * cy * cz
+    v, sums = orc.box27_run_f64(np.cos(ph), w, 2)
+    assert np.max(np.abs(v - sym ** 2 * np.cos(ph))) <= 1e-14
