@@ -1,0 +1,298 @@
+"""Benchmark: 7-point explicit heat, 512^3 FP64, r = 0.125, 200 sweeps per step.
+
+One step is one pass of the hot path over the workload: region analysis of
+the interior loop nest (host), specialisation (a cache hit after warm-up) and
+one graph launch of 200 ping-pong sweeps, each with its fused max-abs
+residual.  Inputs stay resident in HBM; the two 1 GiB fields exceed L2.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  With torchrun (N > 1) every rank runs an
+independent replica (the path has no exchange step); value = total updates
+of all ranks / max-over-ranks time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 512
+R = 0.125
+SWEEPS = 200
+LUP_PER_SWEEP = (N - 2) ** 3
+
+
+def set_size(n, sweeps):
+    global N, SWEEPS, LUP_PER_SWEEP, WORKLOAD
+    N, SWEEPS, LUP_PER_SWEEP = n, sweeps, (n - 2) ** 3
+    WORKLOAD = f"heat3d 7-point FP64 {n}^3, r=0.125, zero Dirichlet, {sweeps} sweeps per CUDA graph"
+BYTES_PER_LUP = 16  # one FP64 read + one FP64 write per interior point
+METRIC = "stencil GLUP/s"
+WORKLOAD = "heat3d 7-point FP64 512^3, r=0.125, zero Dirichlet, 200 sweeps per CUDA graph"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"bench_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def region_nest():
+    I3 = [[1, 0, 0], [0, 1, 0], [0, 0, 1]]
+    refs = [dict(array=0, coef=I3, off=o) for o in
+            ([-1, 0, 0], [1, 0, 0], [0, -1, 0], [0, 1, 0], [0, 0, -1], [0, 0, 1], [0, 0, 0])]
+    refs.append(dict(array=1, write=True, coef=I3, off=[0, 0, 0]))
+    return [(1, N - 2, 1)] * 3, refs, [[N, N, N], [N, N, N]]
+
+
+def cpu_baseline_oracle(nsweeps=3):
+    """The oracle, as it stands (single thread), on the full 512^3 grid for a few sweeps."""
+    import numpy as np  # noqa: F401
+    import oracle
+    from paper_2110_14340_gb300 import inputs
+    oracle.build()
+    u = inputs.heat3d_field(N, seed=2)
+    t0 = time.perf_counter()
+    oracle.heat3d_run(u, R, nsweeps)
+    dt = time.perf_counter() - t0
+    return {"value": LUP_PER_SWEEP * nsweeps / dt / 1e9, "unit": "GLUP/s", "cores": 1, "kind": "oracle",
+            "sample": f"512^3 grid, {nsweeps} sweeps (of 200), single-threaded plain C, {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2110_14340_gb300 import inputs
+    oracle.build()
+    u = inputs.heat3d_field(N, seed=2)
+    for _ in range(args.warmup):
+        oracle.heat3d_sweep(u, R)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        u, _ = oracle.heat3d_sweep(u, R)
+        times.append(time.perf_counter() - t0)
+    dt = sum(times)
+    value = LUP_PER_SWEEP * args.steps / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GLUP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "step": "1 sweep of the 512^3 grid by the CPU oracle"},
+            "cpu_baseline": {"value": value, "unit": "GLUP/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} single sweeps of the 512^3 grid"},
+            "e2e": {"value": value, "unit": "GLUP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_2110_14340_gb300 import build, inputs, jacc
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    jacc.lib()
+
+    u_host = inputs.heat3d_field(N, seed=2)
+    a = torch.from_numpy(u_host).to(dev)
+    b = torch.empty_like(a)
+    resid = torch.zeros(SWEEPS, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    loops, refs, arrays = region_nest()
+
+    def step(x, y):
+        st, _ = jacc.region_analyze(loops, refs, arrays)
+        assert st == 0
+        k = jacc.Kernel(jacc.STENCIL_7PT, jacc.F64, N, N, N, coeffs=(R,), tile_id=args.tile)
+        fb = jacc.sweep(k, x, y, SWEEPS, resid, graph=True)
+        k.release()
+        return fb
+
+    keep = jacc.Kernel(jacc.STENCIL_7PT, jacc.F64, N, N, N, coeffs=(R,), tile_id=args.tile)  # holds the cache entry
+    info = keep.info()
+    bufs = [a, b]
+    for _ in range(args.warmup):
+        fb = step(bufs[0], bufs[1])
+        if fb == 1:
+            bufs.reverse()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        fb = step(bufs[0], bufs[1])
+        if fb == 1:
+            bufs.reverse()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    total_lup = LUP_PER_SWEEP * SWEEPS * args.steps * ws
+    value = total_lup / (ms * 1e-3) / 1e9
+    ms_step = ms / args.steps
+
+    # Roofline of the dominant kernel (the 7-point sweep): algorithmic bytes
+    # per launch / average launch time.  The step's time also holds one
+    # max-abs pre-pass (1 GiB read), so this is a lower bound on the kernel's rate.
+    peak, peak_kind = peaks()
+    achieved = LUP_PER_SWEEP * BYTES_PER_LUP / (ms_step / SWEEPS * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": args.traffic, "peak_kind": peak_kind,
+            "per_unit": "16 B per interior point per sweep (8 B read + 8 B write), 510^3 points per launch"}
+
+    # End to end through the public API with host buffers: pinned H2D of the
+    # input field, the 200-sweep graph, D2H of the result field and residuals.
+    e2e = None
+    if not args.no_e2e:
+        e2e = measure_e2e(step, a, b, resid, u_host, args, ws)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GLUP/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "int64", "storage_dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "grid": [N, N, N], "sweeps_per_step": SWEEPS, "r": R,
+                           "tile": info["tile_id"], "fixed_point": info["fixed_point"],
+                           "l2": "inputs larger than L2 (two 1 GiB fields)",
+                           "parallelism": "replicas" if ws > 1 else "single GPU"},
+                "roofline": roof, "e2e": e2e, "gpu_launches": (SWEEPS + 1) * args.steps,
+                "clocks": clk}
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline_oracle()
+        print(json.dumps(line), flush=True)
+    keep.release()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def measure_e2e(step, a, b, resid, u_host, args, ws):
+    import numpy as np
+    import torch
+    pin_in = torch.from_numpy(u_host).pin_memory()
+    pin_out = torch.empty_like(pin_in).pin_memory()
+    pin_res = torch.empty(SWEEPS, dtype=torch.float64).pin_memory()
+    e_steps = max(1, min(args.steps, 3))
+    for it in range(e_steps + 1):
+        if it == 1:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+        a.copy_(pin_in, non_blocking=True)
+        fb = step(a, b)
+        pin_out.copy_(a if fb == 0 else b, non_blocking=True)
+        pin_res.copy_(resid, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e_steps
+    e2e = {"value": LUP_PER_SWEEP * SWEEPS * ws / e2e_s / 1e9, "unit": "GLUP/s",
+           "h2d_bytes_per_step": int(pin_in.numel() * 8), "d2h_bytes_per_step": int(pin_out.numel() * 8 + SWEEPS * 8),
+           "ms_per_step": 1e3 * e2e_s}
+
+    assert np.isfinite(pin_res.numpy()).all()
+    return e2e
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--tile", type=int, default=-1)
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="ncu dram bytes per launch of the sweep kernel, if captured for this build")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--n", type=int, default=512, help="grid side (profiling of small cases)")
+    ap.add_argument("--sweeps", type=int, default=200)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    set_size(args.n, args.sweeps)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()
