@@ -215,6 +215,24 @@ jacc_status jacc_launch(jacc_kernel k, const void* u_in, void* u_out, double* re
 jacc_status jacc_sweep(jacc_kernel k, void* u0, void* u1, int32_t nsweeps, double* resid_dev, uint32_t flags,
                        uintptr_t stream, int32_t* final_buf);
 
+/* jacc_launch_static: jacc_launch without any device allocation.
+ * The paper has no counterpart; this exists for callers that cannot allocate
+ * device memory when they launch (a memory pool that must own every device
+ * byte, a latency-critical path that must not hit cudaMalloc's implicit
+ * synchronisation, code that must not fail on allocation).  Arguments,
+ * results and errors are those of jacc_launch.  Instead of the handle's
+ * cudaMalloc'd word, the FP64 fixed-point scale word lives in a file-scope
+ * static device array of 256 bytes (32 words; a launch uses one, whatever the
+ * grid size), which every GPU that loads the library holds until exit.  The
+ * first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the array and the call
+ * clears the word it uses; calls that overlap on the GPU (other streams, or
+ * other threads) race on it.  No cudaMalloc, cudaFree or allocating library
+ * routine is called.  The handle itself comes from jacc_specialize, which
+ * may allocate: create it during set-up. */
+jacc_status jacc_launch_static(jacc_kernel k, const void* u_in, void* u_out, double* resid_dev, uintptr_t stream);
+
 /* Release every cached kernel, graph and library allocation.  Handles become
  * invalid.  Safe to call more than once. */
 jacc_status jacc_shutdown(void);

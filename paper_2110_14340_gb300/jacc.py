@@ -81,6 +81,7 @@ SIGNATURES = {
     "jacc_release": ([P], C.c_int32),
     "jacc_tile_info": ([C.c_int32, P], C.c_int32),
     "jacc_launch": ([P, P, P, P, C.c_size_t], C.c_int32),
+    "jacc_launch_static": ([P, P, P, P, C.c_size_t], C.c_int32),
     "jacc_sweep": ([P, P, P, C.c_int32, P, C.c_uint32, C.c_size_t, P], C.c_int32),
     "jacc_shutdown": ([], C.c_int32),
 }
