@@ -215,6 +215,62 @@ jacc_status jacc_launch(jacc_kernel k, const void* u_in, void* u_out, double* re
 jacc_status jacc_sweep(jacc_kernel k, void* u0, void* u1, int32_t nsweeps, double* resid_dev, uint32_t flags,
                        uintptr_t stream, int32_t* final_buf);
 
+/* ---------------------------------------------------------- batched sweeps
+ * Many independent 2D 5-point Jacobi grids (FP64, Dirichlet boundary held)
+ * swept together in one persistent, cooperative launch.  No counterpart in
+ * the paper, which overlaps independent kernels on OpenACC queues (§6.1).
+ * Every sweep of every grid runs inside that launch: work is a sequence of
+ * tickets (sweep, band of rows of one grid) in sweep-major order; a band
+ * waits, bounded by a time limit, until the previous sweep of its own grid
+ * has finished, so grids advance independently.  Arithmetic is the 5-point
+ * stencil's (exact fixed point for finite inputs, see jacc_specialize).
+ *
+ * Schedule (jacc_batch_config): target points per band (band height =
+ * max(1, item_points / nx) rows), persistent CTAs per SM (0 = as many as
+ * fit), and band order (0: grids largest first, bands grid by grid;
+ * 1: round-robin over grids).  timeout_ms bounds every device wait (0 =
+ * 2000 ms).  test_stall_ticket is a fault-injection hook for tests: that
+ * ticket never reports completion, so the waits behind it time out; -1 = off.
+ * jacc_batch_tune times every schedule candidate (band size in {4K, 8K, 16K,
+ * 32K, 64K} points x CTAs per SM in {1, 2, max} x both orders) for
+ * probe_sweeps sweeps on the batch's own buffers (their contents change),
+ * keeps the fastest, and returns it and its time.  */
+typedef struct {
+  int64_t nx, ny; /* extents, each in [3, 2^31]                                   */
+  void* u0;       /* device FP64 field [ny][nx], 16-byte aligned: sweep 0 input    */
+  void* u1;       /* device FP64 field, same shape, must not overlap u0            */
+} jacc_grid;
+
+typedef struct {
+  int32_t item_points;       /* target points per band; 0 = 16384                */
+  int32_t ctas_per_sm;       /* persistent CTAs per SM; 0 = as many as fit        */
+  int32_t order;             /* 0 largest grid first, 1 round-robin               */
+  int32_t timeout_ms;        /* bound on each device wait; 0 = 2000               */
+  int64_t test_stall_ticket; /* fault injection for tests; -1 = off               */
+} jacc_batch_config;
+
+typedef struct jacc_batch_s* jacc_batch;
+
+/* Copies the grid descriptors and uploads the device tables (synchronous).
+ * cfg may be NULL for the defaults.  The fields stay caller-owned. */
+jacc_status jacc_batch_create(int32_t ngrids, const jacc_grid* grids, const jacc_batch_config* cfg, jacc_batch* out);
+/* Replace the schedule (synchronous; drops cached graphs). */
+jacc_status jacc_batch_configure(jacc_batch b, const jacc_batch_config* cfg);
+jacc_status jacc_batch_get_config(jacc_batch b, jacc_batch_config* out);
+/* nsweeps ping-pong sweeps of every grid.  resid_dev (nullable, device,
+ * ngrids * nsweeps doubles, row g = grid g) receives each grid's per-sweep
+ * max |v - u| over its interior.  flags: JACC_SWEEP_GRAPH captures the
+ * sequence once per (nsweeps, resid_dev) and replays it.  *final_buf = 0 if
+ * every grid's result is in u0, 1 if in u1.  Asynchronous on `stream`. */
+jacc_status jacc_batch_sweep(jacc_batch b, int32_t nsweeps, double* resid_dev, uint32_t flags, uintptr_t stream,
+                             int32_t* final_buf);
+/* Synchronises `stream` and reports the last run: JACC_OK, or
+ * JACC_ERR_TIMEOUT if a device wait gave up (the fields are then partial). */
+jacc_status jacc_batch_status(jacc_batch b, uintptr_t stream);
+jacc_status jacc_batch_tune(jacc_batch b, int32_t probe_sweeps, uintptr_t stream, jacc_batch_config* best,
+                            double* best_ms);
+jacc_status jacc_batch_release(jacc_batch b);
+
 /* jacc_launch_static: jacc_launch without any device allocation.
  * The paper has no counterpart; this exists for callers that cannot allocate
  * device memory when they launch (a memory pool that must own every device

@@ -121,10 +121,20 @@ template <> struct VecT<double, 2> { typedef double2 type; };
 template <> struct VecT<float, 1> { typedef float type; };
 template <> struct VecT<float, 4> { typedef float4 type; };
 
-template <class T, int V> JD void ldv(const T* __restrict__ p, T (&r)[V]) {
-  if constexpr (V == 1) { r[0] = __ldg(p); }
-  else if constexpr (V == 2) { double2 t = __ldg(reinterpret_cast<const double2*>(p)); r[0] = t.x; r[1] = t.y; }
-  else { float4 t = __ldg(reinterpret_cast<const float4*>(p)); r[0] = t.x; r[1] = t.y; r[2] = t.z; r[3] = t.w; }
+// CG = true loads through L2 only (ld.global.cg): required where the same
+// kernel launch writes the array (the persistent batched kernel), since the
+// non-coherent and L1 paths may return stale lines there.
+template <bool CG, class T> JD T ld1(const T* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return __ldg(p);
+}
+template <class T, int V, bool CG = false> JD void ldv(const T* __restrict__ p, T (&r)[V]) {
+  if constexpr (V == 1) { r[0] = ld1<CG>(p); }
+  else if constexpr (V == 2) {
+    double2 t = ld1<CG>(reinterpret_cast<const double2*>(p)); r[0] = t.x; r[1] = t.y;
+  } else {
+    float4 t = ld1<CG>(reinterpret_cast<const float4*>(p)); r[0] = t.x; r[1] = t.y; r[2] = t.z; r[3] = t.w;
+  }
 }
 template <class T, int V> JD void stv(T* __restrict__ p, const T (&r)[V]) {
   if constexpr (V == 1) { p[0] = r[0]; }
@@ -208,32 +218,27 @@ JD void two_sum_acc(float& hi, float& lo, float x) {
 
 // ====================================================================== 5-point Jacobi (2D)
 //
-// CTA = BX x BY threads.  Thread (tx, ty) owns columns x0 .. x0+V-1 and marches
-// down rows [ys, ys+ZC), keeping rows y-1, y, y+1 in registers; the x
+// One warp owns 32*V consecutive columns starting at its lane-0 column and
+// marches rows [ys, ye), keeping rows y-1, y, y+1 in registers; the x
 // neighbours come from warp shuffles (lanes 0 and 31 read the edge columns
-// from global memory).  Rows y+2 are prefetched one iteration ahead.
+// from memory).  Row y+3 is prefetched two iterations ahead.  All 32 lanes
+// must call it with the same ys, ye (full-mask shuffles).
 
-template <class T, int BX, int BY, int V, int ZC, int MODE, class P>
-JD void jacobi2d_body(const T* __restrict__ u, T* __restrict__ v, const P& p, int F,
-                        typename RT<T, MODE>::type& rmax) {
+template <class T, int V, int MODE, bool CG>
+JD void jacobi_march(const T* __restrict__ u, T* __restrict__ v, i64 nx, i64 ny, i64 x0, i64 ys, i64 ye, int F,
+                     typename RT<T, MODE>::type& rmax) {
   typedef typename WT<T, MODE>::type W;
-  const i64 nx = p.nx, ny = p.ny;
   const int lane = threadIdx.x & 31;
-  const i64 x0 = (i64)blockIdx.x * (BX * V) + (i64)threadIdx.x * V;
-  const i64 ys = ((i64)blockIdx.y * BY + threadIdx.y) * ZC;
-  const i64 ye = (ys + ZC < ny) ? ys + ZC : ny;
   const bool xin = x0 < nx;
-  if (ys >= ny) return;  // whole warp (a warp lies within one thread row)
-
   T rup[V], rcur[V], rdn[V], rnx[V];
   W up[V], cur[V], dn[V];
 #pragma unroll
   for (int e = 0; e < V; ++e) { rup[e] = rcur[e] = rdn[e] = rnx[e] = T(0); }
   if (xin) {
-    if (ys >= 1) ldv<T, V>(u + (ys - 1) * nx + x0, rup);
-    ldv<T, V>(u + ys * nx + x0, rcur);
-    if (ys + 1 < ny) ldv<T, V>(u + (ys + 1) * nx + x0, rdn);
-    if (ys + 2 < ny) ldv<T, V>(u + (ys + 2) * nx + x0, rnx);
+    if (ys >= 1) ldv<T, V, CG>(u + (ys - 1) * nx + x0, rup);
+    ldv<T, V, CG>(u + ys * nx + x0, rcur);
+    if (ys + 1 < ny) ldv<T, V, CG>(u + (ys + 1) * nx + x0, rdn);
+    if (ys + 2 < ny) ldv<T, V, CG>(u + (ys + 2) * nx + x0, rnx);
   }
 #pragma unroll
   for (int e = 0; e < V; ++e) {
@@ -245,13 +250,13 @@ JD void jacobi2d_body(const T* __restrict__ u, T* __restrict__ v, const P& p, in
     // x neighbours of the row
     W left = __shfl_up_sync(0xffffffffu, cur[V - 1], 1);
     W right = __shfl_down_sync(0xffffffffu, cur[0], 1);
-    if (lane == 0 && xin && x0 >= 1) left = cvt_in<T, MODE>(__ldg(u + y * nx + x0 - 1), F);
-    if (lane == 31 && xin && x0 + V < nx) right = cvt_in<T, MODE>(__ldg(u + y * nx + x0 + V), F);
+    if (lane == 0 && xin && x0 >= 1) left = cvt_in<T, MODE>(ld1<CG>(u + y * nx + x0 - 1), F);
+    if (lane == 31 && xin && x0 + V < nx) right = cvt_in<T, MODE>(ld1<CG>(u + y * nx + x0 + V), F);
     // prefetch row y+3
     T rnn[V];
 #pragma unroll
     for (int e = 0; e < V; ++e) rnn[e] = T(0);
-    if (xin && y + 3 < ny) ldv<T, V>(u + (y + 3) * nx + x0, rnn);
+    if (xin && y + 3 < ny) ldv<T, V, CG>(u + (y + 3) * nx + x0, rnn);
 
     const bool yint = (y >= 1) && (y <= ny - 2);
     T out[V];
@@ -287,6 +292,18 @@ JD void jacobi2d_body(const T* __restrict__ u, T* __restrict__ v, const P& p, in
       rnx[e] = rnn[e];
     }
   }
+}
+
+// CTA = BX x BY threads; thread row ty marches rows [ys, ys + ZC).
+template <class T, int BX, int BY, int V, int ZC, int MODE, class P>
+JD void jacobi2d_body(const T* __restrict__ u, T* __restrict__ v, const P& p, int F,
+                      typename RT<T, MODE>::type& rmax) {
+  const i64 nx = p.nx, ny = p.ny;
+  const i64 x0 = (i64)blockIdx.x * (BX * V) + (i64)threadIdx.x * V;
+  const i64 ys = ((i64)blockIdx.y * BY + threadIdx.y) * ZC;
+  const i64 ye = (ys + ZC < ny) ? ys + ZC : ny;
+  if (ys >= ny) return;  // whole warp (a warp lies within one thread row)
+  jacobi_march<T, V, MODE, false>(u, v, nx, ny, x0, ys, ye, F, rmax);
 }
 
 // ====================================================================== 3D z-marching tiles

@@ -66,6 +66,15 @@ class KernelInfo(C.Structure):
                 ("block", C.c_int32 * 3), ("grid", C.c_int32 * 3), ("compile_ms", C.c_double)]
 
 
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int64), ("ny", C.c_int64), ("u0", C.c_void_p), ("u1", C.c_void_p)]
+
+
+class BatchConfig(C.Structure):
+    _fields_ = [("item_points", C.c_int32), ("ctas_per_sm", C.c_int32), ("order", C.c_int32),
+                ("timeout_ms", C.c_int32), ("test_stall_ticket", C.c_int64)]
+
+
 class Tile(C.Structure):
     _fields_ = [("bx", C.c_int32), ("by", C.c_int32), ("vec16", C.c_int32), ("zc", C.c_int32)]
 
@@ -84,6 +93,13 @@ SIGNATURES = {
     "jacc_launch_static": ([P, P, P, P, C.c_size_t], C.c_int32),
     "jacc_sweep": ([P, P, P, C.c_int32, P, C.c_uint32, C.c_size_t, P], C.c_int32),
     "jacc_shutdown": ([], C.c_int32),
+    "jacc_batch_create": ([C.c_int32, P, P, P], C.c_int32),
+    "jacc_batch_configure": ([P, P], C.c_int32),
+    "jacc_batch_get_config": ([P, P], C.c_int32),
+    "jacc_batch_sweep": ([P, C.c_int32, P, C.c_uint32, C.c_size_t, P], C.c_int32),
+    "jacc_batch_status": ([P, C.c_size_t], C.c_int32),
+    "jacc_batch_tune": ([P, C.c_int32, C.c_size_t, P, P], C.c_int32),
+    "jacc_batch_release": ([P], C.c_int32),
 }
 
 _lib = None
@@ -248,3 +264,81 @@ def sweep(k, u0, u1, nsweeps, resid=None, graph=True, stream=None):
 def shutdown():
     if _lib is not None:
         _check(_lib.jacc_shutdown())
+
+
+# ----------------------------------------------------------------------------- batched sweeps
+
+def _cfg_dict(c):
+    return dict(item_points=c.item_points, ctas_per_sm=c.ctas_per_sm, order=c.order, timeout_ms=c.timeout_ms,
+                test_stall_ticket=c.test_stall_ticket)
+
+
+def _cfg_struct(item_points=0, ctas_per_sm=0, order=0, timeout_ms=0, test_stall_ticket=-1):
+    c = BatchConfig()
+    c.item_points, c.ctas_per_sm, c.order = item_points, ctas_per_sm, order
+    c.timeout_ms, c.test_stall_ticket = timeout_ms, test_stall_ticket
+    return c
+
+
+class Batch:
+    """Many 2D 5-point FP64 grids swept in one persistent launch.
+
+    fields: list of (u0, u1) CUDA float64 tensor pairs of shape (ny, nx)."""
+
+    def __init__(self, fields, **cfg):
+        import torch
+        n = len(fields)
+        G = (Grid * n)()
+        for g, (a, b) in enumerate(fields):
+            for t in (a, b):
+                if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or \
+                        not t.is_contiguous() or t.dim() != 2:
+                    raise ValueError("batch fields must be contiguous 2D CUDA float64 tensors")
+            if a.shape != b.shape:
+                raise ValueError("u0 and u1 of a grid must have the same shape")
+            G[g].ny, G[g].nx = a.shape
+            G[g].u0, G[g].u1 = a.data_ptr(), b.data_ptr()
+        self.n = n
+        self.fields = list(fields)
+        h = C.c_void_p()
+        c = _cfg_struct(**cfg) if cfg else None
+        _check(lib().jacc_batch_create(n, C.cast(G, P), C.byref(c) if c is not None else None, C.byref(h)))
+        self.handle = h
+
+    def configure(self, **cfg):
+        _check(lib().jacc_batch_configure(self.handle, C.byref(_cfg_struct(**cfg))))
+
+    def config(self):
+        c = BatchConfig()
+        _check(lib().jacc_batch_get_config(self.handle, C.byref(c)))
+        return _cfg_dict(c)
+
+    def sweep(self, nsweeps, resid=None, graph=True, stream=None):
+        if resid is not None and resid.numel() < self.n * nsweeps:
+            raise ValueError("resid needs ngrids * nsweeps elements")
+        fb = C.c_int32(-1)
+        _check(lib().jacc_batch_sweep(self.handle, nsweeps, _resid(resid), SWEEP_GRAPH if graph else 0,
+                                      _stream(stream), C.byref(fb)))
+        return fb.value
+
+    def status(self, stream=None):
+        """JACC_OK or the status of the last run (raises JaccError on a timeout)."""
+        _check(lib().jacc_batch_status(self.handle, _stream(stream)))
+
+    def tune(self, probe_sweeps=20, stream=None):
+        c = BatchConfig()
+        ms = C.c_double()
+        _check(lib().jacc_batch_tune(self.handle, probe_sweeps, _stream(stream), C.byref(c), C.byref(ms)))
+        return _cfg_dict(c), ms.value
+
+    def release(self):
+        if self.handle:
+            _check(lib().jacc_batch_release(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            if self.handle and _lib is not None:
+                _lib.jacc_batch_release(self.handle)
+        except Exception:
+            pass
