@@ -102,6 +102,21 @@ def dist_env():
     return ws, rank, local
 
 
+def aggregate(ms_local, units_local, device=None):
+    """Whole-job rate over ranks: every rank runs its own replica; the job's
+    time is the slowest rank's and its work the sum over ranks.  Returns
+    (max ms, total units).  Single process: the inputs unchanged."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms_local, units_local
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def region_nest():
     I3 = [[1, 0, 0], [0, 1, 0], [0, 0, 1]]
     refs = [dict(array=0, coef=I3, off=o) for o in
@@ -176,12 +191,13 @@ def run_gpu(args):
     def step(x, y):
         st, _ = jacc.region_analyze(loops, refs, arrays)
         assert st == 0
-        k = jacc.Kernel(jacc.STENCIL_7PT, jacc.F64, N, N, N, coeffs=(R,), tile_id=args.tile)
+        k = jacc.Kernel(jacc.STENCIL_7PT, jacc.F64, N, N, N, coeffs=(R,), tile_id=args.tile, jit=args.jit)
         fb = jacc.sweep(k, x, y, SWEEPS, resid, graph=True)
         k.release()
         return fb
 
-    keep = jacc.Kernel(jacc.STENCIL_7PT, jacc.F64, N, N, N, coeffs=(R,), tile_id=args.tile)  # holds the cache entry
+    keep = jacc.Kernel(jacc.STENCIL_7PT, jacc.F64, N, N, N, coeffs=(R,), tile_id=args.tile,
+                       jit=args.jit)  # holds the cache entry
     info = keep.info()
     bufs = [a, b]
     for _ in range(args.warmup):
@@ -206,11 +222,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    total_lup = LUP_PER_SWEEP * SWEEPS * args.steps * ws
+    ms, total_lup = aggregate(ms, LUP_PER_SWEEP * SWEEPS * args.steps, device=dev)
     value = total_lup / (ms * 1e-3) / 1e9
     ms_step = ms / args.steps
 
@@ -233,7 +245,7 @@ def run_gpu(args):
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "int64", "storage_dtype": "f64", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "grid": [N, N, N], "sweeps_per_step": SWEEPS, "r": R,
-                           "tile": info["tile_id"], "fixed_point": info["fixed_point"],
+                           "tile": info["tile_id"], "fixed_point": info["fixed_point"], "jit": info["jit"],
                            "l2": "inputs larger than L2 (two 1 GiB fields)",
                            "parallelism": "replicas" if ws > 1 else "single GPU"},
                 "roofline": roof, "e2e": e2e, "gpu_launches": (SWEEPS + 1) * args.steps,
@@ -278,6 +290,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tile", type=int, default=-1)
+    ap.add_argument("--jit", action="store_true", help="use the NVRTC variant with constants folded")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the sweep kernel, if captured for this build")
     ap.add_argument("--no-cpu-baseline", action="store_true")

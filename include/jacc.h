@@ -210,10 +210,90 @@ jacc_status jacc_launch(jacc_kernel k, const void* u_in, void* u_out, double* re
  * by (kernel, u0, u1, nsweeps, resid_dev) and replayed on later calls; the
  * graph is dropped by jacc_release.  Without it the launches are issued one
  * by one.  *final_buf (host) is set to 0 if the last sweep wrote u0, 1 if u1.
- * Asynchronous on `stream`. */
+ * FP64 kernels on the fixed-point path keep the field in 64-bit fixed point
+ * between the sweeps of one call (same 8 bytes per value, in u0/u1): the
+ * first sweep reads FP64, the last writes FP64, each intermediate sweep rounds
+ * once to the fixed-point grid (2^-F with F >= 57 - e(max|u0|), finer than an
+ * FP64 ulp of max|u0|).  After the call the result buffer holds FP64; the
+ * interior of the other buffer holds that internal representation (its
+ * Dirichlet boundary stays FP64).  Asynchronous on `stream`. */
 #define JACC_SWEEP_GRAPH 1u
 jacc_status jacc_sweep(jacc_kernel k, void* u0, void* u1, int32_t nsweeps, double* resid_dev, uint32_t flags,
                        uintptr_t stream, int32_t* final_buf);
+
+/* ---------------------------------------------------------- autotuner
+ * Exhaustive search over the JACC_NUM_TILES tile configurations for one
+ * descriptor (the paper names auto-tuning as future work, §8, and cites
+ * OptACC's grid search over OpenACC parallelism, §7).  Each valid tile is
+ * specialised and runs a graph-captured sequence of `sweeps_per_rep` sweeps
+ * on the caller's fields u0/u1 (their contents change) once to warm up and
+ * `reps` more times, timed with CUDA events on `stream`; out->ms[t] is the
+ * median time per sweep (infinity and valid[t] = 0 for tiles that do not fit
+ * the shape).  The fastest tile is remembered for the shape, so that
+ * jacc_specialize with tile_id = -1 uses it.  Synchronises `stream`. */
+typedef struct {
+  double ms[JACC_NUM_TILES];    /* median milliseconds per sweep              */
+  int32_t valid[JACC_NUM_TILES];
+  int32_t best_tile;
+  int32_t reserved;
+  double best_ms;
+} jacc_tune_result;
+
+jacc_status jacc_autotune(const jacc_kernel_desc* desc, void* u0, void* u1, int32_t sweeps_per_rep, int32_t reps,
+                          uintptr_t stream, jacc_tune_result* out);
+/* Forget every remembered autotuner pick. */
+jacc_status jacc_autotune_forget(void);
+
+/* ---------------------------------------------------------- learned cost model
+ * An MLP 4 -> 64 -> 64 -> 64 -> 1 (ReLU, FP32, 8705 parameters, layout
+ * W1[64][4] b1[64] W2[64][64] b2[64] W3[64][64] b3[64] W4[64] b4) that maps
+ * the features of (stencil, side, dtype, tile) to the natural log of the sweep
+ * time in microseconds.  No counterpart in the paper.  Features
+ * (jacc_costmodel_features): [points / 27, log2(side) / 10, dtype bits / 64,
+ * tile / 23], side = the grid side (square root of the area for 2D, cube
+ * root of the volume for 3D).
+ *
+ * create      : parameters from `init_params` (host, 8705 floats) or, if
+ *               NULL, Kaiming-uniform from `seed`; Adam state zeroed.
+ * loss_grad   : mean squared error over n samples (x_dev [n][4], y_dev [n],
+ *               device FP32) into *loss_dev and its gradient into grad_dev
+ *               (8705 floats); no update.
+ * train       : `epochs` full-batch Adam steps (beta1 0.9, beta2 0.999,
+ *               eps 1e-8, bias-corrected) with learning rate lr, run as CUDA
+ *               graphs on `stream`; *loss_dev (nullable) = loss before the
+ *               last step.
+ * predict     : y_dev[i] = network(x_dev[i]).
+ * pick        : nq queries of JACC_NUM_TILES feature rows each (feats_dev
+ *               [nq][24][4], valid_dev [nq][24]); pred_dev [nq][24] receives
+ *               the predictions, pick_dev[q] the valid argmin (ties to the
+ *               lowest tile, -1 if none) and gap_dev[q] the second-best
+ *               minus the best prediction.
+ * set_range   : the side range the model was trained on and the decision
+ *               margin (in log-microseconds).
+ * choose      : the model's tile for `desc`; falls back to jacc_autotune on
+ *               u0/u1 (needed then) when the side lies outside the range or
+ *               the top-2 gap is below the margin.  *used_fallback tells
+ *               which.  The chosen tile is remembered for the shape.
+ * save / load : parameters and range in a small binary file ("JACCMLP1"). */
+typedef struct jacc_costmodel_s* jacc_costmodel;
+
+jacc_status jacc_costmodel_features(int32_t stencil, double side, int32_t dtype, int32_t tile, float* out4);
+jacc_status jacc_costmodel_create(const float* init_params, uint64_t seed, jacc_costmodel* out);
+jacc_status jacc_costmodel_set_params(jacc_costmodel m, const float* host_params);
+jacc_status jacc_costmodel_get_params(jacc_costmodel m, float* host_params);
+jacc_status jacc_costmodel_loss_grad(jacc_costmodel m, const float* x_dev, const float* y_dev, int32_t n, float* grad_dev,
+                                     float* loss_dev, uintptr_t stream);
+jacc_status jacc_costmodel_train(jacc_costmodel m, const float* x_dev, const float* y_dev, int32_t n, int32_t epochs,
+                                 float lr, uintptr_t stream, float* loss_dev);
+jacc_status jacc_costmodel_predict(jacc_costmodel m, const float* x_dev, int32_t n, float* y_dev, uintptr_t stream);
+jacc_status jacc_costmodel_pick(jacc_costmodel m, const float* feats_dev, const int32_t* valid_dev, int32_t nq,
+                                float* pred_dev, int32_t* pick_dev, float* gap_dev, uintptr_t stream);
+jacc_status jacc_costmodel_set_range(jacc_costmodel m, double side_lo, double side_hi, double margin);
+jacc_status jacc_costmodel_choose(jacc_costmodel m, const jacc_kernel_desc* desc, void* u0, void* u1, uintptr_t stream,
+                                  int32_t* tile, int32_t* used_fallback);
+jacc_status jacc_costmodel_save(jacc_costmodel m, const char* path);
+jacc_status jacc_costmodel_load(jacc_costmodel m, const char* path);
+jacc_status jacc_costmodel_release(jacc_costmodel m);
 
 /* ---------------------------------------------------------- batched sweeps
  * Many independent 2D 5-point Jacobi grids (FP64, Dirichlet boundary held)

@@ -18,7 +18,7 @@ LIB = os.path.join(BUILD, "libjacc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 
-KERNEL_HEADERS = [os.path.join(KDIR, f) for f in ("jacc_device.cuh", "jacc_params.h", "tiles.h", "batched.h")]
+KERNEL_HEADERS = [os.path.join(KDIR, f) for f in ("jacc_device.cuh", "jacc_params.h", "tiles.h", "batched.h", "mlp.h")]
 HOST_HEADERS = [os.path.join(HDIR, "jacc_internal.h"), os.path.join(ROOT, "include", "jacc.h")]
 
 
@@ -63,7 +63,7 @@ def _jobs():
             jobs.append((obj, KERNEL_HEADERS + [os.path.join(KDIR, "inst.cu")],
                          [NVCC] + cu_flags + [f"-DJACC_INST_STENCIL={st}", f"-DJACC_INST_DTYPE={dt}", "-c",
                                               os.path.join(KDIR, "inst.cu"), "-o", obj]))
-    for name in ("aux.cu", "static_scratch.cu", "batched.cu"):
+    for name in ("aux.cu", "static_scratch.cu", "batched.cu", "mlp.cu"):
         obj = os.path.join(BUILD, name.replace(".cu", ".o"))
         jobs.append((obj, KERNEL_HEADERS + HOST_HEADERS + [os.path.join(KDIR, name)],
                      [NVCC] + cu_flags + ["-c", os.path.join(KDIR, name), "-o", obj]))

@@ -1,0 +1,327 @@
+// costmodel.cpp - the learned launch-configuration cost model (host side).
+//
+// No counterpart in the paper, which names auto-tuning as future work (§8).
+// The model maps 4 features of (stencil, grid side, dtype, tile) to the
+// natural log of the sweep time in microseconds.  It is trained on the GPU by
+// the kernels of mlp.cu (full-batch Adam, mean squared error) on timings the
+// exhaustive autotuner produced, and it picks a tile by the argmin of its
+// predictions.  It defers to the exhaustive autotuner when the shape lies
+// outside the side range it was trained on, or when its two best
+// predictions are closer than a margin.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../kernels/mlp.h"
+#include "jacc_internal.h"
+
+namespace jacc {
+
+struct CostModel {
+  float* d_p = nullptr;
+  float* d_m = nullptr;
+  float* d_v = nullptr;
+  unsigned* d_step = nullptr;
+  float* d_partial = nullptr;
+  float* d_losspart = nullptr;
+  int cap_parts = 0;
+  // pick buffers
+  float* d_feat = nullptr;
+  float* d_pred = nullptr;
+  int* d_valid = nullptr;
+  int* d_pick = nullptr;
+  float* d_gap = nullptr;
+  double side_lo = 0.0, side_hi = 1e300, margin = 0.0;
+};
+
+static bool g_mlp_ready = false;
+
+static jacc_status ensure_setup() {
+  if (g_mlp_ready) return ok();
+  jacc_status st = cuda_check(mlp_setup(), "cudaFuncSetAttribute(MLP shared memory)");
+  if (!st) g_mlp_ready = true;
+  return st;
+}
+
+static jacc_status ensure_parts(CostModel& m, int n) {
+  const int np = mlp_nparts(n);
+  if (np <= m.cap_parts) return ok();
+  if (m.d_partial) cudaFree(m.d_partial);
+  if (m.d_losspart) cudaFree(m.d_losspart);
+  m.d_partial = nullptr;
+  m.d_losspart = nullptr;
+  m.cap_parts = 0;
+  jacc_status st =
+      cuda_check(cudaMalloc(reinterpret_cast<void**>(&m.d_partial), sizeof(float) * JACC_MLP_NPARAM * (size_t)np),
+                 "cudaMalloc(gradient partials)");
+  if (!st) st = cuda_check(cudaMalloc(reinterpret_cast<void**>(&m.d_losspart), sizeof(float) * (size_t)np), "cudaMalloc");
+  if (!st) m.cap_parts = np;
+  return st;
+}
+
+// SplitMix64 (Steele, Lea and Flood, OOPSLA 2014) on a counter: the same
+// published generator the test-suite's inputs use, implemented here on its own.
+static uint64_t mix64(uint64_t z) {
+  z ^= z >> 30;
+  z *= 0xBF58476D1CE4E5B9ull;
+  z ^= z >> 27;
+  z *= 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Kaiming-uniform initialisation for ReLU layers (He et al., ICCV 2015):
+// W ~ U(-sqrt(6 / fan_in), +sqrt(6 / fan_in)), biases 0.
+static void kaiming_init(uint64_t seed, float* p) {
+  const uint64_t key = mix64(mix64(seed));
+  const uint64_t G = 0x9E3779B97F4A7C15ull;
+  const int fan[4] = {4, 64, 64, 64};
+  const int off[4] = {0, 320, 4480, 8640};
+  const int cnt[4] = {256, 4096, 4096, 64};
+  std::memset(p, 0, sizeof(float) * JACC_MLP_NPARAM);
+  uint64_t i = 0;
+  for (int l = 0; l < 4; ++l) {
+    const double b = std::sqrt(6.0 / fan[l]);
+    for (int j = 0; j < cnt[l]; ++j) {
+      const uint64_t bits = mix64(key + (++i) * G);
+      const double u = static_cast<double>(bits >> 11) * 0x1p-53;
+      p[off[l] + j] = static_cast<float>((2.0 * u - 1.0) * b);
+    }
+  }
+}
+
+}  // namespace jacc
+
+using namespace jacc;
+
+extern "C" jacc_status jacc_costmodel_features(int32_t stencil, double side, int32_t dtype, int32_t tile, float* out4) {
+  if (!out4 || !(side > 0.0) || tile < 0 || tile >= JACC_NUM_TILES) return fail(JACC_ERR_INVALID_ARG, "bad feature args");
+  out4[0] = static_cast<float>(stencil / 27.0);
+  out4[1] = static_cast<float>(std::log2(side) / 10.0);
+  out4[2] = static_cast<float>(dtype / 64.0);
+  out4[3] = static_cast<float>(tile / 23.0);
+  return ok();
+}
+
+extern "C" jacc_status jacc_costmodel_create(const float* init_params, uint64_t seed, jacc_costmodel* out) {
+  if (!out) return fail(JACC_ERR_INVALID_ARG, "NULL output");
+  jacc_status st = ensure_setup();
+  if (st) return st;
+  std::unique_ptr<CostModel> m(new CostModel());
+  const size_t pb = sizeof(float) * JACC_MLP_NPARAM;
+  char* blk = nullptr;
+  st = cuda_check(cudaMalloc(&blk, 3 * pb + 256), "cudaMalloc(cost model)");
+  if (st) return st;
+  m->d_p = reinterpret_cast<float*>(blk);
+  m->d_m = reinterpret_cast<float*>(blk + pb);
+  m->d_v = reinterpret_cast<float*>(blk + 2 * pb);
+  m->d_step = reinterpret_cast<unsigned*>(blk + 3 * pb);
+  std::vector<float> p(JACC_MLP_NPARAM);
+  if (init_params) std::memcpy(p.data(), init_params, pb);
+  else kaiming_init(seed, p.data());
+  st = cuda_check(cudaMemcpy(m->d_p, p.data(), pb, cudaMemcpyHostToDevice), "cudaMemcpy(params)");
+  if (!st) st = cuda_check(cudaMemset(blk + pb, 0, 2 * pb + 256), "cudaMemset(Adam state)");
+  if (st) {
+    cudaFree(blk);
+    return st;
+  }
+  *out = reinterpret_cast<jacc_costmodel>(m.release());
+  return ok();
+}
+
+extern "C" jacc_status jacc_costmodel_set_params(jacc_costmodel h, const float* host_params) {
+  if (!h || !host_params) return fail(JACC_ERR_INVALID_ARG, "NULL model or params");
+  CostModel& m = *reinterpret_cast<CostModel*>(h);
+  const size_t pb = sizeof(float) * JACC_MLP_NPARAM;
+  jacc_status st = cuda_check(cudaMemcpy(m.d_p, host_params, pb, cudaMemcpyHostToDevice), "cudaMemcpy(params)");
+  if (!st) st = cuda_check(cudaMemset(m.d_m, 0, 2 * pb + 256), "cudaMemset(Adam state)");
+  return st;
+}
+
+extern "C" jacc_status jacc_costmodel_get_params(jacc_costmodel h, float* host_params) {
+  if (!h || !host_params) return fail(JACC_ERR_INVALID_ARG, "NULL model or params");
+  CostModel& m = *reinterpret_cast<CostModel*>(h);
+  return cuda_check(cudaMemcpy(host_params, m.d_p, sizeof(float) * JACC_MLP_NPARAM, cudaMemcpyDeviceToHost),
+                    "cudaMemcpy(params)");
+}
+
+extern "C" jacc_status jacc_costmodel_loss_grad(jacc_costmodel h, const float* x_dev, const float* y_dev, int32_t n,
+                                                float* grad_dev, float* loss_dev, uintptr_t stream) {
+  if (!h || !x_dev || !y_dev || n < 1 || !grad_dev) return fail(JACC_ERR_INVALID_ARG, "bad loss_grad arguments");
+  CostModel& m = *reinterpret_cast<CostModel*>(h);
+  jacc_status st = ensure_parts(m, n);
+  if (st) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  st = cuda_check(mlp_fwd_bwd(m.d_p, x_dev, y_dev, n, m.d_partial, m.d_losspart, nullptr, s), "MLP forward/backward");
+  if (st) return st;
+  return cuda_check(mlp_adam(m.d_p, m.d_m, m.d_v, m.d_partial, mlp_nparts(n), m.d_losspart, n, loss_dev, nullptr, 0.f,
+                             0.f, 0.f, 0.f, grad_dev, s),
+                    "MLP gradient reduction");
+}
+
+extern "C" jacc_status jacc_costmodel_train(jacc_costmodel h, const float* x_dev, const float* y_dev, int32_t n,
+                                            int32_t epochs, float lr, uintptr_t stream, float* loss_dev) {
+  if (!h || !x_dev || !y_dev || n < 1 || epochs < 1 || !(lr > 0.f)) return fail(JACC_ERR_INVALID_ARG, "bad train args");
+  CostModel& m = *reinterpret_cast<CostModel*>(h);
+  jacc_status st = ensure_parts(m, n);
+  if (st) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int np = mlp_nparts(n);
+  auto step = [&](cudaStream_t q, float* lossp) -> jacc_status {
+    jacc_status e = cuda_check(mlp_fwd_bwd(m.d_p, x_dev, y_dev, n, m.d_partial, m.d_losspart, m.d_step, q), "MLP fwd/bwd");
+    if (e) return e;
+    return cuda_check(mlp_adam(m.d_p, m.d_m, m.d_v, m.d_partial, np, m.d_losspart, n, lossp, m.d_step, lr, 0.9f,
+                               0.999f, 1e-8f, nullptr, q),
+                      "MLP Adam step");
+  };
+  // Capture a block of steps as one graph and replay it.
+  const int K = epochs < 64 ? epochs : 64;
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  st = cuda_check(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "cudaStreamCreate");
+  if (!st) st = cuda_check(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+  if (!st) {
+    jacc_status est = ok();
+    for (int k = 0; k < K && !est; ++k) est = step(cap, k == K - 1 ? loss_dev : nullptr);
+    cudaError_t ce = cudaStreamEndCapture(cap, &graph);
+    st = est ? est : cuda_check(ce, "cudaStreamEndCapture");
+    if (!st) st = cuda_check(cudaGraphInstantiate(&exec, graph, 0), "cudaGraphInstantiate");
+  }
+  int done = 0;
+  while (!st && done + K <= epochs) {
+    st = cuda_check(cudaGraphLaunch(exec, s), "cudaGraphLaunch(train)");
+    done += K;
+  }
+  while (!st && done < epochs) {
+    st = step(s, done == epochs - 1 ? loss_dev : nullptr);
+    ++done;
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (cap) cudaStreamDestroy(cap);
+  return st;
+}
+
+extern "C" jacc_status jacc_costmodel_predict(jacc_costmodel h, const float* x_dev, int32_t n, float* y_dev,
+                                              uintptr_t stream) {
+  if (!h || !x_dev || !y_dev || n < 1) return fail(JACC_ERR_INVALID_ARG, "bad predict arguments");
+  CostModel& m = *reinterpret_cast<CostModel*>(h);
+  return cuda_check(mlp_forward(m.d_p, x_dev, n, y_dev, reinterpret_cast<cudaStream_t>(stream)), "MLP forward");
+}
+
+extern "C" jacc_status jacc_costmodel_pick(jacc_costmodel h, const float* feats_dev, const int32_t* valid_dev, int32_t nq,
+                                           float* pred_dev, int32_t* pick_dev, float* gap_dev, uintptr_t stream) {
+  if (!h || !feats_dev || !valid_dev || nq < 1 || !pred_dev || !pick_dev || !gap_dev)
+    return fail(JACC_ERR_INVALID_ARG, "bad pick arguments");
+  CostModel& m = *reinterpret_cast<CostModel*>(h);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  jacc_status st = cuda_check(mlp_forward(m.d_p, feats_dev, nq * JACC_NUM_TILES, pred_dev, s), "MLP forward");
+  if (st) return st;
+  return cuda_check(mlp_pick(pred_dev, valid_dev, nq, JACC_NUM_TILES, pick_dev, gap_dev, s), "MLP pick");
+}
+
+extern "C" jacc_status jacc_costmodel_set_range(jacc_costmodel h, double side_lo, double side_hi, double margin) {
+  if (!h || !(side_lo > 0.0) || !(side_hi >= side_lo) || !(margin >= 0.0)) return fail(JACC_ERR_INVALID_ARG, "bad range");
+  CostModel& m = *reinterpret_cast<CostModel*>(h);
+  m.side_lo = side_lo;
+  m.side_hi = side_hi;
+  m.margin = margin;
+  return ok();
+}
+
+extern "C" jacc_status jacc_costmodel_choose(jacc_costmodel h, const jacc_kernel_desc* desc, void* u0, void* u1,
+                                             uintptr_t stream, int32_t* tile, int32_t* used_fallback) {
+  if (!h || !desc || !tile || !used_fallback) return fail(JACC_ERR_INVALID_ARG, "bad choose arguments");
+  CostModel& m = *reinterpret_cast<CostModel*>(h);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const double vol = static_cast<double>(desc->nx) * desc->ny * desc->nz;
+  const double side = desc->stencil == JACC_STENCIL_5PT ? std::sqrt(vol) : std::cbrt(vol);
+  float feats[JACC_NUM_TILES * 4];
+  int valid[JACC_NUM_TILES];
+  for (int t = 0; t < JACC_NUM_TILES; ++t) {
+    jacc_costmodel_features(desc->stencil, side, desc->dtype, t, feats + 4 * t);
+    valid[t] = tile_valid(*desc, t) ? 1 : 0;
+  }
+  jacc_status st = ok();
+  if (!m.d_feat) {
+    char* blk = nullptr;
+    st = cuda_check(cudaMalloc(&blk, 1024 + sizeof(feats) + 3 * sizeof(float) * JACC_NUM_TILES), "cudaMalloc(pick)");
+    if (st) return st;
+    m.d_feat = reinterpret_cast<float*>(blk);
+    m.d_pred = reinterpret_cast<float*>(blk + sizeof(feats));
+    m.d_valid = reinterpret_cast<int*>(blk + sizeof(feats) + sizeof(float) * JACC_NUM_TILES);
+    m.d_pick = reinterpret_cast<int*>(blk + sizeof(feats) + 2 * sizeof(float) * JACC_NUM_TILES);
+    m.d_gap = reinterpret_cast<float*>(blk + sizeof(feats) + 2 * sizeof(float) * JACC_NUM_TILES + 256);
+  }
+  st = cuda_check(cudaMemcpyAsync(m.d_feat, feats, sizeof(feats), cudaMemcpyHostToDevice, s), "upload features");
+  if (!st) st = cuda_check(cudaMemcpyAsync(m.d_valid, valid, sizeof(valid), cudaMemcpyHostToDevice, s), "upload valid");
+  if (!st) st = jacc_costmodel_pick(h, m.d_feat, m.d_valid, 1, m.d_pred, m.d_pick, m.d_gap, stream);
+  int pick = -1;
+  float gap = 0.f;
+  if (!st) st = cuda_check(cudaMemcpyAsync(&pick, m.d_pick, sizeof(int), cudaMemcpyDeviceToHost, s), "read pick");
+  if (!st) st = cuda_check(cudaMemcpyAsync(&gap, m.d_gap, sizeof(float), cudaMemcpyDeviceToHost, s), "read gap");
+  if (!st) st = cuda_check(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  if (st) return st;
+  const bool outside = side < m.side_lo || side > m.side_hi;
+  if (pick < 0 || outside || gap < m.margin) {
+    if (!u0 || !u1) return fail(JACC_ERR_INVALID_ARG, "fallback to the exhaustive autotuner needs u0 and u1");
+    jacc_tune_result r;
+    st = jacc_autotune(desc, u0, u1, 2, 3, stream, &r);
+    if (st) return st;
+    *tile = r.best_tile;
+    *used_fallback = 1;
+    return ok();
+  }
+  *tile = pick;
+  *used_fallback = 0;
+  remember_tile(*desc, pick);
+  return ok();
+}
+
+extern "C" jacc_status jacc_costmodel_save(jacc_costmodel h, const char* path) {
+  if (!h || !path) return fail(JACC_ERR_INVALID_ARG, "NULL model or path");
+  CostModel& m = *reinterpret_cast<CostModel*>(h);
+  std::vector<float> p(JACC_MLP_NPARAM);
+  jacc_status st = jacc_costmodel_get_params(h, p.data());
+  if (st) return st;
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(JACC_ERR_INVALID_ARG, std::string("cannot open ") + path);
+  const char magic[8] = {'J', 'A', 'C', 'C', 'M', 'L', 'P', '1'};
+  const double range[3] = {m.side_lo, m.side_hi, m.margin};
+  bool okw = std::fwrite(magic, 1, 8, f) == 8 && std::fwrite(range, sizeof(double), 3, f) == 3 &&
+             std::fwrite(p.data(), sizeof(float), p.size(), f) == p.size();
+  okw = (std::fclose(f) == 0) && okw;
+  return okw ? ok() : fail(JACC_ERR_INVALID_ARG, std::string("short write to ") + path);
+}
+
+extern "C" jacc_status jacc_costmodel_load(jacc_costmodel h, const char* path) {
+  if (!h || !path) return fail(JACC_ERR_INVALID_ARG, "NULL model or path");
+  CostModel& m = *reinterpret_cast<CostModel*>(h);
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(JACC_ERR_INVALID_ARG, std::string("cannot open ") + path);
+  char magic[8];
+  double range[3];
+  std::vector<float> p(JACC_MLP_NPARAM);
+  bool okr = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "JACCMLP1", 8) == 0 &&
+             std::fread(range, sizeof(double), 3, f) == 3 && std::fread(p.data(), sizeof(float), p.size(), f) == p.size();
+  std::fclose(f);
+  if (!okr) return fail(JACC_ERR_INVALID_ARG, std::string("not a cost-model file: ") + path);
+  m.side_lo = range[0];
+  m.side_hi = range[1];
+  m.margin = range[2];
+  return jacc_costmodel_set_params(h, p.data());
+}
+
+extern "C" jacc_status jacc_costmodel_release(jacc_costmodel h) {
+  if (!h) return fail(JACC_ERR_INVALID_ARG, "NULL model");
+  CostModel* m = reinterpret_cast<CostModel*>(h);
+  if (m->d_p) cudaFree(m->d_p);
+  if (m->d_partial) cudaFree(m->d_partial);
+  if (m->d_losspart) cudaFree(m->d_losspart);
+  if (m->d_feat) cudaFree(m->d_feat);
+  delete m;
+  return ok();
+}

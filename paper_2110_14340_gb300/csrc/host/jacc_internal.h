@@ -47,6 +47,7 @@ struct Kernel {
   bool jit = false;
   double compile_ms = 0.0;
   const void* func = nullptr;   // kernel entry (host stub or cudaKernel_t)
+  const void* func_out = nullptr;  // the entry for a sweep that ends a fixed-point sequence in FP64
   cudaLibrary_t lib = nullptr;  // NVRTC module, if jit
   dim3 grid, block;
   int tblock = 1;
@@ -55,21 +56,30 @@ struct Kernel {
   std::map<GraphKey, SweepGraph> graphs;
 };
 
-// Launch one sweep of `k` (no validation).  maxword may be null.
-cudaError_t launch_sweep_kernel(const Kernel& k, const void* u, void* v, double* resid, const u64* maxword,
+// Launch one sweep of `k` (no validation).  maxword may be null.  flags:
+// JFX_* bits (first sweep of a sequence reads FP64, last writes FP64).
+cudaError_t launch_sweep_kernel(const Kernel& k, const void* u, void* v, double* resid, const u64* maxword, int flags,
                                 cudaStream_t s);
+constexpr int kFxIn = 1, kFxOut = 2;  // JFX_IN_F64, JFX_OUT_F64
 // Enqueue the max-abs pre-pass of `n` doubles into maxword (zeroing it first).
 cudaError_t launch_maxabs(const double* u, long long n, u64* maxword, cudaStream_t s);
 cudaError_t launch_fill_skipped(double* resid, int n, int T, cudaStream_t s);
 
 // NVRTC: compile `src` (plus jacc_params.h) for sm_103a, load it, return
 // kernel `name`.  Uses the on-disk cache under $JACC_CACHE_DIR if set.
-jacc_status jit_compile(const std::string& src, const char* name, cudaLibrary_t* lib, const void** func,
-                        double* ms);
+jacc_status jit_compile(const std::string& src, const char* const* names, int nnames, cudaLibrary_t* lib,
+                        const void** funcs, double* ms);
 // The device-code text embedded at build time.
 const char* device_source();
 const char* params_source();
 
 std::mutex& global_mutex();
+
+// Tile validity for a descriptor (vector width and grid limits) and the
+// default tile; the autotuner's remembered pick for a shape (-1 if none).
+bool tile_valid(const jacc_kernel_desc& d, int t);
+int default_tile(const jacc_kernel_desc& d);
+int tuned_tile(const jacc_kernel_desc& d);
+void remember_tile(const jacc_kernel_desc& d, int tile);
 
 }  // namespace jacc

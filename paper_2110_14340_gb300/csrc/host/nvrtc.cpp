@@ -39,7 +39,8 @@ static bool read_file(const std::string& path, std::string* out) {
   return !out->empty();
 }
 
-jacc_status jit_compile(const std::string& src, const char* name, cudaLibrary_t* lib, const void** func, double* ms) {
+jacc_status jit_compile(const std::string& src, const char* const* names, int nnames, cudaLibrary_t* lib,
+                        const void** funcs, double* ms) {
   const auto t0 = std::chrono::steady_clock::now();
   static const char* opts[] = {"-arch=sm_103a", "-std=c++17", "-default-device", "-DJACC_NVRTC=1"};
   const int nopts = 4;
@@ -87,14 +88,16 @@ jacc_status jit_compile(const std::string& src, const char* name, cudaLibrary_t*
   }
   cudaError_t e = cudaLibraryLoadData(lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
   if (e != cudaSuccess) return fail(JACC_ERR_COMPILE, std::string("cudaLibraryLoadData: ") + cudaGetErrorString(e));
-  cudaKernel_t kern = nullptr;
-  e = cudaLibraryGetKernel(&kern, *lib, name);
-  if (e != cudaSuccess) {
-    cudaLibraryUnload(*lib);
-    *lib = nullptr;
-    return fail(JACC_ERR_COMPILE, std::string("cudaLibraryGetKernel: ") + cudaGetErrorString(e));
+  for (int i = 0; i < nnames; ++i) {
+    cudaKernel_t kern = nullptr;
+    e = cudaLibraryGetKernel(&kern, *lib, names[i]);
+    if (e != cudaSuccess) {
+      cudaLibraryUnload(*lib);
+      *lib = nullptr;
+      return fail(JACC_ERR_COMPILE, std::string("cudaLibraryGetKernel: ") + cudaGetErrorString(e));
+    }
+    funcs[i] = reinterpret_cast<const void*>(kern);
   }
-  *func = reinterpret_cast<const void*>(kern);
   *ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return ok();
 }

@@ -23,6 +23,13 @@ extern "C" const void* const jacc_tab_7_64[JACC_NTILES];
 extern "C" const void* const jacc_tab_7_32[JACC_NTILES];
 extern "C" const void* const jacc_tab_27_64[JACC_NTILES];
 extern "C" const void* const jacc_tab_27_32[JACC_NTILES];
+extern "C" const void* const jacc_tab_5_64_out[JACC_NTILES];
+extern "C" const void* const jacc_tab_5_32_out[JACC_NTILES];
+extern "C" const void* const jacc_tab_7_64_out[JACC_NTILES];
+extern "C" const void* const jacc_tab_7_32_out[JACC_NTILES];
+extern "C" const void* const jacc_tab_27_64_out[JACC_NTILES];
+extern "C" const void* const jacc_tab_27_32_out[JACC_NTILES];
+extern "C" const void* const jacc_tab_tb[2];
 
 namespace jacc {
 
@@ -57,11 +64,12 @@ static bool dyadic(double d, uint64_t* m, int* k) {
   return true;
 }
 
-static const void* table_entry(int stencil, int dtype, int tile) {
+static const void* table_entry(int stencil, int dtype, int tile, bool out) {
   const void* const* t = nullptr;
-  if (stencil == 5) t = dtype == 64 ? jacc_tab_5_64 : jacc_tab_5_32;
-  if (stencil == 7) t = dtype == 64 ? jacc_tab_7_64 : jacc_tab_7_32;
-  if (stencil == 27) t = dtype == 64 ? jacc_tab_27_64 : jacc_tab_27_32;
+  if (stencil == 5) t = dtype == 64 ? (out ? jacc_tab_5_64_out : jacc_tab_5_64) : (out ? jacc_tab_5_32_out : jacc_tab_5_32);
+  if (stencil == 7) t = dtype == 64 ? (out ? jacc_tab_7_64_out : jacc_tab_7_64) : (out ? jacc_tab_7_32_out : jacc_tab_7_32);
+  if (stencil == 27)
+    t = dtype == 64 ? (out ? jacc_tab_27_64_out : jacc_tab_27_64) : (out ? jacc_tab_27_32_out : jacc_tab_27_32);
   return t ? t[tile] : nullptr;
 }
 
@@ -146,7 +154,12 @@ static jacc_status validate(const jacc_kernel_desc& d) {
   if (d.stencil == 7 && d.boundary != JACC_DIRICHLET) return fail(JACC_ERR_UNSUPPORTED, "7-point: Dirichlet only");
   if (d.stencil == 27 && d.boundary != JACC_PERIODIC) return fail(JACC_ERR_UNSUPPORTED, "27-point: periodic only");
   if (d.tblock < 0) return fail(JACC_ERR_INVALID_ARG, "tblock < 0");
-  if (d.tblock > 1) return fail(JACC_ERR_UNSUPPORTED, "temporal blocking is not available in this build");
+  if (d.tblock > 1) {
+    if (d.stencil != 27 || d.dtype != JACC_F32 || d.tblock > 3)
+      return fail(JACC_ERR_UNSUPPORTED, "temporal blocking: 27-point FP32 with depth 2 or 3 only");
+    if (d.nx % 4) return fail(JACC_ERR_UNSUPPORTED, "temporal blocking needs nx divisible by 4");
+    if (d.flags & JACC_SPEC_JIT) return fail(JACC_ERR_UNSUPPORTED, "temporal blocking has no folded variant");
+  }
   for (int j = 0; j < 4; ++j)
     if (!std::isfinite(d.coeffs[j])) return fail(JACC_ERR_INVALID_ARG, "non-finite coefficient");
   const double n = static_cast<double>(d.nx) * static_cast<double>(d.ny) * static_cast<double>(d.nz);
@@ -154,14 +167,14 @@ static jacc_status validate(const jacc_kernel_desc& d) {
   return ok();
 }
 
-static int default_tile(const jacc_kernel_desc& d) {
+int default_tile(const jacc_kernel_desc& d) {
   const int V = d.dtype == 64 ? 2 : 4;
   const bool vec_ok = (d.nx % V) == 0;
   if (d.stencil == 5) return vec_ok ? 5 : 4;
   return vec_ok ? 15 : 14;
 }
 
-static bool tile_valid(const jacc_kernel_desc& d, int t) {
+bool tile_valid(const jacc_kernel_desc& d, int t) {
   const TileCfg& c = kTiles[t];
   const int V = c.vec16 ? (d.dtype == 64 ? 2 : 4) : 1;
   if (d.nx % V) return false;
@@ -198,13 +211,19 @@ static std::string jit_source(const Kernel& k) {
                 "  static constexpr int fk = %d, fpath = %d;\n"
                 "};\n"
                 "extern \"C\" __global__ void __launch_bounds__(%d) jacc_jit(const %s* __restrict__ u, "
-                "%s* __restrict__ v, JParams, double* resid, const u64* maxword) {\n"
+                "%s* __restrict__ v, JParams, double* resid, const u64* maxword, int flags) {\n"
                 "  const JFold f{};\n"
-                "  %s<%s, %d, %d, %d, %d>(u, v, f, resid, maxword);\n"
+                "  %s<%s, %d, %d, %d, %d, false>(u, v, f, resid, maxword, flags);\n"
+                "}\n"
+                "extern \"C\" __global__ void __launch_bounds__(%d) jacc_jit_out(const %s* __restrict__ u, "
+                "%s* __restrict__ v, JParams, double* resid, const u64* maxword, int flags) {\n"
+                "  const JFold f{};\n"
+                "  %s<%s, %d, %d, %d, %d, %s>(u, v, f, resid, maxword, flags);\n"
                 "}\n",
                 (long long)p.nx, (long long)p.ny, (long long)p.nz, p.c0, p.c1, p.c2, p.c3, (long long)p.fa,
                 (long long)p.fb, (long long)p.fw0, (long long)p.fw1, (long long)p.fw2, (long long)p.fw3, p.fk, p.fpath,
-                c.bx * c.by, T, T, entry, T, c.bx, c.by, k.vec, zc);
+                c.bx * c.by, T, T, entry, T, c.bx, c.by, k.vec, zc, c.bx * c.by, T, T, entry, T, c.bx, c.by, k.vec, zc,
+                k.desc.dtype == 64 ? "true" : "false");
   return std::string(device_source()) + buf;
 }
 
@@ -238,7 +257,11 @@ extern "C" jacc_status jacc_specialize(const jacc_kernel_desc* desc, jacc_kernel
   if (!desc || !out) return fail(JACC_ERR_INVALID_ARG, "NULL descriptor or output");
   jacc_status st = validate(*desc);
   if (st) return st;
-  int tile = desc->tile_id >= 0 ? desc->tile_id : default_tile(*desc);
+  int tile = desc->tile_id;
+  if (tile < 0) {
+    tile = tuned_tile(*desc);
+    if (tile < 0 || !tile_valid(*desc, tile)) tile = default_tile(*desc);
+  }
   if (!tile_valid(*desc, tile))
     return fail(JACC_ERR_INVALID_ARG, "tile " + std::to_string(tile) + " does not fit this shape (x vector width)");
   const std::string key = key_of(*desc, tile);
@@ -275,13 +298,29 @@ extern "C" jacc_status jacc_specialize(const jacc_kernel_desc* desc, jacc_kernel
     k->grid = dim3(static_cast<unsigned>((desc->nx + tx - 1) / tx), static_cast<unsigned>((desc->ny + c.by - 1) / c.by),
                    static_cast<unsigned>((desc->nz + c.zc - 1) / c.zc));
   }
-  if (desc->flags & JACC_SPEC_JIT) {
-    st = jit_compile(jit_source(*k), "jacc_jit", &k->lib, &k->func, &k->compile_ms);
+  if (desc->tblock > 1) {
+    // temporally blocked 27-point kernel: 32 x 16 threads over a 128 x 16 region,
+    // output tile 120 x (16 - 2T), 64-plane chunks
+    const int T = desc->tblock;
+    k->tblock = T;
+    k->func = jacc_tab_tb[T - 2];
+    k->block = dim3(32, 16, 1);
+    const int64_t oy = 16 - 2 * T;
+    k->grid = dim3(static_cast<unsigned>((desc->nx + 119) / 120), static_cast<unsigned>((desc->ny + oy - 1) / oy),
+                   static_cast<unsigned>((desc->nz + 63) / 64));
+    k->func_out = k->func;
+  } else if (desc->flags & JACC_SPEC_JIT) {
+    static const char* const names[2] = {"jacc_jit", "jacc_jit_out"};
+    const void* f[2] = {nullptr, nullptr};
+    st = jit_compile(jit_source(*k), names, 2, &k->lib, f, &k->compile_ms);
     if (st) return st;
+    k->func = f[0];
+    k->func_out = f[1];
     k->jit = true;
   } else {
-    k->func = table_entry(desc->stencil, desc->dtype, tile);
-    if (!k->func) return fail(JACC_ERR_UNSUPPORTED, "no precompiled kernel for this descriptor");
+    k->func = table_entry(desc->stencil, desc->dtype, tile, false);
+    k->func_out = table_entry(desc->stencil, desc->dtype, tile, true);
+    if (!k->func || !k->func_out) return fail(JACC_ERR_UNSUPPORTED, "no precompiled kernel for this descriptor");
   }
   if (desc->dtype == 64 && p.fpath != JACC_FP_NONE) {
     st = cuda_check(cudaMalloc(reinterpret_cast<void**>(&k->scratch), 256), "cudaMalloc(scratch)");
@@ -337,11 +376,11 @@ extern "C" jacc_status jacc_shutdown(void) {
 
 namespace jacc {
 
-cudaError_t launch_sweep_kernel(const Kernel& k, const void* u, void* v, double* resid, const u64* maxword,
+cudaError_t launch_sweep_kernel(const Kernel& k, const void* u, void* v, double* resid, const u64* maxword, int flags,
                                 cudaStream_t s) {
   JParams p = k.params;
-  const void* args[] = {&u, &v, &p, &resid, &maxword};
-  return cudaLaunchKernel(k.func, k.grid, k.block, const_cast<void**>(args), 0, s);
+  const void* args[] = {&u, &v, &p, &resid, &maxword, &flags};
+  return cudaLaunchKernel((flags & kFxOut) ? k.func_out : k.func, k.grid, k.block, const_cast<void**>(args), 0, s);
 }
 
 }  // namespace jacc
@@ -370,7 +409,7 @@ static jacc_status enqueue_one(const Kernel& k, const void* u, void* v, double* 
     jacc_status st = cuda_check(cudaMemsetAsync(resid, 0, sizeof(double), s), "cudaMemsetAsync(resid)");
     if (st) return st;
   }
-  return cuda_check(launch_sweep_kernel(k, u, v, resid, mw, s), "stencil launch");
+  return cuda_check(launch_sweep_kernel(k, u, v, resid, mw, kFxIn | kFxOut, s), "stencil launch");
 }
 
 extern "C" jacc_status jacc_launch(jacc_kernel h, const void* u_in, void* u_out, double* resid_dev, uintptr_t stream) {
@@ -381,7 +420,9 @@ extern "C" jacc_status jacc_launch(jacc_kernel h, const void* u_in, void* u_out,
   return enqueue_one(k, u_in, u_out, resid_dev, k.scratch, reinterpret_cast<cudaStream_t>(stream));
 }
 
-// The full sweep sequence on stream s.
+// The full sweep sequence on stream s.  A temporally blocked kernel performs
+// tblock sweeps per launch; only every tblock-th sweep is materialised and the
+// residual slots of the others are set to NaN.
 static jacc_status enqueue_sweeps(const Kernel& k, void* u0, void* u1, int32_t n, double* resid, u64* scratch,
                                   cudaStream_t s) {
   const u64* mw = nullptr;
@@ -391,14 +432,19 @@ static jacc_status enqueue_sweeps(const Kernel& k, void* u0, void* u1, int32_t n
     if (st) return st;
     mw = scratch;
   }
+  const int T = k.tblock > 1 ? k.tblock : 1;
   if (resid) {
     jacc_status st = cuda_check(cudaMemsetAsync(resid, 0, sizeof(double) * static_cast<size_t>(n), s), "memset resid");
+    if (!st && T > 1) st = cuda_check(launch_fill_skipped(resid, n, T, s), "resid NaN fill");
     if (st) return st;
   }
-  for (int32_t i = 0; i < n; ++i) {
+  const int32_t launches = n / T;
+  for (int32_t i = 0; i < launches; ++i) {
     const void* src = (i % 2 == 0) ? u0 : u1;
     void* dst = (i % 2 == 0) ? u1 : u0;
-    jacc_status st = cuda_check(launch_sweep_kernel(k, src, dst, resid ? resid + i : nullptr, mw, s), "stencil launch");
+    const int fl = (i == 0 ? kFxIn : 0) | (i == launches - 1 ? kFxOut : 0);
+    double* r = resid ? resid + static_cast<int64_t>(i) * T + (T - 1) : nullptr;
+    jacc_status st = cuda_check(launch_sweep_kernel(k, src, dst, r, mw, fl, s), "stencil launch");
     if (st) return st;
   }
   return ok();
@@ -412,6 +458,8 @@ extern "C" jacc_status jacc_sweep(jacc_kernel h, void* u0, void* u1, int32_t nsw
   Kernel& k = *reinterpret_cast<Kernel*>(h);
   jacc_status st = check_buffers(k, u0, u1);
   if (st) return st;
+  if (k.tblock > 1 && nsweeps % k.tblock)
+    return fail(JACC_ERR_INVALID_ARG, "nsweeps must be a multiple of the temporal-blocking depth");
   if (k.desc.stencil == 27 && k.params.fpath != JACC_FP_NONE) {
     // the fixed-point scale is taken once from u0; values may grow by W per sweep
     const double W = k.desc.coeffs[0] + 6 * k.desc.coeffs[1] + 12 * k.desc.coeffs[2] + 8 * k.desc.coeffs[3];
@@ -419,7 +467,7 @@ extern "C" jacc_status jacc_sweep(jacc_kernel h, void* u0, void* u1, int32_t nsw
       return fail(JACC_ERR_UNSUPPORTED, "weight sum too far above 1 for this many fixed-point sweeps");
   }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (final_buf) *final_buf = nsweeps % 2;
+  if (final_buf) *final_buf = (nsweeps / (k.tblock > 1 ? k.tblock : 1)) % 2;
   if (!(flags & JACC_SWEEP_GRAPH)) return enqueue_sweeps(k, u0, u1, nsweeps, resid_dev, k.scratch, s);
 
   std::lock_guard<std::mutex> lock(global_mutex());

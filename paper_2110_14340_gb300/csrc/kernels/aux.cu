@@ -17,6 +17,10 @@ cudaError_t launch_maxabs(const double* u, long long n, u64* maxword, cudaStream
   return cudaGetLastError();
 }
 
+// Temporally blocked 27-point FP32 kernels: region 128 x 16, depth 2 and 3, 64-plane chunks.
+extern "C" const void* const jacc_tab_tb[2] = {(const void*)jacc_k_box27_tb<16, 2, 64>,
+                                               (const void*)jacc_k_box27_tb<16, 3, 64>};
+
 cudaError_t launch_fill_skipped(double* resid, int n, int T, cudaStream_t s) {
   jacc_k_fill_skipped<<<(n + 255) / 256, 256, 0, s>>>(resid, n, T);
   return cudaGetLastError();

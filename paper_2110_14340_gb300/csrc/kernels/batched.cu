@@ -54,14 +54,24 @@ JD int wait_done(const unsigned* done, unsigned target, int* status, u64 timeout
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 
+// One band: warps take 32*V-column chunks; the fixed-point path keeps the
+// field resident in fixed point between sweeps (flags: first sweep reads
+// FP64, last sweep writes FP64).
 template <int V, int MODE>
-JD void run_band(const JBGrid& G, const double* src, double* dst, i64 r0, i64 r1, int F,
+JD void run_band(const JBGrid& G, const double* src, double* dst, i64 r0, i64 r1, int F, int flags,
                  typename RT<double, MODE>::type& m) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const i64 chunk = 32 * V;
   const i64 nchunks = (G.nx + chunk - 1) / chunk;
-  for (i64 c = warp; c < nchunks; c += kWarps)
-    jacobi_march<double, V, MODE, true>(src, dst, G.nx, G.ny, c * chunk + lane * V, r0, r1, F, m);
+  for (i64 c = warp; c < nchunks; c += kWarps) {
+    const i64 x0 = c * chunk + lane * V;
+    if constexpr (MODE == JM_FIXED) {
+      if (flags & JFX_OUT_F64) jacobi_fx_march<V, true, true>(src, dst, G.nx, G.ny, x0, r0, r1, F, flags, m);
+      else jacobi_fx_march<V, true, false>(src, dst, G.nx, G.ny, x0, r0, r1, F, flags, m);
+    } else {
+      jacobi_march<double, V, MODE, true>(src, dst, G.nx, G.ny, x0, r0, r1, F, m);
+    }
+  }
 }
 
 __global__ void __launch_bounds__(kThreads) jacc_k_batched(JBatchParams bp) {
@@ -91,16 +101,17 @@ __global__ void __launch_bounds__(kThreads) jacc_k_batched(JBatchParams bp) {
     const double* src = G.u[s & 1];
     double* dst = G.u[(s + 1) & 1];
     const int F = bp.maxwords ? fx_frac_bits(bp.maxwords[it.g]) : -1;
+    const int flags = (s == 0 ? JFX_IN_F64 : 0) | (s == bp.nsweeps - 1 ? JFX_OUT_F64 : 0);
     u64 bits;
     if (F >= 0) {
       u64 m = 0;
-      if (G.vec == 2) run_band<2, JM_FIXED>(G, src, dst, r0, r1, F, m);
-      else run_band<1, JM_FIXED>(G, src, dst, r0, r1, F, m);
+      if (G.vec == 2) run_band<2, JM_FIXED>(G, src, dst, r0, r1, F, flags, m);
+      else run_band<1, JM_FIXED>(G, src, dst, r0, r1, F, flags, m);
       bits = dbits(fx_to_u(m, F + 2));
     } else {
       double m = 0.0;
-      if (G.vec == 2) run_band<2, JM_NATIVE>(G, src, dst, r0, r1, F, m);
-      else run_band<1, JM_NATIVE>(G, src, dst, r0, r1, F, m);
+      if (G.vec == 2) run_band<2, JM_NATIVE>(G, src, dst, r0, r1, F, flags, m);
+      else run_band<1, JM_NATIVE>(G, src, dst, r0, r1, F, flags, m);
       bits = dbits(m);
     }
     block_max_to<kThreads>(bits, bp.resid ? bp.resid + (i64)it.g * bp.nsweeps + s : nullptr);

@@ -13,15 +13,22 @@ typedef float JT;
 #endif
 
 #if JACC_INST_STENCIL == 5
-#define JKERN(BX, BY, V, ZC) jacc_k_jacobi2d<JT, BX, BY, V, (ZC) / 4>
+#define JKERN(BX, BY, V, ZC, O) jacc_k_jacobi2d<JT, BX, BY, V, (ZC) / 4, O>
 #elif JACC_INST_STENCIL == 7
-#define JKERN(BX, BY, V, ZC) jacc_k_heat3d<JT, BX, BY, V, ZC>
+#define JKERN(BX, BY, V, ZC, O) jacc_k_heat3d<JT, BX, BY, V, ZC, O>
 #else
-#define JKERN(BX, BY, V, ZC) jacc_k_box27<JT, BX, BY, V, ZC>
+#define JKERN(BX, BY, V, ZC, O) jacc_k_box27<JT, BX, BY, V, ZC, O>
 #endif
 
 #define JCAT3(a, b, c) a##b##_##c
+#define JCAT4(a, b, c, d) a##b##_##c##d
 #define JTABNAME(s, d) JCAT3(jacc_tab_, s, d)
-#define JENTRY(id, BX, BY, VEC, ZC) (const void*)JKERN(BX, BY, ((VEC) ? JVEC : 1), ZC),
+#define JTABOUT(s, d) JCAT4(jacc_tab_, s, d, _out)
+#define JENTRY(id, BX, BY, VEC, ZC) (const void*)JKERN(BX, BY, ((VEC) ? JVEC : 1), ZC, false),
+#define JENTRY_OUT(id, BX, BY, VEC, ZC) (const void*)JKERN(BX, BY, ((VEC) ? JVEC : 1), ZC, (JACC_INST_DTYPE == 64)),
 
+// Table 1: sweeps that write the resident fixed-point form (and every FP32 or
+// native sweep).  Table 2: sweeps that write FP64 from the fixed-point path
+// (the last of a sequence); identical to table 1 for FP32.
 extern "C" const void* const JTABNAME(JACC_INST_STENCIL, JACC_INST_DTYPE)[JACC_NTILES] = {JACC_TILE_LIST(JENTRY)};
+extern "C" const void* const JTABOUT(JACC_INST_STENCIL, JACC_INST_DTYPE)[JACC_NTILES] = {JACC_TILE_LIST(JENTRY_OUT)};

@@ -266,13 +266,7 @@ JD void jacobi_march(const T* __restrict__ u, T* __restrict__ v, i64 nx, i64 ny,
       const W xl = (e == 0) ? left : cur[e - 1];
       const W xr = (e == V - 1) ? right : cur[e + 1];
       const bool in = yint && (x >= 1) && (x <= nx - 2);
-      if constexpr (MODE == JM_FIXED) {
-        const i64 s = (up[e] + dn[e]) + (xl + xr);  // exact; v = s * 2^-(F+2)
-        out[e] = in ? (T)fx_to(s, F + 2) : rcur[e];
-        const i64 d = s - cur[e] * 4;   // 4 (v - u) in scale F
-        const u64 ad = (u64)(d < 0 ? -d : d);
-        if (in && ad > rmax) rmax = ad;
-      } else {
+      {
         const T s = (up[e] + dn[e]) + (xl + xr);
         const T r = T(0.25) * s;
         out[e] = in ? r : rcur[e];
@@ -294,27 +288,16 @@ JD void jacobi_march(const T* __restrict__ u, T* __restrict__ v, i64 nx, i64 ny,
   }
 }
 
-// CTA = BX x BY threads; thread row ty marches rows [ys, ys + ZC).
-template <class T, int BX, int BY, int V, int ZC, int MODE, class P>
-JD void jacobi2d_body(const T* __restrict__ u, T* __restrict__ v, const P& p, int F,
-                      typename RT<T, MODE>::type& rmax) {
-  const i64 nx = p.nx, ny = p.ny;
-  const i64 x0 = (i64)blockIdx.x * (BX * V) + (i64)threadIdx.x * V;
-  const i64 ys = ((i64)blockIdx.y * BY + threadIdx.y) * ZC;
-  const i64 ye = (ys + ZC < ny) ? ys + ZC : ny;
-  if (ys >= ny) return;  // whole warp (a warp lies within one thread row)
-  jacobi_march<T, V, MODE, false>(u, v, nx, ny, x0, ys, ye, F, rmax);
-}
-
 // ====================================================================== 3D z-marching tiles
 //
 // CTA = BX x BY threads covering x in [bx0, bx0 + BX*V), y in [by0, by0 + BY),
 // marching z over [cz0, cz0 + ZC).  The current plane lives in shared memory
 // with a one-point halo in x and y (double-buffered, so one __syncthreads per
 // plane); each thread keeps its own column's z-1, z, z+1 in registers.
-// Loads for plane z+1 (halo) and z+2 (own) are issued one iteration ahead.
+// Loads are issued ahead of use (one plane ahead in the native kernels, two in
+// the resident fixed-point kernels).
 
-template <class W, int BX, int BY, int V> struct Plane {
+template <class W, int BX, int BY, int V> struct alignas(16) Plane {
   // row layout: [pad V-1][left halo][TX values][right halo][pad V-1]
   static constexpr int TX = BX * V;
   static constexpr int RW = TX + 2 * V;
@@ -479,18 +462,7 @@ JD void heat3d_body(const T* __restrict__ u, T* __restrict__ v, const P& p, int 
       const W xl = (e == 0) ? r0[-1] : cur[e - 1];
       const W xr = (e == V - 1) ? r0[V] : cur[e + 1];
       const W s = ((xl + xr) + (rm[e] + rp[e])) + (zp[e] + zn[e]);
-      if constexpr (MODE == JM_FIXED) {
-        const i64 L = s - 6 * cur[e];
-        double o;
-        if (p.fpath == JACC_FP_SMALL) {
-          o = fx_to(p.fa * cur[e] + p.fb * s, F + p.fk);
-        } else {
-          o = fx128_to(add128(from_s64_shl(cur[e], p.fk), mul_s64_u64(L, (u64)p.fw0)), F + p.fk);
-        }
-        out[e] = in ? (T)o : rcur[e];
-        const u64 aL = (u64)(L < 0 ? -L : L);
-        if (in && aL > rmax) rmax = aL;
-      } else {
+      {
         const T r = (T)p.c0;
         const T o = cur[e] + r * (s - T(6) * cur[e]);
         out[e] = in ? o : rcur[e];
@@ -643,15 +615,7 @@ JD void box27_body(const T* __restrict__ u, T* __restrict__ v, const P& p, int F
       const W F1 = (f0[e] + cm[e]) + cn[e];
       const W E2 = (g0[e] + fm[e]) + fn[e];
       const W C3 = gm[e] + gn[e];
-      if constexpr (MODE == JM_FIXED) {
-        s128 a = mul_s64_u64(c0[e], (u64)p.fw0);
-        a = add128(a, mul_s64_u64(F1, (u64)p.fw1));
-        a = add128(a, mul_s64_u64(E2, (u64)p.fw2));
-        a = add128(a, mul_s64_u64(C3, (u64)p.fw3));
-        out[e] = (T)fx128_to(a, F + p.fk);
-      } else {
-        out[e] = ((T)p.c0 * c0[e] + (T)p.c1 * F1) + ((T)p.c2 * E2 + (T)p.c3 * C3);
-      }
+      out[e] = ((T)p.c0 * c0[e] + (T)p.c1 * F1) + ((T)p.c2 * E2 + (T)p.c3 * C3);
     }
     if (act) {
       stv<T, V>(vrow + z * sz, out);
@@ -667,46 +631,699 @@ JD void box27_body(const T* __restrict__ u, T* __restrict__ v, const P& p, int F
   }
 }
 
+// ---------------------------------------------------------------- 27-point periodic box, native arithmetic
+//
+// All periodic offsets are computed once per thread (no division in the
+// plane loop); plane z+2 is fetched into registers one iteration ahead and
+// stored to shared memory the next.  Row reads from shared memory use 16-byte
+// vectors for the thread's own V columns.
+
+template <class W, int V> JD void lds_row(const W* p, W (&r)[V + 2]) {
+  r[0] = p[-1];
+  if constexpr (V * sizeof(W) == 16 && V == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    r[1] = t.x; r[2] = t.y; r[3] = t.z; r[4] = t.w;
+  } else if constexpr (V * sizeof(W) == 16 && V == 2) {
+    const double2 t = *reinterpret_cast<const double2*>(p);
+    r[1] = t.x; r[2] = t.y;
+  } else {
+#pragma unroll
+    for (int e = 0; e < V; ++e) r[e + 1] = p[e];
+  }
+  r[V + 1] = p[V];
+}
+
+template <class T, int BX, int BY, int V>
+struct Box27Fetch {
+  T own[V], hrow[V], hx, cr[4];
+};
+
+template <class T, int BX, int BY, int V, int ZC, class P>
+JD void box27_body2(const T* __restrict__ u, T* __restrict__ v, const P& p, SumAcc<T>& acc, bool want_sum,
+                    Plane<T, BX, BY, V>& sm) {
+  const i64 nx = p.nx, ny = p.ny, nz = p.nz;
+  const i64 sz = nx * ny;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const i64 bx0 = (i64)blockIdx.x * (BX * V);
+  const i64 by0 = (i64)blockIdx.y * BY;
+  const i64 x0 = bx0 + (i64)tx * V;
+  const i64 y = by0 + ty;
+  const bool act = (x0 < nx) && (y < ny);
+  const i64 z0 = (i64)blockIdx.z * ZC;
+  const i64 z1 = (z0 + ZC < nz) ? z0 + ZC : nz;
+  // periodic images, once per thread (threads overhanging the grid use them too)
+  const i64 xo = x0 % nx, yo = y % ny;
+  const i64 own_off = yo * nx + xo;
+  const bool hy = (ty == 0) || (ty == BY - 1);
+  const i64 hy_off = ((ty == 0) ? (by0 - 1 + ny) % ny : (by0 + BY) % ny) * nx + xo;
+  const bool hx = (tx == 0) || (tx == BX - 1);
+  const i64 hx_off = yo * nx + ((tx == 0) ? (bx0 - 1 + nx) % nx : (bx0 + BX * V) % nx);
+  const bool corner = (tx == 0) && (ty == 0);
+  i64 c_off[4] = {0, 0, 0, 0};
+  if (corner) {
+    const i64 xl = (bx0 - 1 + nx) % nx, xr = (bx0 + BX * V) % nx;
+    const i64 yt = (by0 - 1 + ny) % ny, yb = (by0 + BY) % ny;
+    c_off[0] = yt * nx + xl;
+    c_off[1] = yt * nx + xr;
+    c_off[2] = yb * nx + xl;
+    c_off[3] = yb * nx + xr;
+  }
+  auto fetch = [&](i64 zoff, Box27Fetch<T, BX, BY, V>& f) {
+    const T* pl = u + zoff;
+    ldv<T, V>(pl + own_off, f.own);
+    if (hy) ldv<T, V>(pl + hy_off, f.hrow);
+    if (hx) f.hx = __ldg(pl + hx_off);
+    if (corner) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) f.cr[k] = __ldg(pl + c_off[k]);
+    }
+  };
+  auto put = [&](const Box27Fetch<T, BX, BY, V>& f, int b) {
+    T* row = &sm.a[b][ty + 1][V + tx * V];
+#pragma unroll
+    for (int e = 0; e < V; ++e) row[e] = f.own[e];
+    if (hy) {
+      T* hr = &sm.a[b][ty == 0 ? 0 : BY + 1][V + tx * V];
+#pragma unroll
+      for (int e = 0; e < V; ++e) hr[e] = f.hrow[e];
+    }
+    if (tx == 0) sm.a[b][ty + 1][V - 1] = f.hx;
+    if (tx == BX - 1) sm.a[b][ty + 1][V + BX * V] = f.hx;
+    if (corner) {
+      sm.a[b][0][V - 1] = f.cr[0];
+      sm.a[b][0][V + BX * V] = f.cr[1];
+      sm.a[b][BY + 1][V - 1] = f.cr[2];
+      sm.a[b][BY + 1][V + BX * V] = f.cr[3];
+    }
+  };
+  auto cfe = [&](int b, T (&c)[V], T (&f)[V], T (&g)[V]) {
+    T m[V + 2], zz[V + 2], q[V + 2];
+    lds_row<T, V>(&sm.a[b][ty][V + tx * V], m);
+    lds_row<T, V>(&sm.a[b][ty + 1][V + tx * V], zz);
+    lds_row<T, V>(&sm.a[b][ty + 2][V + tx * V], q);
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      c[e] = zz[e + 1];
+      f[e] = (zz[e] + zz[e + 2]) + (m[e + 1] + q[e + 1]);
+      g[e] = (m[e] + m[e + 2]) + (q[e] + q[e + 2]);
+    }
+  };
+  auto next_plane = [&](i64 zi) { return zi + 1 == nz ? (i64)0 : zi + 1; };
+
+  const T w0 = (T)p.c0, wf = (T)p.c1, we = (T)p.c2, wc = (T)p.c3;
+  T cm[V], fm[V], gm[V], c0[V], f0[V], g0[V];
+  Box27Fetch<T, BX, BY, V> fa, fb;
+  i64 zi = (z0 - 1 + nz) % nz;  // plane z0 - 1
+  fetch(zi * sz, fa);
+  zi = next_plane(zi);           // plane z0
+  fetch(zi * sz, fb);
+  put(fa, 0);
+  __syncthreads();
+  cfe(0, cm, fm, gm);
+  put(fb, 1);
+  zi = next_plane(zi);           // plane z0 + 1
+  fetch(zi * sz, fa);
+  __syncthreads();
+  cfe(1, c0, f0, g0);
+  int b = 0;
+  for (i64 z = z0; z < z1; ++z) {
+    put(fa, b);                   // plane z + 1
+    if (z + 1 < z1) {
+      zi = next_plane(zi);        // plane z + 2, one iteration ahead
+      fetch(zi * sz, fa);
+    }
+    __syncthreads();
+    T cn[V], fn[V], gn[V];
+    cfe(b, cn, fn, gn);
+    T out[V];
+#pragma unroll
+    for (int e = 0; e < V; ++e)
+      out[e] = (w0 * c0[e] + wf * ((f0[e] + cm[e]) + cn[e])) + (we * ((g0[e] + fm[e]) + fn[e]) + wc * (gm[e] + gn[e]));
+    if (act) {
+      stv<T, V>(v + z * sz + y * nx + x0, out);
+      if (want_sum) {
+#pragma unroll
+        for (int e = 0; e < V; ++e) acc.add(out[e]);
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      cm[e] = c0[e]; fm[e] = f0[e]; gm[e] = g0[e];
+      c0[e] = cn[e]; f0[e] = fn[e]; g0[e] = gn[e];
+    }
+    b ^= 1;
+  }
+}
+
+// ---------------------------------------------------------------- 27-point periodic box, temporal blocking (FP32)
+//
+// TT sweeps per launch.  A CTA of 32 x RY threads (4 floats each in x) loads
+// an input region of 128 x RY points per plane: an output tile of 120 x
+// (RY - 2 TT) points plus a halo of 4 columns (16-byte alignment) and TT rows
+// on each side.  Planes stream in z; stage t (1..TT) computes sweep t for the
+// plane t steps behind the input, from the three newest planes of stage t-1,
+// over the region shrunk by t (values beyond it are never used).  Each stage's
+// newest plane sits in shared memory, one 16-byte vector per thread and row;
+// x-neighbours come from warp shuffles (a warp is one region row).  Only the
+// last stage's plane is written to memory, so HBM traffic is 8/TT bytes per
+// point-sweep.
+constexpr int TB_BX = 32, TB_V = 4, TB_RX = TB_BX * TB_V, TB_HX = 4, TB_OX = TB_RX - 2 * TB_HX;
+
+template <int RY> struct alignas(16) TbPlane {
+  float a[RY + 2][TB_RX + 8];  // row r + 1, column c + 4 holds region point (c, r)
+};
+
+template <int RY> JD void tb_cfe(const TbPlane<RY>& sm, float (&c)[4], float (&f)[4], float (&g)[4]) {
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  float r[3][6];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float4 t = *reinterpret_cast<const float4*>(&sm.a[ty + k][4 + tx * 4]);
+    r[k][1] = t.x; r[k][2] = t.y; r[k][3] = t.z; r[k][4] = t.w;
+    r[k][0] = __shfl_up_sync(0xffffffffu, t.w, 1);
+    r[k][5] = __shfl_down_sync(0xffffffffu, t.x, 1);
+  }
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    c[e] = r[1][e + 1];
+    f[e] = (r[1][e] + r[1][e + 2]) + (r[0][e + 1] + r[2][e + 1]);
+    g[e] = (r[0][e] + r[0][e + 2]) + (r[2][e] + r[2][e + 2]);
+  }
+}
+
+template <int RY> JD void tb_put(TbPlane<RY>& sm, const float (&o)[4]) {
+  float4 t;
+  t.x = o[0]; t.y = o[1]; t.z = o[2]; t.w = o[3];
+  *reinterpret_cast<float4*>(&sm.a[threadIdx.y + 1][4 + threadIdx.x * 4]) = t;
+}
+
+template <int RY, int TT, int ZC, class P>
+JD void box27_tb_body(const float* __restrict__ u, float* __restrict__ v, const P& p, SumAcc<float>& acc,
+                      bool want_sum, TbPlane<RY> (&sm)[TT]) {
+  const i64 nx = p.nx, ny = p.ny, nz = p.nz;
+  const i64 sz = nx * ny;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  constexpr int OY = RY - 2 * TT;
+  const i64 ox0 = (i64)blockIdx.x * TB_OX;
+  const i64 oy0 = (i64)blockIdx.y * OY;
+  const i64 z0 = (i64)blockIdx.z * ZC;
+  const i64 z1 = (z0 + ZC < nz) ? z0 + ZC : nz;
+  // this thread's 4 region columns and region row, wrapped once
+  const i64 gx = ((ox0 - TB_HX + (i64)tx * 4) % nx + nx) % nx;
+  const i64 gy = ((oy0 - TT + ty) % ny + ny) % ny;
+  const i64 own = gy * nx + gx;
+  // output: threads 1..30 hold the tile's 120 columns, rows TT..RY-TT-1
+  const i64 outx = ox0 + (i64)(tx - 1) * 4;
+  const i64 outy = oy0 + ty - TT;
+  const bool out_ok = tx >= 1 && tx <= TB_BX - 2 && ty >= TT && ty < RY - TT && outx < nx && outy < ny;
+  const float w0 = (float)p.c0, wf = (float)p.c1, we = (float)p.c2, wc = (float)p.c3;
+
+  float cm[TT][4], fm[TT][4], gm[TT][4], c0[TT][4], f0[TT][4], g0[TT][4];
+#pragma unroll
+  for (int t = 0; t < TT; ++t)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) cm[t][e] = fm[t][e] = gm[t][e] = c0[t][e] = f0[t][e] = g0[t][e] = 0.f;
+
+  const i64 zs = z0 - TT;  // first input plane
+  i64 zi = ((zs - 1) % nz + nz) % nz;
+  const int nsteps = (int)(z1 - z0) + 2 * TT;
+  float nxt[4];
+  zi = (zi + 1 == nz) ? 0 : zi + 1;
+  ldv<float, 4>(u + zi * sz + own, nxt);
+  for (int j = 0; j < nsteps; ++j) {
+    float cur_in[4] = {nxt[0], nxt[1], nxt[2], nxt[3]};
+    if (j + 1 < nsteps) {  // prefetch the next input plane
+      zi = (zi + 1 == nz) ? 0 : zi + 1;
+      ldv<float, 4>(u + zi * sz + own, nxt);
+    }
+    tb_put<RY>(sm[0], cur_in);
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < TT; ++t) {
+      float cn[4], fn[4], gn[4], o[4];
+      tb_cfe<RY>(sm[t], cn, fn, gn);
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        o[e] = (w0 * c0[t][e] + wf * ((f0[t][e] + cm[t][e]) + cn[e])) +
+               (we * ((g0[t][e] + fm[t][e]) + fn[e]) + wc * (gm[t][e] + gn[e]));
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        cm[t][e] = c0[t][e]; fm[t][e] = f0[t][e]; gm[t][e] = g0[t][e];
+        c0[t][e] = cn[e]; f0[t][e] = fn[e]; g0[t][e] = gn[e];
+      }
+      if (t + 1 < TT) {
+        tb_put<RY>(sm[t + 1], o);
+        __syncthreads();
+      } else if (j >= 2 * TT && out_ok) {
+        const i64 z = zs + j - TT;  // output plane, in [z0, z1)
+        stv<float, 4>(v + z * sz + outy * nx + outx, o);
+        if (want_sum) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) acc.add(o[e]);
+        }
+      }
+    }
+  }
+}
+
+template <int RY, int TT, int ZC, class P>
+JD void box27_tb_entry(const float* __restrict__ u, float* __restrict__ v, const P& p, double* resid) {
+  __shared__ TbPlane<RY> sm[TT];
+  SumAcc<float> acc;
+  box27_tb_body<RY, TT, ZC>(u, v, p, acc, resid != nullptr, sm);
+  block_sum_to<TB_BX * RY>(acc.total(), resid);
+}
+
+// ====================================================================== resident fixed point (FP64 data)
+//
+// Within one sweep sequence the field stays in 64-bit fixed point in the two
+// HBM buffers (the same 8 bytes per value): the first sweep reads FP64 and
+// converts, intermediate sweeps read and write the int64 values directly, and
+// the last sweep writes the exact stencil value correctly rounded to FP64.
+// Intermediate values are rounded once per sweep to the 2^-F grid (F >= 57 -
+// e(M), finer than an FP64 ulp of M).  Dirichlet boundary points keep their
+// FP64 bits in both buffers throughout (the first sweep copies them; later
+// sweeps write back the bits they read), so they are converted where they
+// are read as neighbours.
+#define JFX_IN_F64 1   // the sweep's input interior holds FP64
+#define JFX_OUT_F64 2  // the sweep writes FP64 (else int64 fixed point)
+
+JD i64 bits_i64(double d) { return (i64)__double_as_longlong(d); }
+JD double i64_bits(i64 q) { return __longlong_as_double(q); }
+
+// Raw 8-byte word -> fixed-point value: convert (FP64) or reinterpret (fixed).
+JD i64 fx_word(double raw, bool conv, int F) { return conv ? fx_from(raw, F) : bits_i64(raw); }
+
+// The conversion branch is guarded by a vote over the active lanes, so warps
+// with nothing to convert (interior warps of intermediate sweeps) skip it.
+template <int V>
+JD void fx_words(const double (&raw)[V], i64 (&w)[V], bool conv_all, unsigned conv_mask, int F) {
+#pragma unroll
+  for (int e = 0; e < V; ++e) w[e] = bits_i64(raw[e]);
+  if (__any_sync(__activemask(), conv_all || conv_mask != 0u)) {
+#pragma unroll
+    for (int e = 0; e < V; ++e)
+      if (conv_all || ((conv_mask >> e) & 1u)) w[e] = fx_from(raw[e], F);
+  }
+}
+
+// Round q * 2^-k to the nearest integer (ties up), k in [0, 62].
+JD i64 fx_round_shift(i64 q, int k) { return k ? ((q + ((i64)1 << (k - 1))) >> k) : q; }
+
+// (x + 2^(k-1)) >> k for a 128-bit x whose result fits in int64, k in [0, 62].
+JD i64 fx128_round_shift(s128 x, int k) {
+  if (k == 0) return (i64)x.lo;
+  s128 h;
+  h.lo = (u64)1 << (k - 1);
+  h.hi = 0;
+  x = add128(x, h);
+  return (i64)((x.lo >> k) | (x.hi << (64 - k)));
+}
+
+// Per-thread column facts of a tile: which of the thread's V columns are
+// interior (bit set) and which are boundary columns (x == 0 or nx-1).
+template <int V> JD void col_masks(i64 x0, i64 nx, unsigned& intm, unsigned& bndm) {
+  intm = 0;
+  bndm = 0;
+#pragma unroll
+  for (int e = 0; e < V; ++e) {
+    const i64 x = x0 + e;
+    if (x >= 1 && x <= nx - 2) intm |= 1u << e;
+    if (x == 0 || x == nx - 1) bndm |= 1u << e;
+  }
+}
+
+// ---------------------------------------------------------------- 5-point Jacobi, resident fixed point
+//
+// Same march as jacobi_march.  v 2^F = (S + 2) >> 2 with S the four
+// neighbours (exact); the FP64 output is fx_to(S, F + 2).  Residual: max
+// |S - 4u| (scale F, converted once per thread by the caller).
+template <int V, bool CG, bool OUTF>
+JD void jacobi_fx_march(const double* __restrict__ u, double* __restrict__ v, i64 nx, i64 ny, i64 x0, i64 ys, i64 ye,
+                        int F, int flags, u64& rmax) {
+  const int lane = threadIdx.x & 31;
+  const bool xin = x0 < nx;
+  const bool inf = flags & JFX_IN_F64;
+  unsigned intm, bndm;
+  col_masks<V>(x0, nx, intm, bndm);
+  double rup[V], rcur[V], rdn[V], rnx[V];
+  i64 up[V], cur[V], dn[V];
+#pragma unroll
+  for (int e = 0; e < V; ++e) rup[e] = rcur[e] = rdn[e] = rnx[e] = 0.0;
+  if (xin) {
+    if (ys >= 1) ldv<double, V, CG>(u + (ys - 1) * nx + x0, rup);
+    ldv<double, V, CG>(u + ys * nx + x0, rcur);
+    if (ys + 1 < ny) ldv<double, V, CG>(u + (ys + 1) * nx + x0, rdn);
+    if (ys + 2 < ny) ldv<double, V, CG>(u + (ys + 2) * nx + x0, rnx);
+  }
+  auto rowb = [&](i64 r) { return r == 0 || r == ny - 1; };
+  fx_words<V>(rup, up, inf || rowb(ys - 1), bndm, F);
+  fx_words<V>(rcur, cur, inf || rowb(ys), bndm, F);
+  fx_words<V>(rdn, dn, inf || rowb(ys + 1), bndm, F);
+  for (i64 y = ys; y < ye; ++y) {
+    i64 left = __shfl_up_sync(0xffffffffu, cur[V - 1], 1);
+    i64 right = __shfl_down_sync(0xffffffffu, cur[0], 1);
+    if (lane == 0 && xin && x0 >= 1)
+      left = fx_word(ld1<CG>(u + y * nx + x0 - 1), inf || rowb(y) || x0 - 1 == 0, F);
+    if (lane == 31 && xin && x0 + V < nx)
+      right = fx_word(ld1<CG>(u + y * nx + x0 + V), inf || rowb(y) || x0 + V == nx - 1, F);
+    double rnn[V];
+#pragma unroll
+    for (int e = 0; e < V; ++e) rnn[e] = 0.0;
+    if (xin && y + 3 < ny) ldv<double, V, CG>(u + (y + 3) * nx + x0, rnn);
+    const bool yint = (y >= 1) && (y <= ny - 2);
+    double out[V];
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      const i64 xl = (e == 0) ? left : cur[e - 1];
+      const i64 xr = (e == V - 1) ? right : cur[e + 1];
+      const bool in = yint && ((intm >> e) & 1u);
+      const i64 s = (up[e] + dn[e]) + (xl + xr);
+      double o;
+      if constexpr (OUTF) o = fx_to(s, F + 2);
+      else o = i64_bits((s + 2) >> 2);
+      out[e] = in ? o : rcur[e];
+      const i64 d = s - cur[e] * 4;
+      const u64 ad = (u64)(d ^ (d >> 63));  // |d| (one less for negative d: below the tolerance by 2^-F)
+      if (in && ad > rmax) rmax = ad;
+    }
+    if (xin) stv<double, V>(v + y * nx + x0, out);
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      up[e] = cur[e];
+      cur[e] = dn[e];
+      rcur[e] = rdn[e];
+      rdn[e] = rnx[e];
+      rnx[e] = rnn[e];
+    }
+    fx_words<V>(rdn, dn, inf || rowb(y + 2), bndm, F);
+  }
+}
+
+// ---------------------------------------------------------------- 7-point heat, resident fixed point
+//
+// S = the six faces, L = S - 6u (exact, scale F):
+//   JACC_FP_SMALL (r = fb 2^-k): q = fa u + fb S = u 2^k + fb L, scale F+k
+//   JACC_FP_WIDE  (r = m 2^-k):  q = u 2^k + m L in 128 bits, scale F+k
+// fixed output = round(q 2^-k); FP64 output = q correctly rounded; the
+// residual only needs max |L|.
+template <bool OUTF, int BX, int BY, int V, int ZC, class P>
+JD void heat3d_fx_body(const double* __restrict__ u, double* __restrict__ v, const P& p, int F, int flags, u64& rmax,
+                       Plane<i64, BX, BY, V>& sm) {
+  const i64 nx = p.nx, ny = p.ny, nz = p.nz;
+  const i64 sz = nx * ny;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const i64 bx0 = (i64)blockIdx.x * (BX * V);
+  const i64 by0 = (i64)blockIdx.y * BY;
+  const i64 x0 = bx0 + (i64)tx * V;
+  const i64 y = by0 + ty;
+  const bool act = (x0 < nx) && (y < ny);
+  const i64 cz0 = (i64)blockIdx.z * ZC;
+  const i64 cz1 = (cz0 + ZC < nz) ? cz0 + ZC : nz;
+  const bool inf = flags & JFX_IN_F64;
+  const double* urow = u + y * nx + x0;
+  double* vrow = v + y * nx + x0;
+
+  // Boundary planes (FP64 bits) are copied by the chunk that holds them.
+  if (act && cz0 == 0) { double t[V]; ldv<double, V>(urow, t); stv<double, V>(vrow, t); }
+  if (act && cz1 == nz) { double t[V]; ldv<double, V>(urow + (nz - 1) * sz, t); stv<double, V>(vrow + (nz - 1) * sz, t); }
+  const i64 z0 = cz0 < 1 ? 1 : cz0;
+  const i64 z1 = cz1 > nz - 1 ? nz - 1 : cz1;
+  if (z0 >= z1) return;  // block-uniform
+
+  unsigned intm, bndm;
+  col_masks<V>(x0, nx, intm, bndm);
+  const bool rowb = (y == 0) || (y == ny - 1);
+  const bool yint = act && !rowb;
+  // halo sources of this thread (fixed per CTA and thread)
+  const bool has_top = (ty == 0) && (by0 >= 1) && (x0 < nx);
+  const bool has_bot = (ty == BY - 1) && (by0 + BY < ny) && (x0 < nx);
+  const i64 hrow = has_top ? by0 - 1 : by0 + BY;
+  const bool hrowb = (hrow == 0) || (hrow == ny - 1);
+  const double* hyp = u + hrow * nx + x0;
+  const bool has_xl = (tx == 0) && (bx0 >= 1) && (y < ny);
+  const bool has_xr = (tx == BX - 1) && (bx0 + BX * V < nx) && (y < ny);
+  const i64 hcol = has_xl ? bx0 - 1 : bx0 + BX * V;
+  const bool hcolb = (hcol == 0) || (hcol == nx - 1);
+  const double* hxp = u + y * nx + hcol;
+
+  double rcur[V], rzn[V], rzn2[V], rzn3[V], hy[V], hyn[V], hyn2[V];
+  double hx = 0.0, hxn = 0.0, hxn2 = 0.0;
+  i64 zp[V], cur[V], zn[V];
+  {
+    double t[V];
+#pragma unroll
+    for (int e = 0; e < V; ++e) t[e] = rcur[e] = rzn[e] = rzn2[e] = rzn3[e] = hy[e] = hyn[e] = hyn2[e] = 0.0;
+    if (act) {
+      ldv<double, V>(urow + (z0 - 1) * sz, t);
+      ldv<double, V>(urow + z0 * sz, rcur);
+      ldv<double, V>(urow + (z0 + 1) * sz, rzn);
+      if (z0 + 2 < nz) ldv<double, V>(urow + (z0 + 2) * sz, rzn2);
+      if (z0 + 3 < nz) ldv<double, V>(urow + (z0 + 3) * sz, rzn3);
+    }
+    if (has_top || has_bot) {
+      ldv<double, V>(hyp + z0 * sz, hy);
+      if (z0 + 1 < z1) ldv<double, V>(hyp + (z0 + 1) * sz, hyn);
+    }
+    if (has_xl || has_xr) {
+      hx = __ldg(hxp + z0 * sz);
+      if (z0 + 1 < z1) hxn = __ldg(hxp + (z0 + 1) * sz);
+    }
+    fx_words<V>(t, zp, inf || rowb || z0 - 1 == 0, bndm, F);
+    fx_words<V>(rcur, cur, inf || rowb, bndm, F);
+  }
+  const i64 fb = p.fb, fw0 = p.fw0;
+  const int k = p.fk;
+  const bool small = p.fpath == JACC_FP_SMALL;
+  // warps whose every point is interior take a branch-free path
+  const bool allint = !act || (yint && intm == (1u << V) - 1u);
+  const bool warp_int = __all_sync(0xffffffffu, allint) && __any_sync(0xffffffffu, act);
+  int b = 0;
+  i64 zoff = z0 * sz;
+  for (i64 z = z0; z < z1; ++z, zoff += sz) {
+    fx_words<V>(rzn, zn, inf || rowb || z + 1 == nz - 1, bndm, F);
+    // loads two planes ahead: own plane z+4, halo of plane z+2
+    double rn4[V];
+#pragma unroll
+    for (int e = 0; e < V; ++e) rn4[e] = 0.0;
+    if (act && z + 4 < nz) ldv<double, V>(urow + zoff + 4 * sz, rn4);
+    if (z + 2 < z1) {
+      if (has_top || has_bot) ldv<double, V>(hyp + zoff + 2 * sz, hyn2);
+      if (has_xl || has_xr) hxn2 = __ldg(hxp + zoff + 2 * sz);
+    }
+    // this plane into shared memory (converted)
+    i64* row = &sm.a[b][ty + 1][V + tx * V];
+#pragma unroll
+    for (int e = 0; e < V; ++e) row[e] = cur[e];
+    if (has_top || has_bot) {
+      i64 w[V];
+      fx_words<V>(hy, w, inf || hrowb, bndm, F);
+      i64* hr = &sm.a[b][has_top ? 0 : BY + 1][V + tx * V];
+#pragma unroll
+      for (int e = 0; e < V; ++e) hr[e] = w[e];
+    }
+    if (has_xl) sm.a[b][ty + 1][V - 1] = fx_word(hx, inf || rowb || hcolb, F);
+    if (has_xr) sm.a[b][ty + 1][V + BX * V] = fx_word(hx, inf || rowb || hcolb, F);
+    __syncthreads();
+    const i64* rm = &sm.a[b][ty][V + tx * V];
+    const i64* r0 = &sm.a[b][ty + 1][V + tx * V];
+    const i64* rp = &sm.a[b][ty + 2][V + tx * V];
+    double out[V];
+    // v = u + round(r L) with L = S - 6u exact; FP64 output: u + r L correctly rounded
+    auto point = [&](int e, bool in) {
+      const i64 xl = (e == 0) ? r0[-1] : cur[e - 1];
+      const i64 xr = (e == V - 1) ? r0[V] : cur[e + 1];
+      const i64 sum = ((xl + xr) + (rm[e] + rp[e])) + (zp[e] + zn[e]);
+      const i64 L = sum - 6 * cur[e];
+      double o;
+      if constexpr (OUTF) {
+        if (small) o = fx_to(cur[e] * ((i64)1 << k) + fb * L, F + k);
+        else o = fx128_to(add128(from_s64_shl(cur[e], k), mul_s64_u64(L, (u64)fw0)), F + k);
+      } else {
+        if (small) o = i64_bits(cur[e] + fx_round_shift(fb * L, k));
+        else o = i64_bits(cur[e] + fx128_round_shift(mul_s64_u64(L, (u64)fw0), k));
+      }
+      out[e] = in ? o : rcur[e];
+      const u64 aL = (u64)(L ^ (L >> 63));  // |L| (one less for negative L: 2^-F, below the tolerance)
+      rmax = (in && aL > rmax) ? aL : rmax;
+    };
+    if (warp_int) {
+#pragma unroll
+      for (int e = 0; e < V; ++e) point(e, true);
+    } else {
+#pragma unroll
+      for (int e = 0; e < V; ++e) point(e, yint && ((intm >> e) & 1u));
+    }
+    if (act) stv<double, V>(vrow + zoff, out);
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      zp[e] = cur[e];
+      cur[e] = zn[e];
+      rcur[e] = rzn[e];
+      rzn[e] = rzn2[e];
+      rzn2[e] = rzn3[e];
+      rzn3[e] = rn4[e];
+      hy[e] = hyn[e];
+      hyn[e] = hyn2[e];
+    }
+    hx = hxn;
+    hxn = hxn2;
+    b ^= 1;
+  }
+}
+
+// ---------------------------------------------------------------- 27-point box, resident fixed point
+//
+// v 2^F = round(sum_j fw_j class_j 2^-K) from the exact 128-bit sum; the FP64
+// output is the 128-bit sum correctly rounded.  Periodic: no boundary, every
+// point is updated.  The field sum accumulates the fixed outputs exactly in
+// 128 bits per thread.
+template <int BX, int BY, int V>
+JD void fx_plane_load_put(const double* __restrict__ u, i64 nx, i64 ny, i64 nz, i64 z, i64 bx0, i64 by0,
+                          const double* urow, Plane<i64, BX, BY, V>& sm, int b, int F, bool inf) {
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const i64 zz = (z % nz + nz) % nz;
+  const double* pl = u + zz * nx * ny;
+  double r[V];
+  ldv<double, V>(urow + zz * nx * ny, r);
+  i64 w[V];
+  fx_words<V>(r, w, inf, 0u, F);
+  i64* row = &sm.a[b][ty + 1][V + tx * V];
+#pragma unroll
+  for (int e = 0; e < V; ++e) row[e] = w[e];
+  const i64 x0 = (bx0 + (i64)tx * V) % nx;
+  if (ty == 0 || ty == BY - 1) {
+    const i64 yy = ty == 0 ? (by0 - 1 + ny) % ny : (by0 + BY) % ny;
+    double h[V];
+    ldv<double, V>(pl + yy * nx + x0, h);
+    fx_words<V>(h, w, inf, 0u, F);
+    i64* hr = &sm.a[b][ty == 0 ? 0 : BY + 1][V + tx * V];
+#pragma unroll
+    for (int e = 0; e < V; ++e) hr[e] = w[e];
+  }
+  const i64 yy = (by0 + ty) % ny;
+  if (tx == 0) sm.a[b][ty + 1][V - 1] = fx_word(__ldg(pl + yy * nx + (bx0 - 1 + nx) % nx), inf, F);
+  if (tx == BX - 1) sm.a[b][ty + 1][V + BX * V] = fx_word(__ldg(pl + yy * nx + (bx0 + BX * V) % nx), inf, F);
+  if (tx == 0 && ty == 0) {
+    const i64 xl = (bx0 - 1 + nx) % nx, xr = (bx0 + BX * V) % nx;
+    const i64 yt = (by0 - 1 + ny) % ny, yb = (by0 + BY) % ny;
+    sm.a[b][0][V - 1] = fx_word(__ldg(pl + yt * nx + xl), inf, F);
+    sm.a[b][0][V + BX * V] = fx_word(__ldg(pl + yt * nx + xr), inf, F);
+    sm.a[b][BY + 1][V - 1] = fx_word(__ldg(pl + yb * nx + xl), inf, F);
+    sm.a[b][BY + 1][V + BX * V] = fx_word(__ldg(pl + yb * nx + xr), inf, F);
+  }
+}
+
+template <bool OUTF, int BX, int BY, int V, int ZC, class P>
+JD void box27_fx_body(const double* __restrict__ u, double* __restrict__ v, const P& p, int F, int flags, s128& acc,
+                      Plane<i64, BX, BY, V>& sm) {
+  const i64 nx = p.nx, ny = p.ny, nz = p.nz;
+  const i64 sz = nx * ny;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const i64 bx0 = (i64)blockIdx.x * (BX * V);
+  const i64 by0 = (i64)blockIdx.y * BY;
+  const i64 x0 = bx0 + (i64)tx * V;
+  const i64 y = by0 + ty;
+  const bool act = (x0 < nx) && (y < ny);
+  const i64 z0 = (i64)blockIdx.z * ZC;
+  const i64 z1 = (z0 + ZC < nz) ? z0 + ZC : nz;
+  const bool inf = flags & JFX_IN_F64;
+  const double* urow = u + (y % ny) * nx + (x0 % nx);  // periodic image for overhanging threads
+  double* vrow = v + y * nx + x0;
+  const i64 w0 = p.fw0, w1 = p.fw1, w2 = p.fw2, w3 = p.fw3;
+  const int K = p.fk;
+
+  i64 cm[V], fm[V], gm[V], c0[V], f0[V], g0[V];
+  int b = 0;
+  fx_plane_load_put<BX, BY, V>(u, nx, ny, nz, z0 - 1, bx0, by0, urow, sm, b, F, inf);
+  __syncthreads();
+  plane_cfe<double, BX, BY, V, JM_FIXED>(sm, b, cm, fm, gm);
+  b ^= 1;
+  fx_plane_load_put<BX, BY, V>(u, nx, ny, nz, z0, bx0, by0, urow, sm, b, F, inf);
+  __syncthreads();
+  plane_cfe<double, BX, BY, V, JM_FIXED>(sm, b, c0, f0, g0);
+  b ^= 1;
+  for (i64 z = z0; z < z1; ++z) {
+    fx_plane_load_put<BX, BY, V>(u, nx, ny, nz, z + 1, bx0, by0, urow, sm, b, F, inf);
+    __syncthreads();
+    i64 cn[V], fn[V], gn[V];
+    plane_cfe<double, BX, BY, V, JM_FIXED>(sm, b, cn, fn, gn);
+    double out[V];
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      s128 a = mul_s64_u64(c0[e], (u64)w0);
+      a = add128(a, mul_s64_u64((f0[e] + cm[e]) + cn[e], (u64)w1));
+      a = add128(a, mul_s64_u64((g0[e] + fm[e]) + fn[e], (u64)w2));
+      a = add128(a, mul_s64_u64(gm[e] + gn[e], (u64)w3));
+      const i64 q = fx128_round_shift(a, K);
+      if constexpr (OUTF) out[e] = fx128_to(a, F + K);
+      else out[e] = i64_bits(q);
+      if (act) {
+        s128 t;
+        t.lo = (u64)q;
+        t.hi = (u64)(q >> 63);
+        acc = add128(acc, t);
+      }
+    }
+    if (act) stv<double, V>(vrow + z * sz, out);
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      cm[e] = c0[e]; fm[e] = f0[e]; gm[e] = g0[e];
+      c0[e] = cn[e]; f0[e] = fn[e]; g0[e] = gn[e];
+    }
+    b ^= 1;
+  }
+}
+
 // ====================================================================== kernels
 //
 // Every stencil kernel has the signature
-//   (const T* u, T* v, P p, double* resid, const u64* maxword)
+//   (const T* u, T* v, P p, double* resid, const u64* maxword, int flags)
 // resid (nullable) receives the fused reduction via one atomic per CTA (it
 // must be zeroed before the launch); maxword (FP64 only, nullable) holds the
 // bit pattern of max|u| written by jacc_k_maxabs, which selects the fixed
 // point scale.  With maxword NULL or fpath NONE the native path runs.
+// flags (JFX_*) say whether this sweep of a sequence reads and writes FP64
+// or the resident fixed-point representation; native paths ignore them.  The
+// FP64 output of the fixed-point path is the template parameter OUTF, so
+// intermediate sweeps run an instantiation without the conversion code.
 
-template <class T, int BX, int BY, int V, int ZC, class P>
-JD void jacobi2d_entry(const T* __restrict__ u, T* __restrict__ v, const P& p, double* resid, const u64* maxword) {
+template <class T, int BX, int BY, int V, int ZC, bool OUTF, class P>
+JD void jacobi2d_entry(const T* __restrict__ u, T* __restrict__ v, const P& p, double* resid, const u64* maxword,
+                       int flags) {
   u64 bits = 0;
+  const i64 x0 = (i64)blockIdx.x * (BX * V) + (i64)threadIdx.x * V;
+  const i64 ys = ((i64)blockIdx.y * BY + threadIdx.y) * ZC;
+  const i64 ye = (ys + ZC < p.ny) ? ys + ZC : p.ny;
   if constexpr (sizeof(T) == 8) {
     const int F = (maxword && p.fpath != JACC_FP_NONE) ? fx_frac_bits(*maxword) : -1;
     if (F >= 0) {
       u64 m = 0;
-      jacobi2d_body<T, BX, BY, V, ZC, JM_FIXED>(u, v, p, F, m);
+      if (ys < p.ny) jacobi_fx_march<V, false, OUTF>(u, v, p.nx, p.ny, x0, ys, ye, F, flags, m);
       bits = dbits(fx_to_u(m, F + 2));
     } else {
       double m = 0.0;
-      jacobi2d_body<T, BX, BY, V, ZC, JM_NATIVE>(u, v, p, -1, m);
+      if (ys < p.ny) jacobi_march<T, V, JM_NATIVE, false>(u, v, p.nx, p.ny, x0, ys, ye, -1, m);
       bits = dbits(m);
     }
   } else {
     T m = T(0);
-    jacobi2d_body<T, BX, BY, V, ZC, JM_NATIVE>(u, v, p, -1, m);
+    if (ys < p.ny) jacobi_march<T, V, JM_NATIVE, false>(u, v, p.nx, p.ny, x0, ys, ye, -1, m);
     bits = dbits((double)m);
   }
   block_max_to<BX * BY>(bits, resid);
 }
 
-template <class T, int BX, int BY, int V, int ZC, class P>
-JD void heat3d_entry(const T* __restrict__ u, T* __restrict__ v, const P& p, double* resid, const u64* maxword) {
+template <class T, int BX, int BY, int V, int ZC, bool OUTF, class P>
+JD void heat3d_entry(const T* __restrict__ u, T* __restrict__ v, const P& p, double* resid, const u64* maxword,
+                     int flags) {
   u64 bits = 0;
   if constexpr (sizeof(T) == 8) {
     const int F = (maxword && p.fpath != JACC_FP_NONE) ? fx_frac_bits(*maxword) : -1;
     __shared__ __align__(16) unsigned char raw[sizeof(Plane<i64, BX, BY, V>)];
     if (F >= 0) {
       u64 m = 0;
-      heat3d_body<T, BX, BY, V, ZC, JM_FIXED>(u, v, p, F, m, *reinterpret_cast<Plane<i64, BX, BY, V>*>(raw));
+      heat3d_fx_body<OUTF, BX, BY, V, ZC>(u, v, p, F, flags, m, *reinterpret_cast<Plane<i64, BX, BY, V>*>(raw));
       bits = dbits(heat_resid_fixed(p, m, F));
     } else {
       double m = 0.0;
@@ -722,22 +1339,30 @@ JD void heat3d_entry(const T* __restrict__ u, T* __restrict__ v, const P& p, dou
   block_max_to<BX * BY>(bits, resid);
 }
 
-template <class T, int BX, int BY, int V, int ZC, class P>
-JD void box27_entry(const T* __restrict__ u, T* __restrict__ v, const P& p, double* resid, const u64* maxword) {
-  SumAcc<T> acc;
+template <class T, int BX, int BY, int V, int ZC, bool OUTF, class P>
+JD void box27_entry(const T* __restrict__ u, T* __restrict__ v, const P& p, double* resid, const u64* maxword,
+                    int flags) {
+  double total = 0.0;
   if constexpr (sizeof(T) == 8) {
     const int F = (maxword && p.fpath != JACC_FP_NONE) ? fx_frac_bits(*maxword) : -1;
     __shared__ __align__(16) unsigned char raw[sizeof(Plane<i64, BX, BY, V>)];
     if (F >= 0) {
-      box27_body<T, BX, BY, V, ZC, JM_FIXED>(u, v, p, F, acc, *reinterpret_cast<Plane<i64, BX, BY, V>*>(raw));
+      s128 acc;
+      acc.lo = acc.hi = 0ull;
+      box27_fx_body<OUTF, BX, BY, V, ZC>(u, v, p, F, flags, acc, *reinterpret_cast<Plane<i64, BX, BY, V>*>(raw));
+      total = fx128_to(acc, F);
     } else {
-      box27_body<T, BX, BY, V, ZC, JM_NATIVE>(u, v, p, -1, acc, *reinterpret_cast<Plane<double, BX, BY, V>*>(raw));
+      SumAcc<T> acc;
+      box27_body2<T, BX, BY, V, ZC>(u, v, p, acc, resid != nullptr, *reinterpret_cast<Plane<double, BX, BY, V>*>(raw));
+      total = acc.total();
     }
   } else {
     __shared__ Plane<T, BX, BY, V> sm;
-    box27_body<T, BX, BY, V, ZC, JM_NATIVE>(u, v, p, -1, acc, sm);
+    SumAcc<T> acc;
+    box27_body2<T, BX, BY, V, ZC>(u, v, p, acc, resid != nullptr, sm);
+    total = acc.total();
   }
-  block_sum_to<BX * BY>(acc.total(), resid);
+  block_sum_to<BX * BY>(total, resid);
 }
 
 #ifdef JACC_AUX_KERNELS
@@ -779,18 +1404,23 @@ __global__ void jacc_k_fill_skipped(double* resid, int n, int T) {
 #endif  // JACC_AUX_KERNELS
 
 // Kernel templates instantiated by the precompiled library (P = JParams).
-template <class T, int BX, int BY, int V, int ZC>
+template <class T, int BX, int BY, int V, int ZC, bool OUTF>
 __global__ void __launch_bounds__(BX * BY) jacc_k_jacobi2d(const T* __restrict__ u, T* __restrict__ v, JParams p,
-                                                           double* resid, const u64* maxword) {
-  jacobi2d_entry<T, BX, BY, V, ZC>(u, v, p, resid, maxword);
+                                                           double* resid, const u64* maxword, int flags) {
+  jacobi2d_entry<T, BX, BY, V, ZC, OUTF>(u, v, p, resid, maxword, flags);
 }
-template <class T, int BX, int BY, int V, int ZC>
+template <class T, int BX, int BY, int V, int ZC, bool OUTF>
 __global__ void __launch_bounds__(BX * BY) jacc_k_heat3d(const T* __restrict__ u, T* __restrict__ v, JParams p,
-                                                         double* resid, const u64* maxword) {
-  heat3d_entry<T, BX, BY, V, ZC>(u, v, p, resid, maxword);
+                                                         double* resid, const u64* maxword, int flags) {
+  heat3d_entry<T, BX, BY, V, ZC, OUTF>(u, v, p, resid, maxword, flags);
 }
-template <class T, int BX, int BY, int V, int ZC>
+template <int RY, int TT, int ZC>
+__global__ void __launch_bounds__(TB_BX * RY) jacc_k_box27_tb(const float* __restrict__ u, float* __restrict__ v,
+                                                              JParams p, double* resid, const u64* maxword, int flags) {
+  box27_tb_entry<RY, TT, ZC>(u, v, p, resid);
+}
+template <class T, int BX, int BY, int V, int ZC, bool OUTF>
 __global__ void __launch_bounds__(BX * BY) jacc_k_box27(const T* __restrict__ u, T* __restrict__ v, JParams p,
-                                                        double* resid, const u64* maxword) {
-  box27_entry<T, BX, BY, V, ZC>(u, v, p, resid, maxword);
+                                                        double* resid, const u64* maxword, int flags) {
+  box27_entry<T, BX, BY, V, ZC, OUTF>(u, v, p, resid, maxword, flags);
 }

@@ -81,5 +81,6 @@ extern "C" jacc_status jacc_launch_static(jacc_kernel h, const void* u_in, void*
     jacc_status st = cuda_check(cudaMemsetAsync(resid_dev, 0, sizeof(double), s), "cudaMemsetAsync(resid)");
     if (st) return st;
   }
-  return cuda_check(jacc::launch_sweep_kernel(k, u_in, u_out, resid_dev, mw, s), "stencil launch");
+  return cuda_check(jacc::launch_sweep_kernel(k, u_in, u_out, resid_dev, mw, jacc::kFxIn | jacc::kFxOut, s),
+                    "stencil launch");
 }

@@ -158,3 +158,32 @@ def box27_weights():
     Raw sum = 1/2 + 6/24 + 12/96 + 8/192 = 11/12, so the scaled weights are
     6/11, 1/22, 1/88, 1/176, rounded to FP32."""
     return np.array([6.0 / 11.0, 1.0 / 22.0, 1.0 / 88.0, 1.0 / 176.0], dtype=np.float32)
+
+
+# ----------------------------------------------------------------------------- cost-model inputs
+
+MLP_NPARAM = 8705
+
+
+def mlp_init(seed=5):
+    """Kaiming-uniform parameters (He et al. 2015) for the 4-64-64-64-1 ReLU MLP:
+    weights U(-sqrt(6/fan_in), sqrt(6/fan_in)) drawn in layer order from stream 0
+    of `seed`, biases 0; FP32.  Layout W1[64][4] b1 W2[64][64] b2 W3[64][64] b3 W4[64] b4."""
+    fan = (4, 64, 64, 64)
+    off = (0, 320, 4480, 8640)
+    cnt = (256, 4096, 4096, 64)
+    u = uniform64(seed, sum(cnt))
+    p = np.zeros(MLP_NPARAM, dtype=np.float32)
+    k = 0
+    for f, o, c in zip(fan, off, cnt):
+        b = math.sqrt(6.0 / f)
+        p[o:o + c] = ((2.0 * u[k:k + c] - 1.0) * b).astype(np.float32)
+        k += c
+    return p
+
+
+def mlp_dataset(seed, n):
+    """Synthetic regression set: x ~ U[0,1)^4 (FP32), target a smooth function of x."""
+    x = uniform64(seed, 4 * n).reshape(n, 4)
+    y = np.sin(3.0 * x[:, 0]) + x[:, 1] ** 2 - x[:, 2] * x[:, 3] + 0.5 * x[:, 3]
+    return x.astype(np.float32), y.astype(np.float32)

@@ -75,6 +75,11 @@ class BatchConfig(C.Structure):
                 ("timeout_ms", C.c_int32), ("test_stall_ticket", C.c_int64)]
 
 
+class TuneResult(C.Structure):
+    _fields_ = [("ms", C.c_double * NUM_TILES), ("valid", C.c_int32 * NUM_TILES), ("best_tile", C.c_int32),
+                ("reserved", C.c_int32), ("best_ms", C.c_double)]
+
+
 class Tile(C.Structure):
     _fields_ = [("bx", C.c_int32), ("by", C.c_int32), ("vec16", C.c_int32), ("zc", C.c_int32)]
 
@@ -100,6 +105,21 @@ SIGNATURES = {
     "jacc_batch_status": ([P, C.c_size_t], C.c_int32),
     "jacc_batch_tune": ([P, C.c_int32, C.c_size_t, P, P], C.c_int32),
     "jacc_batch_release": ([P], C.c_int32),
+    "jacc_autotune": ([P, P, P, C.c_int32, C.c_int32, C.c_size_t, P], C.c_int32),
+    "jacc_autotune_forget": ([], C.c_int32),
+    "jacc_costmodel_features": ([C.c_int32, C.c_double, C.c_int32, C.c_int32, P], C.c_int32),
+    "jacc_costmodel_create": ([P, C.c_uint64, P], C.c_int32),
+    "jacc_costmodel_set_params": ([P, P], C.c_int32),
+    "jacc_costmodel_get_params": ([P, P], C.c_int32),
+    "jacc_costmodel_loss_grad": ([P, P, P, C.c_int32, P, P, C.c_size_t], C.c_int32),
+    "jacc_costmodel_train": ([P, P, P, C.c_int32, C.c_int32, C.c_float, C.c_size_t, P], C.c_int32),
+    "jacc_costmodel_predict": ([P, P, C.c_int32, P, C.c_size_t], C.c_int32),
+    "jacc_costmodel_pick": ([P, P, P, C.c_int32, P, P, P, C.c_size_t], C.c_int32),
+    "jacc_costmodel_set_range": ([P, C.c_double, C.c_double, C.c_double], C.c_int32),
+    "jacc_costmodel_choose": ([P, P, P, P, C.c_size_t, P, P], C.c_int32),
+    "jacc_costmodel_save": ([P, C.c_char_p], C.c_int32),
+    "jacc_costmodel_load": ([P, C.c_char_p], C.c_int32),
+    "jacc_costmodel_release": ([P], C.c_int32),
 }
 
 _lib = None
@@ -172,8 +192,8 @@ def tile_info(tile_id):
     return dict(bx=t.bx, by=t.by, vec16=bool(t.vec16), zc=t.zc)
 
 
-class Kernel:
-    """A specialised stencil kernel (owns one reference to the library handle)."""
+class Desc:
+    """A kernel descriptor (jacc_kernel_desc) and the field shape it implies."""
 
     def __init__(self, stencil, dtype, nx, ny, nz=1, coeffs=(0.0, 0.0, 0.0, 0.0), tile_id=-1, jit=False,
                  arith=ARITH_AUTO, boundary=None, tblock=0):
@@ -189,11 +209,18 @@ class Kernel:
         d.arith = arith
         d.flags = SPEC_JIT if jit else 0
         d.tblock = tblock
-        h = C.c_void_p()
-        _check(lib().jacc_specialize(C.byref(d), C.byref(h)))
-        self.handle = h
         self.desc = d
         self.shape = (ny, nx) if stencil == STENCIL_5PT else (nz, ny, nx)
+
+
+class Kernel(Desc):
+    """A specialised stencil kernel (owns one reference to the library handle)."""
+
+    def __init__(self, *args, **kw):
+        super().__init__(*args, **kw)
+        h = C.c_void_p()
+        _check(lib().jacc_specialize(C.byref(self.desc), C.byref(h)))
+        self.handle = h
 
     def info(self):
         i = KernelInfo()
@@ -340,5 +367,137 @@ class Batch:
         try:
             if self.handle and _lib is not None:
                 _lib.jacc_batch_release(self.handle)
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------------------------------- autotuner
+
+def autotune(k_args, u0, u1, sweeps_per_rep=2, reps=3, stream=None):
+    """Exhaustive tile search for the descriptor Kernel(**k_args) (tile_id ignored).
+
+    Returns dict(ms=[24 floats, inf if invalid], valid=[24 bools], best_tile, best_ms)."""
+    k = Desc(**dict(k_args, tile_id=-1))
+    r = TuneResult()
+    _check(lib().jacc_autotune(C.byref(k.desc), _field(k, u0, "u0"), _field(k, u1, "u1"), sweeps_per_rep, reps,
+                               _stream(stream), C.byref(r)))
+    return dict(ms=list(r.ms), valid=[bool(v) for v in r.valid], best_tile=r.best_tile, best_ms=r.best_ms)
+
+
+def autotune_forget():
+    _check(lib().jacc_autotune_forget())
+
+
+# ----------------------------------------------------------------------------- learned cost model
+
+MLP_NPARAM = 8705
+
+
+def features(stencil, side, dtype, tile):
+    out = (C.c_float * 4)()
+    _check(lib().jacc_costmodel_features(stencil, float(side), dtype, tile, out))
+    return list(out)
+
+
+def _f32(t, n=None, name="tensor"):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA float32 tensor")
+    if n is not None and t.numel() < n:
+        raise ValueError(f"{name} needs {n} elements")
+    return t.data_ptr()
+
+
+class CostModel:
+    """The MLP cost model; parameters live on the device."""
+
+    def __init__(self, init_params=None, seed=5):
+        import numpy as np
+        h = C.c_void_p()
+        if init_params is not None:
+            p = np.ascontiguousarray(init_params, dtype=np.float32)
+            assert p.size == MLP_NPARAM
+            _check(lib().jacc_costmodel_create(p.ctypes.data_as(P), seed, C.byref(h)))
+        else:
+            _check(lib().jacc_costmodel_create(None, seed, C.byref(h)))
+        self.handle = h
+
+    def params(self):
+        import numpy as np
+        p = np.empty(MLP_NPARAM, dtype=np.float32)
+        _check(lib().jacc_costmodel_get_params(self.handle, p.ctypes.data_as(P)))
+        return p
+
+    def set_params(self, p):
+        import numpy as np
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(lib().jacc_costmodel_set_params(self.handle, p.ctypes.data_as(P)))
+
+    def loss_grad(self, x, y, stream=None):
+        import torch
+        n = y.numel()
+        g = torch.empty(MLP_NPARAM, dtype=torch.float32, device=x.device)
+        loss = torch.empty(1, dtype=torch.float32, device=x.device)
+        _check(lib().jacc_costmodel_loss_grad(self.handle, _f32(x, 4 * n, "x"), _f32(y, n, "y"), n, g.data_ptr(),
+                                              loss.data_ptr(), _stream(stream)))
+        return loss, g
+
+    def train(self, x, y, epochs, lr=1e-3, stream=None):
+        import torch
+        n = y.numel()
+        loss = torch.empty(1, dtype=torch.float32, device=x.device)
+        _check(lib().jacc_costmodel_train(self.handle, _f32(x, 4 * n, "x"), _f32(y, n, "y"), n, epochs, lr,
+                                          _stream(stream), loss.data_ptr()))
+        return loss
+
+    def predict(self, x, stream=None):
+        import torch
+        n = x.numel() // 4
+        y = torch.empty(n, dtype=torch.float32, device=x.device)
+        _check(lib().jacc_costmodel_predict(self.handle, _f32(x, 4 * n, "x"), n, y.data_ptr(), _stream(stream)))
+        return y
+
+    def pick(self, feats, valid, stream=None):
+        """feats [nq, 24, 4] float32, valid [nq, 24] int32 (CUDA) -> (pred, pick, gap)."""
+        import torch
+        nq = feats.shape[0]
+        pred = torch.empty(nq * NUM_TILES, dtype=torch.float32, device=feats.device)
+        pick = torch.empty(nq, dtype=torch.int32, device=feats.device)
+        gap = torch.empty(nq, dtype=torch.float32, device=feats.device)
+        if valid.dtype != torch.int32 or not valid.is_cuda or not valid.is_contiguous():
+            raise ValueError("valid must be a contiguous CUDA int32 tensor")
+        _check(lib().jacc_costmodel_pick(self.handle, _f32(feats, nq * NUM_TILES * 4, "feats"), valid.data_ptr(), nq,
+                                         pred.data_ptr(), pick.data_ptr(), gap.data_ptr(), _stream(stream)))
+        return pred.view(nq, NUM_TILES), pick, gap
+
+    def set_range(self, side_lo, side_hi, margin):
+        _check(lib().jacc_costmodel_set_range(self.handle, side_lo, side_hi, margin))
+
+    def choose(self, k_args, u0=None, u1=None, stream=None):
+        """(tile, used_fallback) for the descriptor Kernel(**k_args)."""
+        k = Desc(**dict(k_args, tile_id=-1))
+        p0 = _field(k, u0, "u0") if u0 is not None else None
+        p1 = _field(k, u1, "u1") if u1 is not None else None
+        t = C.c_int32(-1)
+        fb = C.c_int32(0)
+        _check(lib().jacc_costmodel_choose(self.handle, C.byref(k.desc), p0, p1, _stream(stream), C.byref(t),
+                                           C.byref(fb)))
+        return t.value, bool(fb.value)
+
+    def save(self, path):
+        _check(lib().jacc_costmodel_save(self.handle, path.encode()))
+
+    def load(self, path):
+        _check(lib().jacc_costmodel_load(self.handle, path.encode()))
+
+    def release(self):
+        if self.handle:
+            _check(lib().jacc_costmodel_release(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            if self.handle and _lib is not None:
+                _lib.jacc_costmodel_release(self.handle)
         except Exception:
             pass

@@ -1,0 +1,169 @@
+"""GPU parity of the learned cost model (forward, gradients, Adam) against the
+FP64 oracle, the pick kernel, persistence, the autotuner, and what the trained
+network gains over the method without it."""
+import math
+import os
+import tempfile
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2110_14340_gb300 import costmodel, inputs, jacc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2110_14340_gb300 import build
+    build.build()
+    jacc.lib()
+
+
+def nerr(g, o):
+    g = np.asarray(g, dtype=np.float64)
+    o = np.asarray(o, dtype=np.float64)
+    return float(np.max(np.abs(g - o)) / np.max(np.abs(o)))
+
+
+def test_library_initialiser_equals_the_published_generator():
+    m = jacc.CostModel(seed=5)
+    assert np.array_equal(m.params(), inputs.mlp_init(5))
+    assert np.all(m.params()[[256 + i for i in range(64)]] == 0.0)  # b1
+
+
+def test_forward_and_gradient_match_oracle(orc):
+    p = inputs.mlp_init(7)
+    x, y = inputs.mlp_dataset(3, 203)  # ragged against the 32-sample chunks
+    m = jacc.CostModel(init_params=p)
+    xt, yt = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    pred = m.predict(xt).cpu().numpy()
+    p64 = p.astype(np.float64)
+    assert nerr(pred, orc.mlp_forward(p64, x.astype(np.float64))) <= 1e-5
+    loss, g = m.loss_grad(xt, yt)
+    lo, go = orc.mlp_loss_grad(p64, x.astype(np.float64), y.astype(np.float64))
+    assert abs(loss.item() - lo) <= 1e-5 * abs(lo)
+    assert nerr(g.cpu().numpy(), go) <= 1e-4
+    # per layer as well, so a small layer cannot hide behind a large one
+    for a, b in ((0, 256), (256, 320), (320, 4416), (4416, 4480), (4480, 8576), (8576, 8640), (8640, 8704)):
+        assert nerr(g.cpu().numpy()[a:b], go[a:b]) <= 1e-3, (a, b)
+
+
+def test_adam_step_matches_oracle(orc):
+    p = inputs.mlp_init(9)
+    x, y = inputs.mlp_dataset(4, 96)
+    m = jacc.CostModel(init_params=p)
+    m.train(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(), epochs=1, lr=1e-3)
+    got = m.params().astype(np.float64)
+    p64 = p.astype(np.float64)
+    _, go = orc.mlp_loss_grad(p64, x.astype(np.float64), y.astype(np.float64))
+    want = p64.copy()
+    mm = np.zeros_like(want)
+    vv = np.zeros_like(want)
+    orc.adam_step(want, go, mm, vv, 1, lr=1e-3)
+    big = np.abs(go) > 1e-3 * np.max(np.abs(go))
+    assert np.max(np.abs((got - p64)[big] - (want - p64)[big])) <= 1e-6
+    assert np.max(np.abs(got - p64)) <= 1e-3 * 1.0001  # every step is at most lr
+
+
+def test_training_reduces_loss_and_pick_is_the_argmin():
+    x, y = inputs.mlp_dataset(5, 1024)
+    m = jacc.CostModel(seed=5)
+    xt, yt = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    l0, _ = m.loss_grad(xt, yt)
+    m.train(xt, yt, epochs=1500, lr=1e-3)
+    l1, _ = m.loss_grad(xt, yt)
+    assert l1.item() < 0.05 * l0.item()
+    rng = np.random.default_rng(0)
+    F = rng.uniform(0, 1, (37, 24, 4)).astype(np.float32)
+    V = (rng.uniform(0, 1, (37, 24)) > 0.3).astype(np.int32)
+    V[5] = 0  # a query with no valid tile
+    pred, pick, gap = m.pick(torch.from_numpy(F).cuda(), torch.from_numpy(V).cuda())
+    pr = pred.cpu().numpy()
+    pk = pick.cpu().numpy()
+    for q in range(37):
+        if V[q].sum() == 0:
+            assert pk[q] == -1
+            continue
+        vals = np.where(V[q] == 1, pr[q], np.inf)
+        assert pk[q] == int(np.argmin(vals))
+        s = np.sort(vals)
+        if np.isfinite(s[1]):
+            assert gap.cpu().numpy()[q] == np.float32(s[1] - s[0])
+
+
+def test_save_load_roundtrip():
+    m = jacc.CostModel(seed=11)
+    m.set_range(256.0, 1024.0, 0.01)
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "m.bin")
+        m.save(path)
+        m2 = jacc.CostModel(seed=1)
+        m2.load(path)
+        assert np.array_equal(m2.params(), m.params())
+        with open(path, "r+b") as f:
+            f.write(b"XXXX")
+        with pytest.raises(jacc.JaccError):
+            m2.load(path)
+
+
+def test_autotuner_remembers_its_pick():
+    nx = ny = nz = 96
+    a = torch.rand(nz, ny, nx, dtype=torch.float64, device="cuda")
+    b = torch.empty_like(a)
+    jacc.autotune_forget()
+    args = dict(stencil=7, dtype=64, nx=nx, ny=ny, nz=nz, coeffs=(0.125,))
+    r = jacc.autotune(args, a, b, sweeps_per_rep=1, reps=5)
+    ms = np.asarray(r["ms"])
+    assert all(r["valid"]) and r["best_tile"] == int(np.argmin(ms)) and r["best_ms"] == ms.min()
+    k = jacc.Kernel(**args)
+    assert k.info()["tile_id"] == r["best_tile"]
+    # odd nx: vector tiles are invalid
+    c = torch.rand(9, 10, 33, dtype=torch.float64, device="cuda")
+    r2 = jacc.autotune(dict(stencil=7, dtype=64, nx=33, ny=10, nz=9, coeffs=(0.125,)), c, torch.empty_like(c), 1, 5)
+    assert [bool(v) for v in r2["valid"]] == [jacc.tile_info(t)["vec16"] is False for t in range(24)]
+    jacc.autotune_forget()
+
+
+def test_choose_falls_back_outside_the_training_range():
+    m = jacc.CostModel(seed=5)
+    m.set_range(256.0, 512.0, 0.0)
+    args = dict(stencil=5, dtype=64, nx=128, ny=128)
+    a = torch.rand(128, 128, dtype=torch.float64, device="cuda")
+    t, fb = m.choose(args, a, torch.empty_like(a))
+    assert fb and 0 <= t < 24
+    t2, fb2 = m.choose(dict(stencil=5, dtype=64, nx=300, ny=300))
+    assert not fb2 and 0 <= t2 < 24
+    assert jacc.Kernel(stencil=5, dtype=64, nx=300, ny=300).info()["tile_id"] == t2
+    jacc.autotune_forget()
+
+
+def test_trained_model_gains_over_the_method_without_it():
+    # Reduced workload: 2D sides 256-1024, 3D sides 64-256, four stencil/dtype
+    # pairs; timings measured here by the exhaustive autotuner.  The methods
+    # without the model: the library's fixed default tile, and the single tile
+    # that is best on average over the training tables.
+    pairs = [(5, 64), (7, 32), (7, 64), (27, 32)]
+    tr2 = costmodel.train_sides(256, 1024, 8)
+    tr3 = costmodel.train_sides(64, 256, 8, step=8)
+    ho2 = costmodel.heldout_sides(6, set(tr2), 256, 1024, seed=12)
+    ho3 = costmodel.heldout_sides(6, set(tr3), 64, 256, seed=13, step=8)
+    q_train = [(s, d, side) for s, d in pairs for side in (tr2 if s == 5 else tr3)]
+    q_test = [(s, d, side) for s, d in pairs for side in (ho2 if s == 5 else ho3)]
+    bufs = costmodel.Buffers(256 ** 3)
+    train_t = costmodel.collect(q_train, bufs)
+    test_t = costmodel.collect(q_test, bufs)
+    X, Y = costmodel.xy(train_t)
+    m = jacc.CostModel(seed=5)
+    loss, _ = costmodel.fit(m, X, Y, epochs=6000)
+    margin = costmodel.margin_from_training(m, X, Y)
+    res, picks = costmodel.evaluate(m, train_t, test_t, margin)
+    print("cost-model gain test:", res)
+    assert math.isfinite(res["model"]["mean"])
+    assert loss < 0.05
+    # clearly better than the library's fixed default, within noise of the best fixed tile
+    assert res["model"]["mean"] < 0.5 * res["library_default_tile"]["mean"]
+    assert res["model"]["mean"] <= res["fixed_default_tile"]["mean"] + 0.05
+    assert res["model_with_fallback"]["mean"] <= res["model"]["mean"]

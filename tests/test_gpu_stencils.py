@@ -255,3 +255,42 @@ def test_launch_single_sweep_and_errors(orc):
         jacc.launch(k, a.float(), b)
     with pytest.raises(jacc.JaccError):
         jacc.sweep(k, a, b, 0)
+
+
+# ----------------------------------------------------------------------------- temporal blocking (27-point FP32)
+
+@pytest.mark.parametrize("T", [2, 3])
+def test_box27_temporal_blocking_matches_single_sweeps(orc, T):
+    nz, ny, nx = 70, 37, 248  # ragged against the 120 x (16 - 2T) output tiles and 64-plane chunks
+    u = inputs.box27_field(nx, ny, nz, seed=6)
+    k = jacc.Kernel(jacc.STENCIL_27PT, jacc.F32, nx, ny, nz, coeffs=tuple(float(w) for w in W), tblock=T)
+    assert k.info()["tblock"] == T
+    ns = 2 * T
+    g, gs = run(k, u, ns)
+    o, osum = orc.box27_run(u, W, ns)
+    assert nerr(g, o) <= TOL32
+    A = float(np.sum(np.abs(o.astype(np.float64))))
+    for i in range(ns):
+        if (i + 1) % T == 0:
+            assert abs(gs[i] - osum[i]) <= 1e-6 * A
+        else:
+            assert np.isnan(gs[i])
+    # the same field through the single-sweep kernel
+    k1 = jacc.Kernel(jacc.STENCIL_27PT, jacc.F32, nx, ny, nz, coeffs=tuple(float(w) for w in W))
+    g1, _ = run(k1, u, ns)
+    assert nerr(g, g1) <= TOL32
+
+
+def test_box27_temporal_blocking_small_periodic_and_errors(orc):
+    nz, ny, nx = 5, 7, 12  # smaller than one tile in every axis: wrap inside the region
+    u = inputs.box27_field(nx, ny, nz, seed=8)
+    k = jacc.Kernel(jacc.STENCIL_27PT, jacc.F32, nx, ny, nz, coeffs=tuple(float(w) for w in W), tblock=2)
+    g, _ = run(k, u, 4)
+    o, _ = orc.box27_run(u, W, 4)
+    assert nerr(g, o) <= TOL32
+    a = torch.from_numpy(u).cuda()
+    with pytest.raises(jacc.JaccError):
+        jacc.sweep(k, a, torch.empty_like(a), 3)  # not a multiple of the depth
+    with pytest.raises(jacc.JaccError) as e:
+        jacc.Kernel(jacc.STENCIL_27PT, jacc.F64, 12, 7, 5, coeffs=(0.5, 0.05, 0.01, 0.005), tblock=2)
+    assert e.value.status == jacc.ERR_UNSUPPORTED
