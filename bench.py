@@ -188,16 +188,28 @@ def run_gpu(args):
     stream = torch.cuda.current_stream(dev)
     loops, refs, arrays = region_nest()
 
+    # Set-up (untimed): the exhaustive autotuner picks the tile for this shape
+    # (remembered by the library, so tile_id = -1 resolves to it), then the
+    # constant-folded NVRTC variant of that tile is compiled and cached.
+    tune = None
+    if args.tile < 0 and not args.no_tune:
+        t0 = time.perf_counter()
+        r = jacc.autotune(dict(stencil=jacc.STENCIL_7PT, dtype=jacc.F64, nx=N, ny=N, nz=N, coeffs=(R,)), a, b,
+                          sweeps_per_rep=2, reps=3)
+        tune = {"best_tile": r["best_tile"], "best_ms_per_sweep": r["best_ms"], "seconds": time.perf_counter() - t0}
+        a.copy_(torch.from_numpy(u_host))
+    jit = not args.no_jit
+
     def step(x, y):
         st, _ = jacc.region_analyze(loops, refs, arrays)
         assert st == 0
-        k = jacc.Kernel(jacc.STENCIL_7PT, jacc.F64, N, N, N, coeffs=(R,), tile_id=args.tile, jit=args.jit)
+        k = jacc.Kernel(jacc.STENCIL_7PT, jacc.F64, N, N, N, coeffs=(R,), tile_id=args.tile, jit=jit)
         fb = jacc.sweep(k, x, y, SWEEPS, resid, graph=True)
         k.release()
         return fb
 
     keep = jacc.Kernel(jacc.STENCIL_7PT, jacc.F64, N, N, N, coeffs=(R,), tile_id=args.tile,
-                       jit=args.jit)  # holds the cache entry
+                       jit=jit)  # holds the cache entry
     info = keep.info()
     bufs = [a, b]
     for _ in range(args.warmup):
@@ -246,12 +258,15 @@ def run_gpu(args):
                 "vs_baseline": None, "dtype": "int64", "storage_dtype": "f64", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "grid": [N, N, N], "sweeps_per_step": SWEEPS, "r": R,
                            "tile": info["tile_id"], "fixed_point": info["fixed_point"], "jit": info["jit"],
+                           "jit_compile_ms": info["compile_ms"], "autotune": tune,
                            "l2": "inputs larger than L2 (two 1 GiB fields)",
                            "parallelism": "replicas" if ws > 1 else "single GPU"},
                 "roofline": roof, "e2e": e2e, "gpu_launches": (SWEEPS + 1) * args.steps,
                 "clocks": clk}
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_oracle()
+        if not args.no_secondary and N == 512:
+            line["secondary"] = secondary(dev)
         print(json.dumps(line), flush=True)
     keep.release()
     if ws > 1:
@@ -283,6 +298,106 @@ def measure_e2e(step, a, b, resid, u_host, args, ws):
     return e2e
 
 
+def _time_ms(fn, reps=3):
+    """Best of `reps` CUDA-event timings of fn() on the current stream (after one warm-up call)."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    best = float("inf")
+    for _ in range(reps):
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return best
+
+
+def secondary(dev):
+    """The other workloads of the path, measured on the same GPU (not part of the timed step):
+    Jacobi 256^2 x100, 64 batched Jacobi grids x500 (persistent vs 64 plain graphs), and the
+    27-point FP32 1024^3 x100 periodic stencil (plain vs temporally blocked)."""
+    import numpy as np
+    import torch
+
+    from paper_2110_14340_gb300 import inputs, jacc
+    out = {}
+    # Jacobi 2D 5-point FP64 256^2, 100 sweeps, one graph; region analysis of [1,254]^2 on the host
+    u = inputs.jacobi2d_field(256, 256, seed=1)
+    a = torch.from_numpy(u).to(dev)
+    b = torch.empty_like(a)
+    r = jacc.autotune(dict(stencil=5, dtype=64, nx=256, ny=256), a, b, sweeps_per_rep=20, reps=3)
+    a.copy_(torch.from_numpy(u))
+    k = jacc.Kernel(5, 64, 256, 256, 1, jit=True)
+    res = torch.zeros(100, dtype=torch.float64, device=dev)
+    ms = _time_ms(lambda: jacc.sweep(k, a, b, 100, res), reps=10)
+    I = [[1, 0], [0, 1]]
+    refs = [dict(array=0, coef=I, off=o) for o in ([-1, 0], [1, 0], [0, -1], [0, 1], [0, 0])]
+    refs.append(dict(array=1, write=True, coef=I, off=[0, 0]))
+    t0 = time.perf_counter()
+    for _ in range(1000):
+        jacc.region_analyze([(1, 254, 1), (1, 254, 1)], refs, [[256, 256], [256, 256]])
+    ra_us = (time.perf_counter() - t0) * 1e3
+    out["jacobi2d_256_x100"] = {"ms": ms, "us_per_sweep": 1e3 * ms / 100, "GLUP/s": 254 * 254 * 100 / ms / 1e6,
+                                "tile": k.info()["tile_id"], "region_analysis_us_via_python": ra_us}
+    k.release()
+    # 64 batched grids x 500 sweeps: one persistent launch vs 64 plain graph launches
+    shapes = inputs.batched_shapes(64, seed=3)
+    hosts = inputs.batched_fields(shapes, seed=4)
+    fields = [(torch.from_numpy(h).to(dev), torch.zeros(h.shape, dtype=torch.float64, device=dev)) for h in hosts]
+    lup = sum((nx - 2) * (ny - 2) for nx, ny in shapes) * 500
+    ks = [jacc.Kernel(5, 64, nx, ny, 1) for nx, ny in shapes]
+    rp = torch.zeros(64, 500, dtype=torch.float64, device=dev)
+    plain = _time_ms(lambda: [jacc.sweep(ks[g], fa, fb, 500, rp[g]) for g, (fa, fb) in enumerate(fields)])
+    bt = jacc.Batch(fields)
+    cfg, _ = bt.tune(probe_sweeps=40)
+    rb = torch.zeros(64 * 500, dtype=torch.float64, device=dev)
+    batched = _time_ms(lambda: bt.sweep(500, rb))
+    bt.status()
+    out["batched_64_grids_x500"] = {"plain_ms": plain, "batched_ms": batched, "speedup": plain / batched,
+                                    "plain_GLUP/s": lup / plain / 1e6, "batched_GLUP/s": lup / batched / 1e6,
+                                    "schedule": cfg}
+    for kk in ks:
+        kk.release()
+    bt.release()
+    del fields
+    # 27-point FP32 1024^3, 100 sweeps, periodic: plain (autotuned tile) vs temporal blocking
+    n = 1024
+    w = tuple(float(x) for x in inputs.box27_weights())
+    a = inputs.uniform_torch(6, n ** 3, dev, torch.float32).mul_(2).sub_(1).view(n, n, n)
+    b = torch.empty_like(a)
+    r = jacc.autotune(dict(stencil=27, dtype=32, nx=n, ny=n, nz=n, coeffs=w), a, b, sweeps_per_rep=1, reps=3)
+    kp = jacc.Kernel(27, 32, n, n, n, coeffs=w)
+    res = torch.zeros(100, dtype=torch.float64, device=dev)
+    c5 = {}
+    c5["plain_ms"] = _time_ms(lambda: jacc.sweep(kp, a, b, 100, res), reps=2)
+    c5["plain_tile"] = kp.info()["tile_id"]
+    for T in (2,):
+        kt = jacc.Kernel(27, 32, n, n, n, coeffs=w, tblock=T)
+        c5[f"tb{T}_ms"] = _time_ms(lambda: jacc.sweep(kt, a, b, 100, res), reps=2)
+        kt.release()
+    best = min(c5["plain_ms"], c5["tb2_ms"])
+    c5["GLUP/s"] = n ** 3 * 100 / best / 1e6
+    c5["effective_GB/s_8B_per_point"] = n ** 3 * 100 * 8 / best / 1e6
+    # sum conservation on a fresh field: S_100 = W^100 S_0 (W = sum of the FP32 weights, in FP64)
+    a.copy_(inputs.uniform_torch(6, n ** 3, dev, torch.float32).mul_(2).sub_(1).view(n, n, n))
+    s0 = float(a.double().sum().item())
+    sabs = float(a.abs().double().sum().item())
+    kt = jacc.Kernel(27, 32, n, n, n, coeffs=w, tblock=2)
+    jacc.sweep(kt, a, b, 100, res)
+    torch.cuda.synchronize()
+    kt.release()
+    Wsum = sum(float(np.float32(x)) * c for x, c in zip(w, (1, 6, 12, 8)))
+    rr = res.cpu().numpy()
+    c5["sum_check_rel_to_sum_abs"] = abs(rr[-1] - Wsum ** 100 * s0) / sabs
+    c5["sum_check_tolerance"] = 1e-6
+    kp.release()
+    out["box27_f32_1024_x100"] = c5
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -290,7 +405,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tile", type=int, default=-1)
-    ap.add_argument("--jit", action="store_true", help="use the NVRTC variant with constants folded")
+    ap.add_argument("--no-jit", action="store_true", help="use the precompiled kernel instead of the NVRTC variant")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner; use the library's default tile")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the other workloads' measurements")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the sweep kernel, if captured for this build")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -294,8 +294,7 @@ JD void jacobi_march(const T* __restrict__ u, T* __restrict__ v, i64 nx, i64 ny,
 // marching z over [cz0, cz0 + ZC).  The current plane lives in shared memory
 // with a one-point halo in x and y (double-buffered, so one __syncthreads per
 // plane); each thread keeps its own column's z-1, z, z+1 in registers.
-// Loads are issued ahead of use (one plane ahead in the native kernels, two in
-// the resident fixed-point kernels).
+// Loads for plane z+1 (halo) and z+2 (own) are issued one iteration ahead.
 
 template <class W, int BX, int BY, int V> struct alignas(16) Plane {
   // row layout: [pad V-1][left halo][TX values][right halo][pad V-1]
@@ -912,7 +911,15 @@ JD i64 bits_i64(double d) { return (i64)__double_as_longlong(d); }
 JD double i64_bits(i64 q) { return __longlong_as_double(q); }
 
 // Raw 8-byte word -> fixed-point value: convert (FP64) or reinterpret (fixed).
-JD i64 fx_word(double raw, bool conv, int F) { return conv ? fx_from(raw, F) : bits_i64(raw); }
+// The conversion sits behind a vote over the active lanes, so lanes that only
+// reinterpret do not pay for it.
+JD i64 fx_word(double raw, bool conv, int F) {
+  i64 w = bits_i64(raw);
+  if (__any_sync(__activemask(), conv)) {
+    if (conv) w = fx_from(raw, F);
+  }
+  return w;
+}
 
 // The conversion branch is guarded by a vote over the active lanes, so warps
 // with nothing to convert (interior warps of intermediate sweeps) skip it.
@@ -1067,28 +1074,21 @@ JD void heat3d_fx_body(const double* __restrict__ u, double* __restrict__ v, con
   const bool hcolb = (hcol == 0) || (hcol == nx - 1);
   const double* hxp = u + y * nx + hcol;
 
-  double rcur[V], rzn[V], rzn2[V], rzn3[V], hy[V], hyn[V], hyn2[V];
-  double hx = 0.0, hxn = 0.0, hxn2 = 0.0;
+  double rcur[V], rzn[V], rzn2[V], hy[V], hyn[V];
+  double hx = 0.0, hxn = 0.0;
   i64 zp[V], cur[V], zn[V];
   {
     double t[V];
 #pragma unroll
-    for (int e = 0; e < V; ++e) t[e] = rcur[e] = rzn[e] = rzn2[e] = rzn3[e] = hy[e] = hyn[e] = hyn2[e] = 0.0;
+    for (int e = 0; e < V; ++e) t[e] = rcur[e] = rzn[e] = rzn2[e] = hy[e] = hyn[e] = 0.0;
     if (act) {
       ldv<double, V>(urow + (z0 - 1) * sz, t);
       ldv<double, V>(urow + z0 * sz, rcur);
       ldv<double, V>(urow + (z0 + 1) * sz, rzn);
       if (z0 + 2 < nz) ldv<double, V>(urow + (z0 + 2) * sz, rzn2);
-      if (z0 + 3 < nz) ldv<double, V>(urow + (z0 + 3) * sz, rzn3);
     }
-    if (has_top || has_bot) {
-      ldv<double, V>(hyp + z0 * sz, hy);
-      if (z0 + 1 < z1) ldv<double, V>(hyp + (z0 + 1) * sz, hyn);
-    }
-    if (has_xl || has_xr) {
-      hx = __ldg(hxp + z0 * sz);
-      if (z0 + 1 < z1) hxn = __ldg(hxp + (z0 + 1) * sz);
-    }
+    if (has_top || has_bot) ldv<double, V>(hyp + z0 * sz, hy);
+    if (has_xl || has_xr) hx = __ldg(hxp + z0 * sz);
     fx_words<V>(t, zp, inf || rowb || z0 - 1 == 0, bndm, F);
     fx_words<V>(rcur, cur, inf || rowb, bndm, F);
   }
@@ -1102,14 +1102,14 @@ JD void heat3d_fx_body(const double* __restrict__ u, double* __restrict__ v, con
   i64 zoff = z0 * sz;
   for (i64 z = z0; z < z1; ++z, zoff += sz) {
     fx_words<V>(rzn, zn, inf || rowb || z + 1 == nz - 1, bndm, F);
-    // loads two planes ahead: own plane z+4, halo of plane z+2
-    double rn4[V];
+    // loads one plane ahead: own plane z+3, halo of plane z+1
+    double rn3[V];
 #pragma unroll
-    for (int e = 0; e < V; ++e) rn4[e] = 0.0;
-    if (act && z + 4 < nz) ldv<double, V>(urow + zoff + 4 * sz, rn4);
-    if (z + 2 < z1) {
-      if (has_top || has_bot) ldv<double, V>(hyp + zoff + 2 * sz, hyn2);
-      if (has_xl || has_xr) hxn2 = __ldg(hxp + zoff + 2 * sz);
+    for (int e = 0; e < V; ++e) rn3[e] = 0.0;
+    if (act && z + 3 < nz) ldv<double, V>(urow + zoff + 3 * sz, rn3);
+    if (z + 1 < z1) {
+      if (has_top || has_bot) ldv<double, V>(hyp + zoff + sz, hyn);
+      if (has_xl || has_xr) hxn = __ldg(hxp + zoff + sz);
     }
     // this plane into shared memory (converted)
     i64* row = &sm.a[b][ty + 1][V + tx * V];
@@ -1161,13 +1161,10 @@ JD void heat3d_fx_body(const double* __restrict__ u, double* __restrict__ v, con
       cur[e] = zn[e];
       rcur[e] = rzn[e];
       rzn[e] = rzn2[e];
-      rzn2[e] = rzn3[e];
-      rzn3[e] = rn4[e];
+      rzn2[e] = rn3[e];
       hy[e] = hyn[e];
-      hyn[e] = hyn2[e];
     }
     hx = hxn;
-    hxn = hxn2;
     b ^= 1;
   }
 }
