@@ -398,6 +398,26 @@ def secondary(dev):
     return out
 
 
+def profile_case(args):
+    """A 27-point FP32 periodic sweep sequence on an n^3 cube, nothing else (for ncu captures)."""
+    import torch
+
+    from paper_2110_14340_gb300 import build, inputs, jacc
+    build.build()
+    n = args.n
+    w = tuple(float(x) for x in inputs.box27_weights())
+    a = inputs.uniform_torch(6, n ** 3, "cuda", torch.float32).mul_(2).sub_(1).view(n, n, n)
+    b = torch.empty_like(a)
+    T = 2 if args.profile_case == "box27-tb2" else 0
+    k = jacc.Kernel(27, 32, n, n, n, coeffs=w, tile_id=3 if args.tile < 0 else args.tile, tblock=T)
+    res = torch.zeros(args.sweeps, dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup + args.steps):
+        jacc.sweep(k, a, b, args.sweeps, res)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": args.profile_case, "n": n, "sweeps": args.sweeps,
+                      "runs": args.warmup + args.steps}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -408,6 +428,8 @@ def main():
     ap.add_argument("--no-jit", action="store_true", help="use the precompiled kernel instead of the NVRTC variant")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner; use the library's default tile")
     ap.add_argument("--no-secondary", action="store_true", help="skip the other workloads' measurements")
+    ap.add_argument("--profile-case", choices=["box27", "box27-tb2"], default=None,
+                    help="run only a 27-point FP32 sweep sequence on an --n cube (for profilers) and exit")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the sweep kernel, if captured for this build")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -418,6 +440,9 @@ def main():
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     set_size(args.n, args.sweeps)
+    if args.profile_case:
+        profile_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

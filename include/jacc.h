@@ -214,9 +214,11 @@ jacc_status jacc_launch(jacc_kernel k, const void* u_in, void* u_out, double* re
  * between the sweeps of one call (same 8 bytes per value, in u0/u1): the
  * first sweep reads FP64, the last writes FP64, each intermediate sweep rounds
  * once to the fixed-point grid (2^-F with F >= 57 - e(max|u0|), finer than an
- * FP64 ulp of max|u0|).  After the call the result buffer holds FP64; the
- * interior of the other buffer holds that internal representation (its
- * Dirichlet boundary stays FP64).  Asynchronous on `stream`. */
+ * FP64 ulp of max|u0|).  Dirichlet boundary values pass through the same grid:
+ * they come back unchanged when they are multiples of 2^-F (for instance any
+ * value within 2^52 ulps of max|u0|) and otherwise within 2^-F.  After the
+ * call the result buffer holds FP64; the other buffer holds the internal
+ * representation.  Asynchronous on `stream`. */
 #define JACC_SWEEP_GRAPH 1u
 jacc_status jacc_sweep(jacc_kernel k, void* u0, void* u1, int32_t nsweeps, double* resid_dev, uint32_t flags,
                        uintptr_t stream, int32_t* final_buf);

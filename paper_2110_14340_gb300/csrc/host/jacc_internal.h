@@ -47,7 +47,7 @@ struct Kernel {
   bool jit = false;
   double compile_ms = 0.0;
   const void* func = nullptr;   // kernel entry (host stub or cudaKernel_t)
-  const void* func_out = nullptr;  // the entry for a sweep that ends a fixed-point sequence in FP64
+  const void* func_out = nullptr;  // entry for the first/last sweep of a fixed-point sequence (FP64 in or out)
   cudaLibrary_t lib = nullptr;  // NVRTC module, if jit
   dim3 grid, block;
   int tblock = 1;

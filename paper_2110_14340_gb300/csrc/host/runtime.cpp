@@ -380,7 +380,7 @@ cudaError_t launch_sweep_kernel(const Kernel& k, const void* u, void* v, double*
                                 cudaStream_t s) {
   JParams p = k.params;
   const void* args[] = {&u, &v, &p, &resid, &maxword, &flags};
-  return cudaLaunchKernel((flags & kFxOut) ? k.func_out : k.func, k.grid, k.block, const_cast<void**>(args), 0, s);
+  return cudaLaunchKernel((flags & (kFxIn | kFxOut)) ? k.func_out : k.func, k.grid, k.block, const_cast<void**>(args), 0, s);
 }
 
 }  // namespace jacc

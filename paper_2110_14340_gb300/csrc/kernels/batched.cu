@@ -66,7 +66,7 @@ JD void run_band(const JBGrid& G, const double* src, double* dst, i64 r0, i64 r1
   for (i64 c = warp; c < nchunks; c += kWarps) {
     const i64 x0 = c * chunk + lane * V;
     if constexpr (MODE == JM_FIXED) {
-      if (flags & JFX_OUT_F64) jacobi_fx_march<V, true, true>(src, dst, G.nx, G.ny, x0, r0, r1, F, flags, m);
+      if (flags) jacobi_fx_march<V, true, true>(src, dst, G.nx, G.ny, x0, r0, r1, F, flags, m);
       else jacobi_fx_march<V, true, false>(src, dst, G.nx, G.ny, x0, r0, r1, F, flags, m);
     } else {
       jacobi_march<double, V, MODE, true>(src, dst, G.nx, G.ny, x0, r0, r1, F, m);

@@ -27,8 +27,9 @@ typedef float JT;
 #define JENTRY(id, BX, BY, VEC, ZC) (const void*)JKERN(BX, BY, ((VEC) ? JVEC : 1), ZC, false),
 #define JENTRY_OUT(id, BX, BY, VEC, ZC) (const void*)JKERN(BX, BY, ((VEC) ? JVEC : 1), ZC, (JACC_INST_DTYPE == 64)),
 
-// Table 1: sweeps that write the resident fixed-point form (and every FP32 or
-// native sweep).  Table 2: sweeps that write FP64 from the fixed-point path
-// (the last of a sequence); identical to table 1 for FP32.
+// Table 1: the intermediate sweeps of a fixed-point sequence (and every FP32
+// or native sweep).  Table 2 ("_out"): the first and last sweeps of a
+// fixed-point sequence and single launches, which convert FP64 on load and/or
+// store; identical to table 1 for FP32.
 extern "C" const void* const JTABNAME(JACC_INST_STENCIL, JACC_INST_DTYPE)[JACC_NTILES] = {JACC_TILE_LIST(JENTRY)};
 extern "C" const void* const JTABOUT(JACC_INST_STENCIL, JACC_INST_DTYPE)[JACC_NTILES] = {JACC_TILE_LIST(JENTRY_OUT)};
