@@ -652,6 +652,23 @@ template <class W, int V> JD void lds_row(const W* p, W (&r)[V + 2]) {
   r[V + 1] = p[V];
 }
 
+// Stores a thread's V values to a shared-memory row as one 16-byte vector
+// where the width allows.
+template <class W, int V> JD void sts_row(W* p, const W (&r)[V]) {
+  if constexpr (V * sizeof(W) == 16 && V == 4) {
+    float4 t;
+    t.x = r[0]; t.y = r[1]; t.z = r[2]; t.w = r[3];
+    *reinterpret_cast<float4*>(p) = t;
+  } else if constexpr (V * sizeof(W) == 16 && V == 2) {
+    double2 t;
+    t.x = r[0]; t.y = r[1];
+    *reinterpret_cast<double2*>(p) = t;
+  } else {
+#pragma unroll
+    for (int e = 0; e < V; ++e) p[e] = r[e];
+  }
+}
+
 template <class T, int BX, int BY, int V>
 struct Box27Fetch {
   T own[V], hrow[V], hx, cr[4];
@@ -698,14 +715,8 @@ JD void box27_body2(const T* __restrict__ u, T* __restrict__ v, const P& p, SumA
     }
   };
   auto put = [&](const Box27Fetch<T, BX, BY, V>& f, int b) {
-    T* row = &sm.a[b][ty + 1][V + tx * V];
-#pragma unroll
-    for (int e = 0; e < V; ++e) row[e] = f.own[e];
-    if (hy) {
-      T* hr = &sm.a[b][ty == 0 ? 0 : BY + 1][V + tx * V];
-#pragma unroll
-      for (int e = 0; e < V; ++e) hr[e] = f.hrow[e];
-    }
+    sts_row<T, V>(&sm.a[b][ty + 1][V + tx * V], f.own);
+    if (hy) sts_row<T, V>(&sm.a[b][ty == 0 ? 0 : BY + 1][V + tx * V], f.hrow);
     if (tx == 0) sm.a[b][ty + 1][V - 1] = f.hx;
     if (tx == BX - 1) sm.a[b][ty + 1][V + BX * V] = f.hx;
     if (corner) {
@@ -910,29 +921,9 @@ JD void box27_tb_entry(const float* __restrict__ u, float* __restrict__ v, const
 JD i64 bits_i64(double d) { return (i64)__double_as_longlong(d); }
 JD double i64_bits(i64 q) { return __longlong_as_double(q); }
 
-// Raw 8-byte word -> fixed-point value: convert (FP64) or reinterpret (fixed).
-// The conversion sits behind a vote over the active lanes, so lanes that only
-// reinterpret do not pay for it.
-JD i64 fx_word(double raw, bool conv, int F) {
-  i64 w = bits_i64(raw);
-  if (__any_sync(__activemask(), conv)) {
-    if (conv) w = fx_from(raw, F);
-  }
-  return w;
-}
-
-// The conversion branch is guarded by a vote over the active lanes, so warps
-// with nothing to convert (interior warps of intermediate sweeps) skip it.
-template <int V>
-JD void fx_words(const double (&raw)[V], i64 (&w)[V], bool conv_all, unsigned conv_mask, int F) {
-#pragma unroll
-  for (int e = 0; e < V; ++e) w[e] = bits_i64(raw[e]);
-  if (__any_sync(__activemask(), conv_all || conv_mask != 0u)) {
-#pragma unroll
-    for (int e = 0; e < V; ++e)
-      if (conv_all || ((conv_mask >> e) & 1u)) w[e] = fx_from(raw[e], F);
-  }
-}
+// Raw 8-byte word -> fixed-point value: convert (FP64 input) or reinterpret
+// (resident fixed point).
+JD i64 fx_in(double raw, bool conv, int F) { return conv ? fx_from(raw, F) : bits_i64(raw); }
 
 // Round q * 2^-k to the nearest integer (ties up), k in [0, 62].
 JD i64 fx_round_shift(i64 q, int k) { return k ? ((q + ((i64)1 << (k - 1))) >> k) : q; }
@@ -964,15 +955,24 @@ template <int V> JD void col_masks(i64 x0, i64 nx, unsigned& intm, unsigned& bnd
 //
 // Same march as jacobi_march.  v 2^F = (S + 2) >> 2 with S the four
 // neighbours (exact); the FP64 output is fx_to(S, F + 2).  Residual: max
-// |S - 4u| (scale F, converted once per thread by the caller).
-template <int V, bool CG, bool OUTF>
+// |S - 4u| (scale F, converted once per thread by the caller).  EDGE as for
+// the 7-point kernel: intermediate sweeps (EDGE = false) convert nothing.
+template <int V, bool CG, bool EDGE>
 JD void jacobi_fx_march(const double* __restrict__ u, double* __restrict__ v, i64 nx, i64 ny, i64 x0, i64 ys, i64 ye,
                         int F, int flags, u64& rmax) {
   const int lane = threadIdx.x & 31;
   const bool xin = x0 < nx;
-  const bool inf = flags & JFX_IN_F64;
+  const bool inf = EDGE && (flags & JFX_IN_F64);
+  const bool outf = EDGE && (flags & JFX_OUT_F64);
   unsigned intm, bndm;
   col_masks<V>(x0, nx, intm, bndm);
+  auto cvt = [&](double raw) -> i64 { return (EDGE && inf) ? fx_from(raw, F) : bits_i64(raw); };
+  auto bnd_out = [&](double raw, i64 w) -> double {
+    if constexpr (!EDGE) return i64_bits(w);
+    if (inf && outf) return raw;
+    if (outf) return fx_to(w, F);
+    return i64_bits(w);
+  };
   double rup[V], rcur[V], rdn[V], rnx[V];
   i64 up[V], cur[V], dn[V];
 #pragma unroll
@@ -983,17 +983,17 @@ JD void jacobi_fx_march(const double* __restrict__ u, double* __restrict__ v, i6
     if (ys + 1 < ny) ldv<double, V, CG>(u + (ys + 1) * nx + x0, rdn);
     if (ys + 2 < ny) ldv<double, V, CG>(u + (ys + 2) * nx + x0, rnx);
   }
-  auto rowb = [&](i64 r) { return r == 0 || r == ny - 1; };
-  fx_words<V>(rup, up, inf || rowb(ys - 1), bndm, F);
-  fx_words<V>(rcur, cur, inf || rowb(ys), bndm, F);
-  fx_words<V>(rdn, dn, inf || rowb(ys + 1), bndm, F);
+#pragma unroll
+  for (int e = 0; e < V; ++e) {
+    up[e] = cvt(rup[e]);
+    cur[e] = cvt(rcur[e]);
+    dn[e] = cvt(rdn[e]);
+  }
   for (i64 y = ys; y < ye; ++y) {
     i64 left = __shfl_up_sync(0xffffffffu, cur[V - 1], 1);
     i64 right = __shfl_down_sync(0xffffffffu, cur[0], 1);
-    if (lane == 0 && xin && x0 >= 1)
-      left = fx_word(ld1<CG>(u + y * nx + x0 - 1), inf || rowb(y) || x0 - 1 == 0, F);
-    if (lane == 31 && xin && x0 + V < nx)
-      right = fx_word(ld1<CG>(u + y * nx + x0 + V), inf || rowb(y) || x0 + V == nx - 1, F);
+    if (lane == 0 && xin && x0 >= 1) left = cvt(ld1<CG>(u + y * nx + x0 - 1));
+    if (lane == 31 && xin && x0 + V < nx) right = cvt(ld1<CG>(u + y * nx + x0 + V));
     double rnn[V];
 #pragma unroll
     for (int e = 0; e < V; ++e) rnn[e] = 0.0;
@@ -1006,10 +1006,8 @@ JD void jacobi_fx_march(const double* __restrict__ u, double* __restrict__ v, i6
       const i64 xr = (e == V - 1) ? right : cur[e + 1];
       const bool in = yint && ((intm >> e) & 1u);
       const i64 s = (up[e] + dn[e]) + (xl + xr);
-      double o;
-      if constexpr (OUTF) o = fx_to(s, F + 2);
-      else o = i64_bits((s + 2) >> 2);
-      out[e] = in ? o : rcur[e];
+      const double o = outf ? fx_to(s, F + 2) : i64_bits((s + 2) >> 2);
+      out[e] = in ? o : bnd_out(rcur[e], cur[e]);
       const i64 d = s - cur[e] * 4;
       const u64 ad = (u64)(d ^ (d >> 63));  // |d| (one less for negative d: below the tolerance by 2^-F)
       if (in && ad > rmax) rmax = ad;
@@ -1021,20 +1019,25 @@ JD void jacobi_fx_march(const double* __restrict__ u, double* __restrict__ v, i6
       cur[e] = dn[e];
       rcur[e] = rdn[e];
       rdn[e] = rnx[e];
+      dn[e] = cvt(rnx[e]);
       rnx[e] = rnn[e];
     }
-    fx_words<V>(rdn, dn, inf || rowb(y + 2), bndm, F);
   }
 }
 
 // ---------------------------------------------------------------- 7-point heat, resident fixed point
 //
 // S = the six faces, L = S - 6u (exact, scale F):
-//   JACC_FP_SMALL (r = fb 2^-k): q = fa u + fb S = u 2^k + fb L, scale F+k
-//   JACC_FP_WIDE  (r = m 2^-k):  q = u 2^k + m L in 128 bits, scale F+k
-// fixed output = round(q 2^-k); FP64 output = q correctly rounded; the
-// residual only needs max |L|.
-template <bool OUTF, int BX, int BY, int V, int ZC, class P>
+//   JACC_FP_SMALL (r = fb 2^-k): v = u + round(fb L 2^-k)      (int64)
+//   JACC_FP_WIDE  (r = m 2^-k):  v = u + round(m L 2^-k)       (128-bit product)
+// FP64 output: u + r L correctly rounded.  The residual only needs max |L|.
+//
+// EDGE = false: an intermediate sweep.  Every value in both buffers, the
+// Dirichlet boundary included, is already in fixed point, so the kernel does
+// no conversion at all.  EDGE = true: the first and/or last sweep of a
+// sequence (flags JFX_IN_F64 / JFX_OUT_F64): loads convert from FP64, stores
+// convert to FP64, boundary points are converted (or copied when both).
+template <bool EDGE, int BX, int BY, int V, int ZC, class P>
 JD void heat3d_fx_body(const double* __restrict__ u, double* __restrict__ v, const P& p, int F, int flags, u64& rmax,
                        Plane<i64, BX, BY, V>& sm) {
   const i64 nx = p.nx, ny = p.ny, nz = p.nz;
@@ -1047,13 +1050,33 @@ JD void heat3d_fx_body(const double* __restrict__ u, double* __restrict__ v, con
   const bool act = (x0 < nx) && (y < ny);
   const i64 cz0 = (i64)blockIdx.z * ZC;
   const i64 cz1 = (cz0 + ZC < nz) ? cz0 + ZC : nz;
-  const bool inf = flags & JFX_IN_F64;
+  const bool inf = EDGE && (flags & JFX_IN_F64);
+  const bool outf = EDGE && (flags & JFX_OUT_F64);
   const double* urow = u + y * nx + x0;
   double* vrow = v + y * nx + x0;
+  // boundary point written by this sweep, from its input word
+  auto bnd_out = [&](double raw, i64 w) -> double {
+    if constexpr (!EDGE) return i64_bits(w);    // fixed in, fixed out (raw holds the same bits)
+    if (inf && outf) return raw;                // FP64 in, FP64 out: copy
+    if (outf) return fx_to(w, F);               // fixed in, FP64 out
+    return i64_bits(w);                         // FP64 in, fixed out
+  };
+  auto cvt = [&](double raw) -> i64 { return (EDGE && inf) ? fx_from(raw, F) : bits_i64(raw); };
 
-  // Boundary planes (FP64 bits) are copied by the chunk that holds them.
-  if (act && cz0 == 0) { double t[V]; ldv<double, V>(urow, t); stv<double, V>(vrow, t); }
-  if (act && cz1 == nz) { double t[V]; ldv<double, V>(urow + (nz - 1) * sz, t); stv<double, V>(vrow + (nz - 1) * sz, t); }
+  // Boundary planes are written by the chunk that holds them.
+  if (act && (cz0 == 0 || cz1 == nz)) {
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      if ((side == 0 && cz0 == 0) || (side == 1 && cz1 == nz)) {
+        const i64 off = side ? (nz - 1) * sz : 0;
+        double t[V];
+        ldv<double, V>(urow + off, t);
+#pragma unroll
+        for (int e = 0; e < V; ++e) t[e] = bnd_out(t[e], cvt(t[e]));
+        stv<double, V>(vrow + off, t);
+      }
+    }
+  }
   const i64 z0 = cz0 < 1 ? 1 : cz0;
   const i64 z1 = cz1 > nz - 1 ? nz - 1 : cz1;
   if (z0 >= z1) return;  // block-uniform
@@ -1065,14 +1088,10 @@ JD void heat3d_fx_body(const double* __restrict__ u, double* __restrict__ v, con
   // halo sources of this thread (fixed per CTA and thread)
   const bool has_top = (ty == 0) && (by0 >= 1) && (x0 < nx);
   const bool has_bot = (ty == BY - 1) && (by0 + BY < ny) && (x0 < nx);
-  const i64 hrow = has_top ? by0 - 1 : by0 + BY;
-  const bool hrowb = (hrow == 0) || (hrow == ny - 1);
-  const double* hyp = u + hrow * nx + x0;
+  const double* hyp = u + (has_top ? by0 - 1 : by0 + BY) * nx + x0;
   const bool has_xl = (tx == 0) && (bx0 >= 1) && (y < ny);
   const bool has_xr = (tx == BX - 1) && (bx0 + BX * V < nx) && (y < ny);
-  const i64 hcol = has_xl ? bx0 - 1 : bx0 + BX * V;
-  const bool hcolb = (hcol == 0) || (hcol == nx - 1);
-  const double* hxp = u + y * nx + hcol;
+  const double* hxp = u + y * nx + (has_xl ? bx0 - 1 : bx0 + BX * V);
 
   double rcur[V], rzn[V], rzn2[V], hy[V], hyn[V];
   double hx = 0.0, hxn = 0.0;
@@ -1089,19 +1108,17 @@ JD void heat3d_fx_body(const double* __restrict__ u, double* __restrict__ v, con
     }
     if (has_top || has_bot) ldv<double, V>(hyp + z0 * sz, hy);
     if (has_xl || has_xr) hx = __ldg(hxp + z0 * sz);
-    fx_words<V>(t, zp, inf || rowb || z0 - 1 == 0, bndm, F);
-    fx_words<V>(rcur, cur, inf || rowb, bndm, F);
+#pragma unroll
+    for (int e = 0; e < V; ++e) { zp[e] = cvt(t[e]); cur[e] = cvt(rcur[e]); }
   }
   const i64 fb = p.fb, fw0 = p.fw0;
   const int k = p.fk;
   const bool small = p.fpath == JACC_FP_SMALL;
-  // warps whose every point is interior take a branch-free path
-  const bool allint = !act || (yint && intm == (1u << V) - 1u);
-  const bool warp_int = __all_sync(0xffffffffu, allint) && __any_sync(0xffffffffu, act);
   int b = 0;
   i64 zoff = z0 * sz;
   for (i64 z = z0; z < z1; ++z, zoff += sz) {
-    fx_words<V>(rzn, zn, inf || rowb || z + 1 == nz - 1, bndm, F);
+#pragma unroll
+    for (int e = 0; e < V; ++e) zn[e] = cvt(rzn[e]);
     // loads one plane ahead: own plane z+3, halo of plane z+1
     double rn3[V];
 #pragma unroll
@@ -1111,48 +1128,40 @@ JD void heat3d_fx_body(const double* __restrict__ u, double* __restrict__ v, con
       if (has_top || has_bot) ldv<double, V>(hyp + zoff + sz, hyn);
       if (has_xl || has_xr) hxn = __ldg(hxp + zoff + sz);
     }
-    // this plane into shared memory (converted)
+    // this plane into shared memory
     i64* row = &sm.a[b][ty + 1][V + tx * V];
 #pragma unroll
     for (int e = 0; e < V; ++e) row[e] = cur[e];
     if (has_top || has_bot) {
-      i64 w[V];
-      fx_words<V>(hy, w, inf || hrowb, bndm, F);
       i64* hr = &sm.a[b][has_top ? 0 : BY + 1][V + tx * V];
 #pragma unroll
-      for (int e = 0; e < V; ++e) hr[e] = w[e];
+      for (int e = 0; e < V; ++e) hr[e] = cvt(hy[e]);
     }
-    if (has_xl) sm.a[b][ty + 1][V - 1] = fx_word(hx, inf || rowb || hcolb, F);
-    if (has_xr) sm.a[b][ty + 1][V + BX * V] = fx_word(hx, inf || rowb || hcolb, F);
+    if (has_xl) sm.a[b][ty + 1][V - 1] = cvt(hx);
+    if (has_xr) sm.a[b][ty + 1][V + BX * V] = cvt(hx);
     __syncthreads();
     const i64* rm = &sm.a[b][ty][V + tx * V];
     const i64* r0 = &sm.a[b][ty + 1][V + tx * V];
     const i64* rp = &sm.a[b][ty + 2][V + tx * V];
     double out[V];
-    // v = u + round(r L) with L = S - 6u exact; FP64 output: u + r L correctly rounded
-    auto point = [&](int e, bool in) {
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      const bool in = yint && ((intm >> e) & 1u);
       const i64 xl = (e == 0) ? r0[-1] : cur[e - 1];
       const i64 xr = (e == V - 1) ? r0[V] : cur[e + 1];
       const i64 sum = ((xl + xr) + (rm[e] + rp[e])) + (zp[e] + zn[e]);
       const i64 L = sum - 6 * cur[e];
       double o;
-      if constexpr (OUTF) {
+      if (outf) {
         if (small) o = fx_to(cur[e] * ((i64)1 << k) + fb * L, F + k);
         else o = fx128_to(add128(from_s64_shl(cur[e], k), mul_s64_u64(L, (u64)fw0)), F + k);
       } else {
         if (small) o = i64_bits(cur[e] + fx_round_shift(fb * L, k));
         else o = i64_bits(cur[e] + fx128_round_shift(mul_s64_u64(L, (u64)fw0), k));
       }
-      out[e] = in ? o : rcur[e];
+      out[e] = in ? o : bnd_out(rcur[e], cur[e]);
       const u64 aL = (u64)(L ^ (L >> 63));  // |L| (one less for negative L: 2^-F, below the tolerance)
       rmax = (in && aL > rmax) ? aL : rmax;
-    };
-    if (warp_int) {
-#pragma unroll
-      for (int e = 0; e < V; ++e) point(e, true);
-    } else {
-#pragma unroll
-      for (int e = 0; e < V; ++e) point(e, yint && ((intm >> e) & 1u));
     }
     if (act) stv<double, V>(vrow + zoff, out);
 #pragma unroll
@@ -1169,6 +1178,8 @@ JD void heat3d_fx_body(const double* __restrict__ u, double* __restrict__ v, con
   }
 }
 
+// Residual of the heat sweep from max |L|: r max|L| scaled.
+
 // ---------------------------------------------------------------- 27-point box, resident fixed point
 //
 // v 2^F = round(sum_j fw_j class_j 2^-K) from the exact 128-bit sum; the FP64
@@ -1184,7 +1195,8 @@ JD void fx_plane_load_put(const double* __restrict__ u, i64 nx, i64 ny, i64 nz, 
   double r[V];
   ldv<double, V>(urow + zz * nx * ny, r);
   i64 w[V];
-  fx_words<V>(r, w, inf, 0u, F);
+#pragma unroll
+  for (int e = 0; e < V; ++e) w[e] = inf ? fx_from(r[e], F) : bits_i64(r[e]);
   i64* row = &sm.a[b][ty + 1][V + tx * V];
 #pragma unroll
   for (int e = 0; e < V; ++e) row[e] = w[e];
@@ -1193,25 +1205,26 @@ JD void fx_plane_load_put(const double* __restrict__ u, i64 nx, i64 ny, i64 nz, 
     const i64 yy = ty == 0 ? (by0 - 1 + ny) % ny : (by0 + BY) % ny;
     double h[V];
     ldv<double, V>(pl + yy * nx + x0, h);
-    fx_words<V>(h, w, inf, 0u, F);
+#pragma unroll
+    for (int e = 0; e < V; ++e) w[e] = inf ? fx_from(h[e], F) : bits_i64(h[e]);
     i64* hr = &sm.a[b][ty == 0 ? 0 : BY + 1][V + tx * V];
 #pragma unroll
     for (int e = 0; e < V; ++e) hr[e] = w[e];
   }
   const i64 yy = (by0 + ty) % ny;
-  if (tx == 0) sm.a[b][ty + 1][V - 1] = fx_word(__ldg(pl + yy * nx + (bx0 - 1 + nx) % nx), inf, F);
-  if (tx == BX - 1) sm.a[b][ty + 1][V + BX * V] = fx_word(__ldg(pl + yy * nx + (bx0 + BX * V) % nx), inf, F);
+  if (tx == 0) sm.a[b][ty + 1][V - 1] = fx_in(__ldg(pl + yy * nx + (bx0 - 1 + nx) % nx), inf, F);
+  if (tx == BX - 1) sm.a[b][ty + 1][V + BX * V] = fx_in(__ldg(pl + yy * nx + (bx0 + BX * V) % nx), inf, F);
   if (tx == 0 && ty == 0) {
     const i64 xl = (bx0 - 1 + nx) % nx, xr = (bx0 + BX * V) % nx;
     const i64 yt = (by0 - 1 + ny) % ny, yb = (by0 + BY) % ny;
-    sm.a[b][0][V - 1] = fx_word(__ldg(pl + yt * nx + xl), inf, F);
-    sm.a[b][0][V + BX * V] = fx_word(__ldg(pl + yt * nx + xr), inf, F);
-    sm.a[b][BY + 1][V - 1] = fx_word(__ldg(pl + yb * nx + xl), inf, F);
-    sm.a[b][BY + 1][V + BX * V] = fx_word(__ldg(pl + yb * nx + xr), inf, F);
+    sm.a[b][0][V - 1] = fx_in(__ldg(pl + yt * nx + xl), inf, F);
+    sm.a[b][0][V + BX * V] = fx_in(__ldg(pl + yt * nx + xr), inf, F);
+    sm.a[b][BY + 1][V - 1] = fx_in(__ldg(pl + yb * nx + xl), inf, F);
+    sm.a[b][BY + 1][V + BX * V] = fx_in(__ldg(pl + yb * nx + xr), inf, F);
   }
 }
 
-template <bool OUTF, int BX, int BY, int V, int ZC, class P>
+template <bool EDGE, int BX, int BY, int V, int ZC, class P>
 JD void box27_fx_body(const double* __restrict__ u, double* __restrict__ v, const P& p, int F, int flags, s128& acc,
                       Plane<i64, BX, BY, V>& sm) {
   const i64 nx = p.nx, ny = p.ny, nz = p.nz;
@@ -1224,7 +1237,8 @@ JD void box27_fx_body(const double* __restrict__ u, double* __restrict__ v, cons
   const bool act = (x0 < nx) && (y < ny);
   const i64 z0 = (i64)blockIdx.z * ZC;
   const i64 z1 = (z0 + ZC < nz) ? z0 + ZC : nz;
-  const bool inf = flags & JFX_IN_F64;
+  const bool inf = EDGE && (flags & JFX_IN_F64);
+  const bool outf = EDGE && (flags & JFX_OUT_F64);
   const double* urow = u + (y % ny) * nx + (x0 % nx);  // periodic image for overhanging threads
   double* vrow = v + y * nx + x0;
   const i64 w0 = p.fw0, w1 = p.fw1, w2 = p.fw2, w3 = p.fw3;
@@ -1253,8 +1267,7 @@ JD void box27_fx_body(const double* __restrict__ u, double* __restrict__ v, cons
       a = add128(a, mul_s64_u64((g0[e] + fm[e]) + fn[e], (u64)w2));
       a = add128(a, mul_s64_u64(gm[e] + gn[e], (u64)w3));
       const i64 q = fx128_round_shift(a, K);
-      if constexpr (OUTF) out[e] = fx128_to(a, F + K);
-      else out[e] = i64_bits(q);
+      out[e] = outf ? fx128_to(a, F + K) : i64_bits(q);
       if (act) {
         s128 t;
         t.lo = (u64)q;
@@ -1281,11 +1294,12 @@ JD void box27_fx_body(const double* __restrict__ u, double* __restrict__ v, cons
 // bit pattern of max|u| written by jacc_k_maxabs, which selects the fixed
 // point scale.  With maxword NULL or fpath NONE the native path runs.
 // flags (JFX_*) say whether this sweep of a sequence reads and writes FP64
-// or the resident fixed-point representation; native paths ignore them.  The
-// FP64 output of the fixed-point path is the template parameter OUTF, so
-// intermediate sweeps run an instantiation without the conversion code.
+// or the resident fixed-point representation; native paths ignore them.
+// EDGE = false instantiations run the intermediate sweeps of a fixed-point
+// sequence and contain no conversion code; EDGE = true ones run the first and
+// last sweeps and single launches.
 
-template <class T, int BX, int BY, int V, int ZC, bool OUTF, class P>
+template <class T, int BX, int BY, int V, int ZC, bool EDGE, class P>
 JD void jacobi2d_entry(const T* __restrict__ u, T* __restrict__ v, const P& p, double* resid, const u64* maxword,
                        int flags) {
   u64 bits = 0;
@@ -1296,7 +1310,7 @@ JD void jacobi2d_entry(const T* __restrict__ u, T* __restrict__ v, const P& p, d
     const int F = (maxword && p.fpath != JACC_FP_NONE) ? fx_frac_bits(*maxword) : -1;
     if (F >= 0) {
       u64 m = 0;
-      if (ys < p.ny) jacobi_fx_march<V, false, OUTF>(u, v, p.nx, p.ny, x0, ys, ye, F, flags, m);
+      if (ys < p.ny) jacobi_fx_march<V, false, EDGE>(u, v, p.nx, p.ny, x0, ys, ye, F, flags, m);
       bits = dbits(fx_to_u(m, F + 2));
     } else {
       double m = 0.0;
@@ -1311,7 +1325,7 @@ JD void jacobi2d_entry(const T* __restrict__ u, T* __restrict__ v, const P& p, d
   block_max_to<BX * BY>(bits, resid);
 }
 
-template <class T, int BX, int BY, int V, int ZC, bool OUTF, class P>
+template <class T, int BX, int BY, int V, int ZC, bool EDGE, class P>
 JD void heat3d_entry(const T* __restrict__ u, T* __restrict__ v, const P& p, double* resid, const u64* maxword,
                      int flags) {
   u64 bits = 0;
@@ -1320,7 +1334,7 @@ JD void heat3d_entry(const T* __restrict__ u, T* __restrict__ v, const P& p, dou
     __shared__ __align__(16) unsigned char raw[sizeof(Plane<i64, BX, BY, V>)];
     if (F >= 0) {
       u64 m = 0;
-      heat3d_fx_body<OUTF, BX, BY, V, ZC>(u, v, p, F, flags, m, *reinterpret_cast<Plane<i64, BX, BY, V>*>(raw));
+      heat3d_fx_body<EDGE, BX, BY, V, ZC>(u, v, p, F, flags, m, *reinterpret_cast<Plane<i64, BX, BY, V>*>(raw));
       bits = dbits(heat_resid_fixed(p, m, F));
     } else {
       double m = 0.0;
@@ -1336,7 +1350,7 @@ JD void heat3d_entry(const T* __restrict__ u, T* __restrict__ v, const P& p, dou
   block_max_to<BX * BY>(bits, resid);
 }
 
-template <class T, int BX, int BY, int V, int ZC, bool OUTF, class P>
+template <class T, int BX, int BY, int V, int ZC, bool EDGE, class P>
 JD void box27_entry(const T* __restrict__ u, T* __restrict__ v, const P& p, double* resid, const u64* maxword,
                     int flags) {
   double total = 0.0;
@@ -1346,7 +1360,7 @@ JD void box27_entry(const T* __restrict__ u, T* __restrict__ v, const P& p, doub
     if (F >= 0) {
       s128 acc;
       acc.lo = acc.hi = 0ull;
-      box27_fx_body<OUTF, BX, BY, V, ZC>(u, v, p, F, flags, acc, *reinterpret_cast<Plane<i64, BX, BY, V>*>(raw));
+      box27_fx_body<EDGE, BX, BY, V, ZC>(u, v, p, F, flags, acc, *reinterpret_cast<Plane<i64, BX, BY, V>*>(raw));
       total = fx128_to(acc, F);
     } else {
       SumAcc<T> acc;
@@ -1401,23 +1415,23 @@ __global__ void jacc_k_fill_skipped(double* resid, int n, int T) {
 #endif  // JACC_AUX_KERNELS
 
 // Kernel templates instantiated by the precompiled library (P = JParams).
-template <class T, int BX, int BY, int V, int ZC, bool OUTF>
+template <class T, int BX, int BY, int V, int ZC, bool EDGE>
 __global__ void __launch_bounds__(BX * BY) jacc_k_jacobi2d(const T* __restrict__ u, T* __restrict__ v, JParams p,
                                                            double* resid, const u64* maxword, int flags) {
-  jacobi2d_entry<T, BX, BY, V, ZC, OUTF>(u, v, p, resid, maxword, flags);
+  jacobi2d_entry<T, BX, BY, V, ZC, EDGE>(u, v, p, resid, maxword, flags);
 }
-template <class T, int BX, int BY, int V, int ZC, bool OUTF>
+template <class T, int BX, int BY, int V, int ZC, bool EDGE>
 __global__ void __launch_bounds__(BX * BY) jacc_k_heat3d(const T* __restrict__ u, T* __restrict__ v, JParams p,
                                                          double* resid, const u64* maxword, int flags) {
-  heat3d_entry<T, BX, BY, V, ZC, OUTF>(u, v, p, resid, maxword, flags);
+  heat3d_entry<T, BX, BY, V, ZC, EDGE>(u, v, p, resid, maxword, flags);
 }
 template <int RY, int TT, int ZC>
 __global__ void __launch_bounds__(TB_BX * RY) jacc_k_box27_tb(const float* __restrict__ u, float* __restrict__ v,
                                                               JParams p, double* resid, const u64* maxword, int flags) {
   box27_tb_entry<RY, TT, ZC>(u, v, p, resid);
 }
-template <class T, int BX, int BY, int V, int ZC, bool OUTF>
+template <class T, int BX, int BY, int V, int ZC, bool EDGE>
 __global__ void __launch_bounds__(BX * BY) jacc_k_box27(const T* __restrict__ u, T* __restrict__ v, JParams p,
                                                         double* resid, const u64* maxword, int flags) {
-  box27_entry<T, BX, BY, V, ZC, OUTF>(u, v, p, resid, maxword, flags);
+  box27_entry<T, BX, BY, V, ZC, EDGE>(u, v, p, resid, maxword, flags);
 }
