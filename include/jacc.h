@@ -187,6 +187,21 @@ jacc_status jacc_specialize(const jacc_kernel_desc* desc, jacc_kernel* out);
 jacc_status jacc_kernel_info(jacc_kernel k, jacc_kernel_info_t* out);
 jacc_status jacc_release(jacc_kernel k);
 
+/* Device status of a handle's launches (no counterpart in the paper).  The
+ * 27PT FP32 kernels with 16-byte columns stage their input planes in shared
+ * memory with bulk copies and wait for them on mbarriers; each such wait is
+ * bounded (default 2 s).  A wait that runs out writes JACC_ERR_TIMEOUT to the
+ * handle's device status word and its CTA returns early, so the output of
+ * that launch is incomplete.  jacc_kernel_status synchronises the device,
+ * stores the word (JACC_OK or JACC_ERR_TIMEOUT) in *status and clears it.
+ * jacc_kernel_set_wait sets the limit of each wait (timeout_ms > 0, or 0 for
+ * the default) and a test hook: stall_plane >= 0 makes CTA (0,0,0) of later
+ * launches never request that staged plane, so its waits run out
+ * (-1 = off).  It applies to the handle (shared by identical descriptors)
+ * and drops its cached graphs. */
+jacc_status jacc_kernel_status(jacc_kernel k, int32_t* status);
+jacc_status jacc_kernel_set_wait(jacc_kernel k, int32_t timeout_ms, int32_t stall_plane);
+
 /* Tile configuration `tile_id`: threads (bx, by) per CTA, elements per thread
  * in x (vec: 1 or a 16-byte vector), and the march length zc (planes per CTA
  * in 3D, rows per thread in 2D).  Host only. */

@@ -61,6 +61,8 @@ struct Kernel {
 cudaError_t launch_sweep_kernel(const Kernel& k, const void* u, void* v, double* resid, const u64* maxword, int flags,
                                 cudaStream_t s);
 constexpr int kFxIn = 1, kFxOut = 2;  // JFX_IN_F64, JFX_OUT_F64
+// Default limit of one bounded device wait (staged kernels): 2 s.
+constexpr int64_t kDefaultTimeoutNs = 2000000000;
 // Enqueue the max-abs pre-pass of `n` doubles into maxword (zeroing it first).
 cudaError_t launch_maxabs(const double* u, long long n, u64* maxword, cudaStream_t s);
 cudaError_t launch_fill_skipped(double* resid, int n, int T, cudaStream_t s);

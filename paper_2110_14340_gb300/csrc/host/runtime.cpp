@@ -211,14 +211,14 @@ static std::string jit_source(const Kernel& k) {
                 "  static constexpr int fk = %d, fpath = %d;\n"
                 "};\n"
                 "extern \"C\" __global__ void __launch_bounds__(%d) jacc_jit(const %s* __restrict__ u, "
-                "%s* __restrict__ v, JParams, double* resid, const u64* maxword, int flags) {\n"
+                "%s* __restrict__ v, JParams rt, double* resid, const u64* maxword, int flags) {\n"
                 "  const JFold f{};\n"
-                "  %s<%s, %d, %d, %d, %d, false>(u, v, f, resid, maxword, flags);\n"
+                "  %s<%s, %d, %d, %d, %d, false>(u, v, f, rt, resid, maxword, flags);\n"
                 "}\n"
                 "extern \"C\" __global__ void __launch_bounds__(%d) jacc_jit_out(const %s* __restrict__ u, "
-                "%s* __restrict__ v, JParams, double* resid, const u64* maxword, int flags) {\n"
+                "%s* __restrict__ v, JParams rt, double* resid, const u64* maxword, int flags) {\n"
                 "  const JFold f{};\n"
-                "  %s<%s, %d, %d, %d, %d, %s>(u, v, f, resid, maxword, flags);\n"
+                "  %s<%s, %d, %d, %d, %d, %s>(u, v, f, rt, resid, maxword, flags);\n"
                 "}\n",
                 (long long)p.nx, (long long)p.ny, (long long)p.nz, p.c0, p.c1, p.c2, p.c3, (long long)p.fa,
                 (long long)p.fb, (long long)p.fw0, (long long)p.fw1, (long long)p.fw2, (long long)p.fw3, p.fk, p.fpath,
@@ -295,7 +295,9 @@ extern "C" jacc_status jacc_specialize(const jacc_kernel_desc* desc, jacc_kernel
     const int64_t ty = static_cast<int64_t>(c.by) * (c.zc / 4);
     k->grid = dim3(static_cast<unsigned>((desc->nx + tx - 1) / tx), static_cast<unsigned>((desc->ny + ty - 1) / ty), 1);
   } else {
-    k->grid = dim3(static_cast<unsigned>((desc->nx + tx - 1) / tx), static_cast<unsigned>((desc->ny + c.by - 1) / c.by),
+    // the staged 27-point FP32 kernel (16-byte columns) gives each thread 2 rows
+    const int64_t ty = static_cast<int64_t>(c.by) * ((desc->stencil == 27 && desc->dtype == 32 && c.vec16) ? 2 : 1);
+    k->grid = dim3(static_cast<unsigned>((desc->nx + tx - 1) / tx), static_cast<unsigned>((desc->ny + ty - 1) / ty),
                    static_cast<unsigned>((desc->nz + c.zc - 1) / c.zc));
   }
   if (desc->tblock > 1) {
@@ -322,17 +324,52 @@ extern "C" jacc_status jacc_specialize(const jacc_kernel_desc* desc, jacc_kernel
     k->func_out = table_entry(desc->stencil, desc->dtype, tile, true);
     if (!k->func || !k->func_out) return fail(JACC_ERR_UNSUPPORTED, "no precompiled kernel for this descriptor");
   }
-  if (desc->dtype == 64 && p.fpath != JACC_FP_NONE) {
-    st = cuda_check(cudaMalloc(reinterpret_cast<void**>(&k->scratch), 256), "cudaMalloc(scratch)");
-    if (st) {
-      if (k->lib) cudaLibraryUnload(k->lib);
-      return st;
-    }
+  // scratch words: [0] max|u| bits of direct FP64 fixed-point launches, [1] the
+  // device status word of bounded waits (JACC_DEV_TIMEOUT)
+  st = cuda_check(cudaMalloc(reinterpret_cast<void**>(&k->scratch), 256), "cudaMalloc(scratch)");
+  if (!st) st = cuda_check(cudaMemset(k->scratch, 0, 256), "cudaMemset(scratch)");
+  if (st) {
+    if (k->scratch) cudaFree(k->scratch);
+    if (k->lib) cudaLibraryUnload(k->lib);
+    return st;
   }
+  p.status = reinterpret_cast<int*>(k->scratch + 1);
+  p.timeout_ns = kDefaultTimeoutNs;
+  p.stall_plane = -1;
   k->refcount = 1;
   Kernel* raw = k.release();
   cache()[key] = raw;
   *out = reinterpret_cast<jacc_kernel>(raw);
+  return ok();
+}
+
+extern "C" jacc_status jacc_kernel_status(jacc_kernel h, int32_t* status) {
+  if (!h || !status) return fail(JACC_ERR_INVALID_ARG, "NULL handle or output");
+  const Kernel& k = *reinterpret_cast<Kernel*>(h);
+  jacc_status st = cuda_check(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+  if (st) return st;
+  int v = 0;
+  st = cuda_check(cudaMemcpy(&v, k.params.status, sizeof(int), cudaMemcpyDeviceToHost), "read status word");
+  if (!st) st = cuda_check(cudaMemset(k.params.status, 0, sizeof(int)), "clear status word");
+  if (st) return st;
+  *status = v;
+  return ok();
+}
+
+extern "C" jacc_status jacc_kernel_set_wait(jacc_kernel h, int32_t timeout_ms, int32_t stall_plane) {
+  if (!h) return fail(JACC_ERR_INVALID_ARG, "NULL handle");
+  if (timeout_ms < 0 || stall_plane < -1) return fail(JACC_ERR_INVALID_ARG, "timeout_ms < 0 or stall_plane < -1");
+  std::lock_guard<std::mutex> lock(global_mutex());
+  Kernel& k = *reinterpret_cast<Kernel*>(h);
+  k.params.timeout_ns = timeout_ms == 0 ? kDefaultTimeoutNs : static_cast<int64_t>(timeout_ms) * 1000000;
+  k.params.stall_plane = stall_plane;
+  // cached graphs hold the old parameters: drop them
+  for (auto& g : k.graphs) {
+    if (g.second.exec) cudaGraphExecDestroy(g.second.exec);
+    if (g.second.graph) cudaGraphDestroy(g.second.graph);
+    if (g.second.scratch) cudaFree(g.second.scratch);
+  }
+  k.graphs.clear();
   return ok();
 }
 

@@ -785,6 +785,264 @@ JD void box27_body2(const T* __restrict__ u, T* __restrict__ v, const P& p, SumA
   }
 }
 
+// ---------------------------------------------------------------- bulk-copy staged planes
+//
+// Plane staging with the bulk-copy engine: cp.async.bulk copies rows of the
+// input field from global to shared memory and counts the bytes that landed
+// on an mbarrier of the stage ("full"); no register holds data in flight, so
+// a CTA keeps up to S planes outstanding at no register cost.  Each stage
+// also has an "empty" mbarrier on which every warp arrives once it has read
+// the stage; warp 0 waits on it before it reuses the stage.  Every wait gives
+// up after JParams::timeout_ns (%globaltimer), records JACC_DEV_TIMEOUT and
+// lets the CTA finish; before it returns, warp 0 waits (bounded too) for the
+// copies it has issued, so no copy targets the shared memory of a CTA that
+// has exited.
+
+JD u32 smem_u32(const void* ptr) { return (u32)__cvta_generic_to_shared(ptr); }
+JD u64 gtimer_ns() {
+  u64 t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+JD void mbar_init(u64* bar, u32 count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+JD void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+JD void mbar_expect_tx(u64* bar, u32 bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+JD void mbar_arrive(u64* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+JD bool mbar_try(u64* bar, u32 parity) {
+  u32 done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Waits for the completion of the phase with the given parity; false after
+// limit_ns without it.
+JD bool mbar_wait(u64* bar, u32 parity, i64 limit_ns) {
+  if (mbar_try(bar, parity)) return true;
+  const u64 t0 = gtimer_ns();
+  while (!mbar_try(bar, parity))
+    if ((i64)(gtimer_ns() - t0) > limit_ns) return false;
+  return true;
+}
+// One bulk copy global -> shared (16-byte aligned addresses, size a multiple
+// of 16), completion counted in bytes on `bar`.
+JD void bulk_g2s(void* dst, const void* src, u32 bytes, u64* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// Geometry of the staged 27-point FP32 kernel: BX x BY threads, each owning 4
+// consecutive columns (one 16-byte vector) of 2 consecutive rows, so a CTA
+// computes a TW x TH tile per plane.  A stage holds R = TH + 2 rows of
+// W = TW + 8 floats: slot i of staged row r is column (bx0 - 4 + i) mod nx of
+// row (by0 - 1 + r) mod ny (the periodic images, so halo columns and rows need
+// no special case).  The halo is 4 columns wide on each side because bulk
+// copies move whole 16-byte units; columns bx0 - 1 and bx0 + TW are used.
+template <int BX, int BY> struct Box27S {
+  static constexpr int RY = 2;
+  static constexpr int TW = BX * 4, TH = BY * RY;
+  static constexpr int W = TW + 8, R = TH + 2;
+  static constexpr int STAGE_BYTES = W * R * 4;
+  static constexpr int S0 = 40960 / STAGE_BYTES;
+  static constexpr int S = S0 < 2 ? 2 : (S0 > 4 ? 4 : S0);  // stages, 2..4, at most ~40 KB
+  static constexpr int NW = BX * BY / 32;
+};
+
+template <int BX, int BY> struct alignas(128) Box27SSmem {
+  float st[Box27S<BX, BY>::S][Box27S<BX, BY>::R][Box27S<BX, BY>::W];
+  u64 full[Box27S<BX, BY>::S];
+  u64 empty[Box27S<BX, BY>::S];
+};
+
+// Warp 0 requests staged plane zg into stage s: lane 0 posts the byte count,
+// then lane r copies staged row r as one bulk copy, or as two or more where
+// the row's slots wrap around the periodic x boundary.
+template <int BX, int BY, class P>
+JD void box27s_issue(Box27SSmem<BX, BY>& sm, int s, const float* __restrict__ u, const P& p, i64 zg, i64 bx0, i64 by0,
+                     int weff) {
+  typedef Box27S<BX, BY> G;
+  const i64 nx = p.nx, ny = p.ny;
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) mbar_expect_tx(&sm.full[s], (u32)(G::R * weff * 4));
+  __syncwarp();
+  for (int r = lane; r < G::R; r += 32) {
+    i64 yg = (by0 - 1 + r) % ny;
+    if (yg < 0) yg += ny;
+    const float* row = u + (zg * ny + yg) * nx;
+    float* dst = &sm.st[s][r][0];
+    i64 c = bx0 - 4;
+    if (c < 0) c += nx;
+    int i = 0;
+    while (i < weff) {
+      i64 len = nx - c;
+      if (len > weff - i) len = weff - i;
+      bulk_g2s(dst + i, row + c, (u32)(len * 4), &sm.full[s]);
+      i += (int)len;
+      c = 0;
+    }
+  }
+}
+
+// One staged plane -> the per-point plane terms of the thread's 2 x 4 points:
+// A = wf c + we f + wc g (the plane's contribution as an upper or lower
+// neighbour plane) and B = w0 c + wf f + we g (as the centre plane), where c
+// is the point, f the sum of its 4 in-plane face neighbours and g of its 4
+// in-plane diagonal neighbours.  Row sums r[x-1] + r[x+1] are shared by the
+// two output rows.
+template <int BX, int BY>
+JD void box27s_terms(const float (*st)[Box27S<BX, BY>::W], float w0, float wf, float we, float wc, float (&A)[2][4],
+                     float (&B)[2][4]) {
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  float r[4][6];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) lds_row<float, 4>(&st[2 * ty + k][4 + 4 * tx], r[k]);
+  float s[4][4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) s[k][e] = r[k][e] + r[k][e + 2];
+#pragma unroll
+  for (int yy = 0; yy < 2; ++yy)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float c = r[yy + 1][e + 1];
+      const float f = s[yy + 1][e] + (r[yy][e + 1] + r[yy + 2][e + 1]);
+      const float g = s[yy][e] + s[yy + 2][e];
+      A[yy][e] = fmaf(wc, g, fmaf(we, f, wf * c));
+      B[yy][e] = fmaf(we, g, fmaf(wf, f, w0 * c));
+    }
+}
+
+// The staged periodic 27-point FP32 sweep of one CTA tile: planes z0-1 ..
+// z1 are staged (L = z1 - z0 + 2), output plane z = A(z-1) + B(z) + A(z+1)
+// is formed as P + A(z+1) with P = A(z-1) + B(z) kept in registers.  Returns
+// the thread's double-float sum of its outputs (want_sum).
+template <int BX, int BY, int ZC, class P>
+JD double box27s_body(const float* __restrict__ u, float* __restrict__ v, const P& p, const JParams& rt,
+                      bool want_sum) {
+  typedef Box27S<BX, BY> G;
+  __shared__ Box27SSmem<BX, BY> sm;
+  const i64 nx = p.nx, ny = p.ny, nz = p.nz, sz = nx * ny;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * BX + tx;
+  const bool warp0 = tid < 32;
+  const i64 bx0 = (i64)blockIdx.x * G::TW, by0 = (i64)blockIdx.y * G::TH;
+  const i64 z0 = (i64)blockIdx.z * ZC;
+  const i64 z1 = (z0 + ZC < nz) ? z0 + ZC : nz;
+  const int L = (int)(z1 - z0) + 2;
+  const int weff = (int)((nx - bx0 < G::TW) ? nx - bx0 : G::TW) + 8;
+  const i64 lim = rt.timeout_ns;
+  const bool stall_cta = rt.stall_plane >= 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0;
+  if (tid == 0) {
+#pragma unroll
+    for (int s = 0; s < G::S; ++s) {
+      mbar_init(&sm.full[s], 1);
+      mbar_init(&sm.empty[s], G::NW);
+    }
+    mbar_init_fence();
+  }
+  __syncthreads();
+  auto plane_z = [&](int j) {
+    i64 z = (z0 - 1 + j) % nz;
+    return z < 0 ? z + nz : z;
+  };
+  auto request = [&](int j) {
+    if (!(stall_cta && j == rt.stall_plane)) box27s_issue<BX, BY>(sm, j % G::S, u, p, plane_z(j), bx0, by0, weff);
+  };
+  int issued = 0, consumed = 0;  // warp 0's counts of requested and waited planes
+  if (warp0)
+    for (; issued < G::S && issued < L; ++issued) request(issued);
+
+  const float w0 = (float)p.c0, wf = (float)p.c1, we = (float)p.c2, wc = (float)p.c3;
+  const i64 x0 = bx0 + 4 * tx, y0 = by0 + 2 * ty;
+  const bool ax = x0 < nx, ay0 = ax && y0 < ny, ay1 = ax && y0 + 1 < ny;
+  float* vo = v + y0 * nx + x0 + z0 * sz;
+  float Ac[2][4], Pz[2][4];
+  float hi = 0.0f, lo = 0.0f;
+  bool ok = true;
+  // consume plane j: wait for it, form its terms, release its stage, and let
+  // warp 0 refill the stage of plane j - 1
+  auto consume = [&](int j, float (&A)[2][4], float (&B)[2][4]) -> bool {
+    const int s = j % G::S;
+    if (!mbar_wait(&sm.full[s], (u32)((j / G::S) & 1), lim)) return false;
+    consumed = j + 1;
+    box27s_terms<BX, BY>(sm.st[s], w0, wf, we, wc, A, B);
+    __syncwarp();
+    if ((tid & 31) == 0) mbar_arrive(&sm.empty[s]);
+    if (warp0 && j >= 1 && issued < L) {
+      const int q = j - 1;
+      if (!mbar_wait(&sm.empty[q % G::S], (u32)((q / G::S) & 1), lim)) return false;
+      request(issued);
+      ++issued;
+    }
+    return true;
+  };
+  {
+    float A[2][4], B[2][4];
+    ok = consume(0, A, B);
+    if (ok) {
+#pragma unroll
+      for (int yy = 0; yy < 2; ++yy)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) Ac[yy][e] = A[yy][e];
+      ok = consume(1, A, B);
+    }
+    if (ok) {
+#pragma unroll
+      for (int yy = 0; yy < 2; ++yy)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          Pz[yy][e] = Ac[yy][e] + B[yy][e];
+          Ac[yy][e] = A[yy][e];
+        }
+    }
+  }
+  if (ok) {
+#pragma unroll 2
+    for (int j = 2; j < L; ++j) {
+      float A[2][4], B[2][4];
+      if (!consume(j, A, B)) {
+        ok = false;
+        break;
+      }
+      float o[2][4];
+#pragma unroll
+      for (int yy = 0; yy < 2; ++yy)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          o[yy][e] = Pz[yy][e] + A[yy][e];
+          Pz[yy][e] = Ac[yy][e] + B[yy][e];
+          Ac[yy][e] = A[yy][e];
+        }
+      if (ay0) stv<float, 4>(vo, o[0]);
+      if (ay1) stv<float, 4>(vo + nx, o[1]);
+      vo += sz;
+      if (want_sum) {
+        const float t0 = ay0 ? (o[0][0] + o[0][1]) + (o[0][2] + o[0][3]) : 0.0f;
+        const float t1 = ay1 ? (o[1][0] + o[1][1]) + (o[1][2] + o[1][3]) : 0.0f;
+        two_sum_acc(hi, lo, t0 + t1);
+      }
+    }
+  }
+  if (!ok) {
+    if (rt.status) atomicExch(rt.status, JACC_DEV_TIMEOUT);
+    if (warp0)
+      for (int j = consumed; j < issued; ++j)
+        if (!(stall_cta && j == rt.stall_plane)) mbar_wait(&sm.full[j % G::S], (u32)((j / G::S) & 1), lim);
+  }
+  return (double)hi + (double)lo;
+}
+
 // ---------------------------------------------------------------- 27-point periodic box, temporal blocking (FP32)
 //
 // TT sweeps per launch.  A CTA of 32 x RY threads (4 floats each in x) loads
@@ -1288,7 +1546,10 @@ JD void box27_fx_body(const double* __restrict__ u, double* __restrict__ v, cons
 // ====================================================================== kernels
 //
 // Every stencil kernel has the signature
-//   (const T* u, T* v, P p, double* resid, const u64* maxword, int flags)
+//   (const T* u, T* v, JParams p, double* resid, const u64* maxword, int flags)
+// and calls an entry below with P = JParams (precompiled) or P = a struct of
+// constants (NVRTC); the runtime-only fields (status word, wait limits) are
+// read from the JParams argument `rt` in both cases.
 // resid (nullable) receives the fused reduction via one atomic per CTA (it
 // must be zeroed before the launch); maxword (FP64 only, nullable) holds the
 // bit pattern of max|u| written by jacc_k_maxabs, which selects the fixed
@@ -1300,8 +1561,8 @@ JD void box27_fx_body(const double* __restrict__ u, double* __restrict__ v, cons
 // last sweeps and single launches.
 
 template <class T, int BX, int BY, int V, int ZC, bool EDGE, class P>
-JD void jacobi2d_entry(const T* __restrict__ u, T* __restrict__ v, const P& p, double* resid, const u64* maxword,
-                       int flags) {
+JD void jacobi2d_entry(const T* __restrict__ u, T* __restrict__ v, const P& p, const JParams& rt, double* resid,
+                       const u64* maxword, int flags) {
   u64 bits = 0;
   const i64 x0 = (i64)blockIdx.x * (BX * V) + (i64)threadIdx.x * V;
   const i64 ys = ((i64)blockIdx.y * BY + threadIdx.y) * ZC;
@@ -1326,8 +1587,8 @@ JD void jacobi2d_entry(const T* __restrict__ u, T* __restrict__ v, const P& p, d
 }
 
 template <class T, int BX, int BY, int V, int ZC, bool EDGE, class P>
-JD void heat3d_entry(const T* __restrict__ u, T* __restrict__ v, const P& p, double* resid, const u64* maxword,
-                     int flags) {
+JD void heat3d_entry(const T* __restrict__ u, T* __restrict__ v, const P& p, const JParams& rt, double* resid,
+                     const u64* maxword, int flags) {
   u64 bits = 0;
   if constexpr (sizeof(T) == 8) {
     const int F = (maxword && p.fpath != JACC_FP_NONE) ? fx_frac_bits(*maxword) : -1;
@@ -1351,8 +1612,8 @@ JD void heat3d_entry(const T* __restrict__ u, T* __restrict__ v, const P& p, dou
 }
 
 template <class T, int BX, int BY, int V, int ZC, bool EDGE, class P>
-JD void box27_entry(const T* __restrict__ u, T* __restrict__ v, const P& p, double* resid, const u64* maxword,
-                    int flags) {
+JD void box27_entry(const T* __restrict__ u, T* __restrict__ v, const P& p, const JParams& rt, double* resid,
+                    const u64* maxword, int flags) {
   double total = 0.0;
   if constexpr (sizeof(T) == 8) {
     const int F = (maxword && p.fpath != JACC_FP_NONE) ? fx_frac_bits(*maxword) : -1;
@@ -1367,6 +1628,8 @@ JD void box27_entry(const T* __restrict__ u, T* __restrict__ v, const P& p, doub
       box27_body2<T, BX, BY, V, ZC>(u, v, p, acc, resid != nullptr, *reinterpret_cast<Plane<double, BX, BY, V>*>(raw));
       total = acc.total();
     }
+  } else if constexpr (V == 4) {
+    total = box27s_body<BX, BY, ZC>(u, v, p, rt, resid != nullptr);
   } else {
     __shared__ Plane<T, BX, BY, V> sm;
     SumAcc<T> acc;
@@ -1418,12 +1681,12 @@ __global__ void jacc_k_fill_skipped(double* resid, int n, int T) {
 template <class T, int BX, int BY, int V, int ZC, bool EDGE>
 __global__ void __launch_bounds__(BX * BY) jacc_k_jacobi2d(const T* __restrict__ u, T* __restrict__ v, JParams p,
                                                            double* resid, const u64* maxword, int flags) {
-  jacobi2d_entry<T, BX, BY, V, ZC, EDGE>(u, v, p, resid, maxword, flags);
+  jacobi2d_entry<T, BX, BY, V, ZC, EDGE>(u, v, p, p, resid, maxword, flags);
 }
 template <class T, int BX, int BY, int V, int ZC, bool EDGE>
 __global__ void __launch_bounds__(BX * BY) jacc_k_heat3d(const T* __restrict__ u, T* __restrict__ v, JParams p,
                                                          double* resid, const u64* maxword, int flags) {
-  heat3d_entry<T, BX, BY, V, ZC, EDGE>(u, v, p, resid, maxword, flags);
+  heat3d_entry<T, BX, BY, V, ZC, EDGE>(u, v, p, p, resid, maxword, flags);
 }
 template <int RY, int TT, int ZC>
 __global__ void __launch_bounds__(TB_BX * RY) jacc_k_box27_tb(const float* __restrict__ u, float* __restrict__ v,
@@ -1433,5 +1696,5 @@ __global__ void __launch_bounds__(TB_BX * RY) jacc_k_box27_tb(const float* __res
 template <class T, int BX, int BY, int V, int ZC, bool EDGE>
 __global__ void __launch_bounds__(BX * BY) jacc_k_box27(const T* __restrict__ u, T* __restrict__ v, JParams p,
                                                         double* resid, const u64* maxword, int flags) {
-  box27_entry<T, BX, BY, V, ZC, EDGE>(u, v, p, resid, maxword, flags);
+  box27_entry<T, BX, BY, V, ZC, EDGE>(u, v, p, p, resid, maxword, flags);
 }

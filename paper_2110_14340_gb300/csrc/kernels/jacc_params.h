@@ -19,4 +19,14 @@ struct JParams {
   i64 fw0, fw1, fw2, fw3;  // JACC_FP_WIDE factors (7pt: fw0 = odd mantissa of r)
   int fk;                  // extra fraction bits of the fixed-point result
   int fpath;               // JACC_FP_*
+  // Bounded waits of the bulk-copy staged kernels: each wait on an mbarrier
+  // gives up after timeout_ns, writes JACC_DEV_TIMEOUT to *status (device,
+  // nullable) and the CTA returns.  stall_plane >= 0 is a test hook: CTA
+  // (0,0,0) never requests that staged plane, so its waits run out.
+  int* status;
+  i64 timeout_ns;
+  int stall_plane;
+  int reserved;
 };
+
+#define JACC_DEV_TIMEOUT (-6)  // the value of JACC_ERR_TIMEOUT

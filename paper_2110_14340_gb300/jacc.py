@@ -93,6 +93,8 @@ SIGNATURES = {
     "jacc_specialize": ([P, P], C.c_int32),
     "jacc_kernel_info": ([P, P], C.c_int32),
     "jacc_release": ([P], C.c_int32),
+    "jacc_kernel_status": ([P, P], C.c_int32),
+    "jacc_kernel_set_wait": ([P, C.c_int32, C.c_int32], C.c_int32),
     "jacc_tile_info": ([C.c_int32, P], C.c_int32),
     "jacc_launch": ([P, P, P, P, C.c_size_t], C.c_int32),
     "jacc_launch_static": ([P, P, P, P, C.c_size_t], C.c_int32),
@@ -227,6 +229,16 @@ class Kernel(Desc):
         _check(lib().jacc_kernel_info(self.handle, C.byref(i)))
         return dict(tile_id=i.tile_id, jit=bool(i.jit), fixed_point=bool(i.fixed_point), tblock=i.tblock,
                     block=tuple(i.block), grid=tuple(i.grid), compile_ms=i.compile_ms)
+
+    def status(self):
+        """Read and clear the device status word (0 or TIMEOUT); synchronises."""
+        v = C.c_int32()
+        _check(lib().jacc_kernel_status(self.handle, C.byref(v)))
+        return v.value
+
+    def set_wait(self, timeout_ms=0, stall_plane=-1):
+        """Limit of each bounded device wait (0: default) and the stall test hook."""
+        _check(lib().jacc_kernel_set_wait(self.handle, int(timeout_ms), int(stall_plane)))
 
     def release(self):
         if self.handle:

@@ -195,6 +195,53 @@ def test_box27_impulse_response_exact():
     assert np.count_nonzero(g) == 27
 
 
+@pytest.mark.parametrize("tile", [1, 3, 11, 23])
+@pytest.mark.parametrize("shape", [(3, 3, 4), (5, 17, 8), (4, 3, 524), (70, 9, 12)])
+def test_box27_f32_staged_small_and_ragged(orc, tile, shape):
+    # 16-byte-column tiles stage planes with bulk copies: widths below one
+    # tile, rows and planes that wrap several times, a 4-wide halo at nx = 4
+    nz, ny, nx = shape
+    u = inputs.box27_field(nx, ny, nz, seed=12)
+    k = jacc.Kernel(jacc.STENCIL_27PT, jacc.F32, nx, ny, nz, coeffs=tuple(float(w) for w in W), tile_id=tile)
+    g, gs = run(k, u, 3)
+    o, osum = orc.box27_run(u, W, 3)
+    assert nerr(g, o) <= TOL32
+    assert np.max(np.abs(gs - osum)) <= 1e-6 * float(np.sum(np.abs(o.astype(np.float64))))
+    assert k.status() == 0
+
+
+@pytest.mark.parametrize("tile", [1, 3])
+def test_box27_staged_impulse_response_exact(tile):
+    nz, ny, nx = 6, 7, 8
+    u = np.zeros((nz, ny, nx), dtype=np.float32)
+    u[0, 0, 0] = 1.0
+    k = jacc.Kernel(jacc.STENCIL_27PT, jacc.F32, nx, ny, nz, coeffs=tuple(float(w) for w in W), tile_id=tile)
+    g, _ = run(k, u, 1)
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                assert g[dz % nz, dy % ny, dx % nx] == W[(dz != 0) + (dy != 0) + (dx != 0)]
+    assert np.count_nonzero(g) == 27
+
+
+def test_box27_staged_wait_timeout_is_reported_and_recoverable(orc):
+    # CTA (0,0,0) never requests staged plane 3: its mbarrier waits run out
+    # after 20 ms, the status word says TIMEOUT, and the context stays usable
+    nz, ny, nx = 40, 20, 256
+    u = inputs.box27_field(nx, ny, nz, seed=13)
+    k = jacc.Kernel(jacc.STENCIL_27PT, jacc.F32, nx, ny, nz, coeffs=tuple(float(w) for w in W), tile_id=3)
+    assert k.status() == 0
+    k.set_wait(timeout_ms=20, stall_plane=3)
+    run(k, u, 1, graph=False)
+    assert k.status() == jacc.ERR_TIMEOUT
+    assert k.status() == 0  # reading clears it
+    k.set_wait()
+    g, _ = run(k, u, 2)
+    o, _ = orc.box27_run(u, W, 2)
+    assert nerr(g, o) <= TOL32
+    assert k.status() == 0
+
+
 # ----------------------------------------------------------------------------- specialisation and graphs
 
 @pytest.mark.parametrize("stencil,dtype,shape,coeffs", [
