@@ -80,6 +80,8 @@ std::mutex& global_mutex();
 // Tile validity for a descriptor (vector width and grid limits) and the
 // default tile; the autotuner's remembered pick for a shape (-1 if none).
 bool tile_valid(const jacc_kernel_desc& d, int t);
+// Tiles that run a bulk-copy staged kernel (2 rows per thread).
+bool staged_tile(const jacc_kernel_desc& d, int t);
 int default_tile(const jacc_kernel_desc& d);
 int tuned_tile(const jacc_kernel_desc& d);
 void remember_tile(const jacc_kernel_desc& d, int tile);

@@ -174,6 +174,10 @@ int default_tile(const jacc_kernel_desc& d) {
   return vec_ok ? 15 : 14;
 }
 
+bool staged_tile(const jacc_kernel_desc& d, int t) {
+  return kTiles[t].vec16 && (d.stencil == 7 || (d.stencil == 27 && d.dtype == 32));
+}
+
 bool tile_valid(const jacc_kernel_desc& d, int t) {
   const TileCfg& c = kTiles[t];
   const int V = c.vec16 ? (d.dtype == 64 ? 2 : 4) : 1;
@@ -295,8 +299,8 @@ extern "C" jacc_status jacc_specialize(const jacc_kernel_desc* desc, jacc_kernel
     const int64_t ty = static_cast<int64_t>(c.by) * (c.zc / 4);
     k->grid = dim3(static_cast<unsigned>((desc->nx + tx - 1) / tx), static_cast<unsigned>((desc->ny + ty - 1) / ty), 1);
   } else {
-    // the staged 27-point FP32 kernel (16-byte columns) gives each thread 2 rows
-    const int64_t ty = static_cast<int64_t>(c.by) * ((desc->stencil == 27 && desc->dtype == 32 && c.vec16) ? 2 : 1);
+    // the staged kernels (16-byte columns: 7-point, and 27-point FP32) give each thread 2 rows
+    const int64_t ty = static_cast<int64_t>(c.by) * (staged_tile(*desc, tile) ? 2 : 1);
     k->grid = dim3(static_cast<unsigned>((desc->nx + tx - 1) / tx), static_cast<unsigned>((desc->ny + ty - 1) / ty),
                    static_cast<unsigned>((desc->nz + c.zc - 1) / c.zc));
   }

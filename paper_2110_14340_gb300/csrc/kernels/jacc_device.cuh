@@ -397,13 +397,13 @@ JD void put_plane(Plane<typename WT<T, MODE>::type, BX, BY, V>& sm, int b, const
 
 template <class T, int BX, int BY, int V, int ZC, int MODE, class P>
 JD void heat3d_body(const T* __restrict__ u, T* __restrict__ v, const P& p, int F, typename RT<T, MODE>::type& rmax,
-                    Plane<typename WT<T, MODE>::type, BX, BY, V>& sm) {
+                    Plane<typename WT<T, MODE>::type, BX, BY, V>& sm, int ys_mul = 1, int ysub = 0) {
   typedef typename WT<T, MODE>::type W;
   const i64 nx = p.nx, ny = p.ny, nz = p.nz;
   const i64 sz = nx * ny;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const i64 bx0 = (i64)blockIdx.x * (BX * V);
-  const i64 by0 = (i64)blockIdx.y * BY;
+  const i64 by0 = ((i64)blockIdx.y * ys_mul + ysub) * BY;  // a CTA may cover ys_mul tiles of BY rows
   const i64 x0 = bx0 + (i64)tx * V;
   const i64 y = by0 + ty;
   const bool act = (x0 < nx) && (y < ny);
@@ -1438,6 +1438,304 @@ JD void heat3d_fx_body(const double* __restrict__ u, double* __restrict__ v, con
 
 // Residual of the heat sweep from max |L|: r max|L| scaled.
 
+// ---------------------------------------------------------------- 7-point heat, bulk-copy staged planes
+//
+// Same staging as the 27-point kernel (bulk copies on full/empty mbarriers,
+// bounded waits), Dirichlet geometry: a thread owns one 16-byte column (V
+// values) of 2 rows; a stage holds rows by0-1 .. by0+TH and columns
+// bx0-V .. bx0+TW+V-1 of one plane, clipped to the grid (points outside are
+// never needed: only interior points read neighbours).  Planes z0-1 .. z1 are
+// staged; a thread keeps its own values of planes z-1 and z in registers,
+// reads its own values of plane z+1 and the in-plane neighbours of plane z
+// (rows y-1 and y+2, the columns left and right of its own) from the stage.
+// The boundary planes z = 0 and nz-1 are written from the staged values.
+//
+// FX: FP64 storage in the resident 64-bit fixed point (EDGE: the first/last
+// sweep converts on load/store); otherwise native arithmetic on T.
+template <class T, int BX, int BY> struct Heat3S {
+  static constexpr int V = 16 / (int)sizeof(T);
+  static constexpr int RY = 2;
+  static constexpr int TW = BX * V, TH = BY * RY;
+  static constexpr int W = TW + 2 * V, R = TH + 2;
+  static constexpr int STAGE_BYTES = W * R * (int)sizeof(T);
+  static constexpr int S0 = 45056 / STAGE_BYTES;
+  static constexpr int S = S0 < 2 ? 2 : (S0 > 4 ? 4 : S0);
+  // A step needs planes z and z+1 staged.  With S >= 3 warp 0 refills the
+  // stage released one step earlier (slack for lagging warps); with S = 2 it
+  // refills the stage just released, and no plane is prefetched.
+  static constexpr int D = S >= 3 ? 1 : 0;
+  static constexpr int NW = BX * BY / 32;
+};
+
+template <class T, int BX, int BY> struct alignas(128) Heat3SSmem {
+  T st[Heat3S<T, BX, BY>::S][Heat3S<T, BX, BY>::R][Heat3S<T, BX, BY>::W];
+  u64 full[Heat3S<T, BX, BY>::S];
+  u64 empty[Heat3S<T, BX, BY>::S];
+};
+
+// Warp 0 requests plane zg into stage s: one bulk copy per staged row inside
+// the grid; lane 0 first posts the byte count of the whole plane.
+template <class T, int BX, int BY, class P>
+JD void heat3s_issue(Heat3SSmem<T, BX, BY>& sm, int s, const T* __restrict__ u, const P& p, i64 zg, i64 bx0, i64 by0) {
+  typedef Heat3S<T, BX, BY> G;
+  const i64 nx = p.nx, ny = p.ny;
+  const int lane = threadIdx.x & 31;
+  const i64 c0 = bx0 - G::V < 0 ? 0 : bx0 - G::V;
+  const i64 c1 = bx0 + G::TW + G::V > nx ? nx : bx0 + G::TW + G::V;
+  const i64 r0 = by0 - 1 < 0 ? 0 : by0 - 1;
+  const i64 r1 = by0 + G::TH + 1 > ny ? ny : by0 + G::TH + 1;
+  const u32 row_bytes = (u32)((c1 - c0) * (i64)sizeof(T));
+  if (lane == 0) mbar_expect_tx(&sm.full[s], row_bytes * (u32)(r1 - r0));
+  __syncwarp();
+  for (i64 y = r0 + lane; y < r1; y += 32)
+    bulk_g2s(&sm.st[s][y - (by0 - 1)][c0 - (bx0 - G::V)], u + (zg * ny + y) * nx + c0, row_bytes, &sm.full[s]);
+}
+
+// 16-byte shared-memory vector reads (bit patterns kept).
+JD void lds_vec(const void* p, float (&r)[4]) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  r[0] = t.x; r[1] = t.y; r[2] = t.z; r[3] = t.w;
+}
+JD void lds_vec(const void* p, double (&r)[2]) {
+  const double2 t = *reinterpret_cast<const double2*>(p);
+  r[0] = t.x; r[1] = t.y;
+}
+JD void lds_vec(const void* p, i64 (&r)[2]) {
+  const longlong2 t = *reinterpret_cast<const longlong2*>(p);
+  r[0] = t.x; r[1] = t.y;
+}
+
+template <class T, bool FX> struct HeatAcc { typedef T type; };
+template <> struct HeatAcc<double, true> { typedef u64 type; };
+
+template <class T, int BX, int BY, int ZC, bool FX, bool EDGE, class P>
+JD void heat3s_body(const T* __restrict__ u, T* __restrict__ v, const P& p, const JParams& rt, int F, int flags,
+                    typename HeatAcc<T, FX>::type& rmax, Heat3SSmem<T, BX, BY>& sm) {
+  typedef Heat3S<T, BX, BY> G;
+  constexpr int V = G::V;
+  typedef typename WT<T, FX ? JM_FIXED : JM_NATIVE>::type Wt;  // working type: i64 (fixed) or T
+  const i64 nx = p.nx, ny = p.ny, nz = p.nz, sz = nx * ny;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * BX + tx;
+  const bool warp0 = tid < 32;
+  const i64 bx0 = (i64)blockIdx.x * G::TW, by0 = (i64)blockIdx.y * G::TH;
+  const i64 x0 = bx0 + (i64)tx * V, y0 = by0 + 2 * ty;
+  const bool ax = x0 < nx;
+  const bool ay[2] = {ax && y0 < ny, ax && y0 + 1 < ny};
+  const bool yi[2] = {y0 >= 1 && y0 <= ny - 2, y0 + 1 >= 1 && y0 + 1 <= ny - 2};
+  const i64 cz0 = (i64)blockIdx.z * ZC;
+  const i64 cz1 = (cz0 + ZC < nz) ? cz0 + ZC : nz;
+  const i64 z0 = cz0 < 1 ? 1 : cz0;
+  const i64 z1 = cz1 > nz - 1 ? nz - 1 : cz1;
+  const bool inf = FX && EDGE && (flags & JFX_IN_F64);
+  const bool outf = FX && EDGE && (flags & JFX_OUT_F64);
+  // raw input word -> working value, and a boundary point's output word
+  auto cvt = [&](T raw) -> Wt {
+    if constexpr (FX) return inf ? fx_from(raw, F) : bits_i64(raw);
+    else return raw;
+  };
+  auto bnd_out = [&](T raw) -> T {
+    if constexpr (FX && EDGE) {
+      if (inf == outf) return raw;
+      if (outf) return fx_to(bits_i64(raw), F);
+      return i64_bits(fx_from(raw, F));
+    } else {
+      return raw;
+    }
+  };
+  if (z0 >= z1) {  // a chunk holding only a boundary plane (block-uniform)
+    for (i64 z = cz0; z < cz1; ++z)
+#pragma unroll
+      for (int yy = 0; yy < 2; ++yy)
+        if (ay[yy]) {
+          T t[V];
+          ldv<T, V>(u + z * sz + (y0 + yy) * nx + x0, t);
+#pragma unroll
+          for (int e = 0; e < V; ++e) t[e] = bnd_out(t[e]);
+          stv<T, V>(v + z * sz + (y0 + yy) * nx + x0, t);
+        }
+    return;
+  }
+  const int L = (int)(z1 - z0) + 2;  // staged planes z0-1 .. z1
+  const i64 lim = rt.timeout_ns;
+  const bool stall_cta = rt.stall_plane >= 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0;
+  if (tid == 0) {
+#pragma unroll
+    for (int s = 0; s < G::S; ++s) {
+      mbar_init(&sm.full[s], 1);
+      mbar_init(&sm.empty[s], G::NW);
+    }
+    mbar_init_fence();
+  }
+  __syncthreads();
+  auto request = [&](int j) {
+    if (!(stall_cta && j == rt.stall_plane)) heat3s_issue<T, BX, BY>(sm, j % G::S, u, p, z0 - 1 + j, bx0, by0);
+  };
+  int issued = 0, consumed = 0;
+  if (warp0)
+    for (; issued < G::S && issued < L; ++issued) request(issued);
+  bool ok = true;
+  auto wait_full = [&](int j) -> bool {
+    if (!mbar_wait(&sm.full[j % G::S], (u32)((j / G::S) & 1), lim)) return false;
+    consumed = j + 1;
+    return true;
+  };
+  // release plane j (this warp has read it for the last time); warp 0 then
+  // refills the stage of plane j - D once every warp has released it
+  auto release = [&](int j) -> bool {
+    __syncwarp();
+    if ((tid & 31) == 0) mbar_arrive(&sm.empty[j % G::S]);
+    if (warp0 && j >= G::D && issued < L) {
+      const int q = j - G::D;
+      if (!mbar_wait(&sm.empty[q % G::S], (u32)((q / G::S) & 1), lim)) return false;
+      request(issued);
+      ++issued;
+    }
+    return true;
+  };
+  // own values of staged plane j (raw words), rows y0, y0+1
+  auto own = [&](int j, T (&raw)[2][V]) {
+#pragma unroll
+    for (int yy = 0; yy < 2; ++yy) lds_vec(&sm.st[j % G::S][2 * ty + 1 + yy][V + V * tx], raw[yy]);
+  };
+  T rzp[2][V], rcur[2][V], rzn[2][V];
+  Wt zp[2][V], cur[2][V];
+  T* vo = v + y0 * nx + x0;
+  const i64 ri = (nx - 2) - x0;  // last interior column relative to x0
+  ok = wait_full(0);
+  if (ok) {
+    own(0, rzp);
+    if (cz0 == 0) {  // boundary plane 0
+#pragma unroll
+      for (int yy = 0; yy < 2; ++yy)
+        if (ay[yy]) {
+          T t[V];
+#pragma unroll
+          for (int e = 0; e < V; ++e) t[e] = bnd_out(rzp[yy][e]);
+          stv<T, V>(vo + yy * nx, t);
+        }
+    }
+#pragma unroll
+    for (int yy = 0; yy < 2; ++yy)
+#pragma unroll
+      for (int e = 0; e < V; ++e) zp[yy][e] = cvt(rzp[yy][e]);
+    ok = release(0) && wait_full(1);
+  }
+  if (ok) {
+    own(1, rcur);
+#pragma unroll
+    for (int yy = 0; yy < 2; ++yy)
+#pragma unroll
+      for (int e = 0; e < V; ++e) cur[yy][e] = cvt(rcur[yy][e]);
+  }
+  const T r = (T)p.c0;
+  const i64 fb = p.fb, fw0 = p.fw0;
+  const int k = p.fk;
+  const bool small = p.fpath == JACC_FP_SMALL;
+  vo += z0 * sz;
+  if (ok) {
+    for (int j = 1; j <= L - 2; ++j) {
+      if (!wait_full(j + 1)) {
+        ok = false;
+        break;
+      }
+      own(j + 1, rzn);
+      const Wt(*pl)[G::W] = reinterpret_cast<const Wt(*)[G::W]>(sm.st[j % G::S]);
+      Wt ym[V], yp[V], xl[2], xr[2];
+      lds_vec(&pl[2 * ty][V + V * tx], ym);
+      lds_vec(&pl[2 * ty + 3][V + V * tx], yp);
+#pragma unroll
+      for (int yy = 0; yy < 2; ++yy) {
+        xl[yy] = pl[2 * ty + 1 + yy][V + V * tx - 1];
+        xr[yy] = pl[2 * ty + 1 + yy][V + V * tx + V];
+      }
+      if constexpr (FX && EDGE) {
+        if (inf) {
+#pragma unroll
+          for (int e = 0; e < V; ++e) {
+            ym[e] = fx_from(i64_bits(ym[e]), F);
+            yp[e] = fx_from(i64_bits(yp[e]), F);
+          }
+#pragma unroll
+          for (int yy = 0; yy < 2; ++yy) {
+            xl[yy] = fx_from(i64_bits(xl[yy]), F);
+            xr[yy] = fx_from(i64_bits(xr[yy]), F);
+          }
+        }
+      }
+      Wt zn[2][V];
+#pragma unroll
+      for (int yy = 0; yy < 2; ++yy)
+#pragma unroll
+        for (int e = 0; e < V; ++e) zn[yy][e] = cvt(rzn[yy][e]);
+#pragma unroll
+      for (int yy = 0; yy < 2; ++yy) {
+        T out[V];
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+          const bool in = yi[yy] && (x0 + e >= 1) && (e <= ri);
+          const Wt a = (e == 0) ? xl[yy] : cur[yy][e - 1];
+          const Wt b = (e == V - 1) ? xr[yy] : cur[yy][e + 1];
+          const Wt c = yy == 0 ? ym[e] : cur[0][e];
+          const Wt d = yy == 0 ? cur[1][e] : yp[e];
+          const Wt sum = ((a + b) + (c + d)) + (zp[yy][e] + zn[yy][e]);
+          const Wt ce = cur[yy][e];
+          if constexpr (FX) {
+            const i64 Ld = sum - 6 * ce;
+            double o;
+            if (outf) {
+              if (small) o = fx_to(ce * ((i64)1 << k) + fb * Ld, F + k);
+              else o = fx128_to(add128(from_s64_shl(ce, k), mul_s64_u64(Ld, (u64)fw0)), F + k);
+            } else {
+              if (small) o = i64_bits(ce + fx_round_shift(fb * Ld, k));
+              else o = i64_bits(ce + fx128_round_shift(mul_s64_u64(Ld, (u64)fw0), k));
+            }
+            out[e] = in ? o : bnd_out(rcur[yy][e]);
+            const u64 aL = (u64)(Ld ^ (Ld >> 63));
+            rmax = (in && aL > rmax) ? aL : rmax;
+          } else {
+            const T o = ce + r * (sum - T(6) * ce);
+            out[e] = in ? o : rcur[yy][e];
+            T dd = o - ce;
+            dd = dd < T(0) ? -dd : dd;
+            rmax = (in && dd > rmax) ? dd : rmax;
+          }
+        }
+        if (ay[yy]) stv<T, V>(vo + yy * nx, out);
+      }
+      vo += sz;
+      if (!release(j)) {
+        ok = false;
+        break;
+      }
+#pragma unroll
+      for (int yy = 0; yy < 2; ++yy)
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+          zp[yy][e] = cur[yy][e];
+          cur[yy][e] = zn[yy][e];
+          rcur[yy][e] = rzn[yy][e];
+        }
+    }
+  }
+  if (ok && cz1 == nz) {  // boundary plane nz-1 = staged plane L-1, now in rcur
+#pragma unroll
+    for (int yy = 0; yy < 2; ++yy)
+      if (ay[yy]) {
+        T t[V];
+#pragma unroll
+        for (int e = 0; e < V; ++e) t[e] = bnd_out(rcur[yy][e]);
+        stv<T, V>(vo + yy * nx, t);
+      }
+  }
+  if (!ok) {
+    if (rt.status) atomicExch(rt.status, JACC_DEV_TIMEOUT);
+    if (warp0)
+      for (int j = consumed; j < issued; ++j)
+        if (!(stall_cta && j == rt.stall_plane)) mbar_wait(&sm.full[j % G::S], (u32)((j / G::S) & 1), lim);
+  }
+}
+
 // ---------------------------------------------------------------- 27-point box, resident fixed point
 //
 // v 2^F = round(sum_j fw_j class_j 2^-K) from the exact 128-bit sum; the FP64
@@ -1591,17 +1889,34 @@ JD void heat3d_entry(const T* __restrict__ u, T* __restrict__ v, const P& p, con
                      const u64* maxword, int flags) {
   u64 bits = 0;
   if constexpr (sizeof(T) == 8) {
+    // 16-byte columns: the staged kernel (2 rows per thread, so a CTA covers
+    // 2 BY rows; the native fallback then runs two BY-row sub-tiles)
+    constexpr bool STAGED = V == 2;
+    constexpr size_t SM_PLANE = sizeof(Plane<i64, BX, BY, V>);
+    constexpr size_t SM_STAGED = STAGED ? sizeof(Heat3SSmem<double, BX, BY>) : 0;
+    __shared__ __align__(128) unsigned char raw[SM_PLANE > SM_STAGED ? SM_PLANE : SM_STAGED];
     const int F = (maxword && p.fpath != JACC_FP_NONE) ? fx_frac_bits(*maxword) : -1;
-    __shared__ __align__(16) unsigned char raw[sizeof(Plane<i64, BX, BY, V>)];
     if (F >= 0) {
       u64 m = 0;
-      heat3d_fx_body<EDGE, BX, BY, V, ZC>(u, v, p, F, flags, m, *reinterpret_cast<Plane<i64, BX, BY, V>*>(raw));
+      if constexpr (STAGED)
+        heat3s_body<double, BX, BY, ZC, true, EDGE>(u, v, p, rt, F, flags, m,
+                                                    *reinterpret_cast<Heat3SSmem<double, BX, BY>*>(raw));
+      else
+        heat3d_fx_body<EDGE, BX, BY, V, ZC>(u, v, p, F, flags, m, *reinterpret_cast<Plane<i64, BX, BY, V>*>(raw));
       bits = dbits(heat_resid_fixed(p, m, F));
     } else {
       double m = 0.0;
-      heat3d_body<T, BX, BY, V, ZC, JM_NATIVE>(u, v, p, -1, m, *reinterpret_cast<Plane<double, BX, BY, V>*>(raw));
+#pragma unroll 1
+      for (int sub = 0; sub < (STAGED ? 2 : 1); ++sub)
+        heat3d_body<T, BX, BY, V, ZC, JM_NATIVE>(u, v, p, -1, m, *reinterpret_cast<Plane<double, BX, BY, V>*>(raw),
+                                                 STAGED ? 2 : 1, sub);
       bits = dbits(m);
     }
+  } else if constexpr (V == 4) {
+    __shared__ Heat3SSmem<float, BX, BY> sm;
+    float m = 0.0f;
+    heat3s_body<float, BX, BY, ZC, false, false>(u, v, p, rt, -1, 0, m, sm);
+    bits = dbits((double)m);
   } else {
     __shared__ Plane<T, BX, BY, V> sm;
     T m = T(0);

@@ -150,6 +150,43 @@ def test_heat3d_f32(orc, tile):
     g, gr = run(k, u, 4)
     o, orr = orc.heat3d_run(u.astype(np.float64), 0.125, 4)
     assert nerr(g, o) <= TOL32
+    assert np.max(np.abs(gr - orr)) <= TOL32 * np.max(np.abs(o))
+
+
+@pytest.mark.parametrize("dtype", [jacc.F64, jacc.F32])
+@pytest.mark.parametrize("tile", [1, 3, 7, 13, 19, 23])
+@pytest.mark.parametrize("shape", [(3, 3, 4), (4, 17, 8), (33, 5, 12), (18, 9, 264)])
+def test_heat3d_staged_small_and_ragged(orc, dtype, tile, shape):
+    # 16-byte-column tiles stage planes with bulk copies: one-point interiors,
+    # widths below one tile, z chunks holding only a boundary plane
+    nz, ny, nx = shape
+    u = inputs.heat3d_field(nx, ny=ny, nz=nz, seed=7)
+    if dtype == jacc.F32:
+        u = u.astype(np.float32)
+    k = jacc.Kernel(jacc.STENCIL_7PT, dtype, nx, ny, nz, coeffs=(0.125,), tile_id=tile)
+    g, gr = run(k, u, 3)
+    o, orr = orc.heat3d_run(u.astype(np.float64), 0.125, 3)
+    tol = TOL64 if dtype == jacc.F64 else TOL32
+    assert nerr(g, o) <= tol
+    assert np.max(np.abs(gr - orr)) <= tol * np.max(np.abs(o))
+    assert k.status() == 0
+
+
+@pytest.mark.parametrize("dtype", [jacc.F64, jacc.F32])
+def test_heat3d_staged_wait_timeout_is_reported_and_recoverable(orc, dtype):
+    nz, ny, nx = 30, 20, 128
+    u = inputs.heat3d_field(nx, ny=ny, nz=nz, seed=8)
+    if dtype == jacc.F32:
+        u = u.astype(np.float32)
+    k = jacc.Kernel(jacc.STENCIL_7PT, dtype, nx, ny, nz, coeffs=(0.125,), tile_id=3)
+    k.set_wait(timeout_ms=20, stall_plane=2)
+    run(k, u, 3, graph=False)
+    assert k.status() == jacc.ERR_TIMEOUT
+    k.set_wait()
+    g, _ = run(k, u, 3)
+    o, _ = orc.heat3d_run(u.astype(np.float64), 0.125, 3)
+    assert nerr(g, o) <= (TOL64 if dtype == jacc.F64 else TOL32)
+    assert k.status() == 0
 
 
 # ----------------------------------------------------------------------------- 27-point periodic box
