@@ -247,7 +247,7 @@ def run_gpu(args):
     achieved = LUP_PER_SWEEP * BYTES_PER_LUP / (ms_step / SWEEPS * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": args.traffic, "peak_kind": peak_kind,
-            "per_unit": "16 B per interior point per sweep (8 B read + 8 B write), 510^3 points per launch"}
+            "per_unit": f"16 B per interior point per sweep (8 B read + 8 B write), {N - 2}^3 points per launch"}
 
     # End to end through the public API with host buffers: pinned H2D of the
     # input field, the 200-sweep graph, D2H of the result field and residuals.
@@ -261,7 +261,7 @@ def run_gpu(args):
                 "config": {"workload": WORKLOAD, "grid": [N, N, N], "sweeps_per_step": SWEEPS, "r": R,
                            "tile": info["tile_id"], "fixed_point": info["fixed_point"], "jit": info["jit"],
                            "jit_compile_ms": info["compile_ms"], "autotune": tune,
-                           "l2": "inputs larger than L2 (two 1 GiB fields)",
+                           "l2": f"inputs larger than L2 (two {N ** 3 * 8 / 2 ** 20:.0f} MiB fields)",
                            "parallelism": "replicas" if ws > 1 else "single GPU"},
                 "roofline": roof, "e2e": e2e, "gpu_launches": (SWEEPS + 1) * args.steps,
                 "clocks": clk}

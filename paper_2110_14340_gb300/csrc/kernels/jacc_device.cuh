@@ -823,12 +823,23 @@ JD bool mbar_try(u64* bar, u32 parity) {
       : "memory");
   return done != 0;
 }
+// try_wait that may suspend the thread for up to `hint_ns` until the phase
+// completes, so waiting warps take no issue slots.
+JD bool mbar_try_suspend(u64* bar, u32 parity, u32 hint_ns) {
+  u32 done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return done != 0;
+}
 // Waits for the completion of the phase with the given parity; false after
 // limit_ns without it.
 JD bool mbar_wait(u64* bar, u32 parity, i64 limit_ns) {
   if (mbar_try(bar, parity)) return true;
   const u64 t0 = gtimer_ns();
-  while (!mbar_try(bar, parity))
+  while (!mbar_try_suspend(bar, parity, 200000u))
     if ((i64)(gtimer_ns() - t0) > limit_ns) return false;
   return true;
 }
@@ -1459,7 +1470,10 @@ template <class T, int BX, int BY> struct Heat3S {
   static constexpr int W = TW + 2 * V, R = TH + 2;
   static constexpr int STAGE_BYTES = W * R * (int)sizeof(T);
   static constexpr int S0 = 45056 / STAGE_BYTES;
-  static constexpr int S = S0 < 2 ? 2 : (S0 > 4 ? 4 : S0);
+  // stages: 2..6 for FP64 (heavier per-plane work, deeper prefetch pays),
+  // 2..4 for FP32 (measured: more stages cost occupancy)
+  static constexpr int SMAX = sizeof(T) == 8 ? 6 : 4;
+  static constexpr int S = S0 < 2 ? 2 : (S0 > SMAX ? SMAX : S0);
   // A step needs planes z and z+1 staged.  With S >= 3 warp 0 refills the
   // stage released one step earlier (slack for lagging warps); with S = 2 it
   // refills the stage just released, and no plane is prefetched.
@@ -1598,8 +1612,15 @@ JD void heat3s_body(const T* __restrict__ u, T* __restrict__ v, const P& p, cons
 #pragma unroll
     for (int yy = 0; yy < 2; ++yy) lds_vec(&sm.st[j % G::S][2 * ty + 1 + yy][V + V * tx], raw[yy]);
   };
+  // rcur (raw words of plane z) is only needed where a boundary point's output
+  // differs from its working value: the converting (EDGE) fixed-point sweeps
+  constexpr bool RAW = FX && EDGE;
   T rzp[2][V], rcur[2][V], rzn[2][V];
   Wt zp[2][V], cur[2][V];
+  auto as_out = [&](Wt w) -> T {
+    if constexpr (FX) return i64_bits(w);
+    else return w;
+  };
   T* vo = v + y0 * nx + x0;
   const i64 ri = (nx - 2) - x0;  // last interior column relative to x0
   ok = wait_full(0);
@@ -1634,6 +1655,7 @@ JD void heat3s_body(const T* __restrict__ u, T* __restrict__ v, const P& p, cons
   const bool small = p.fpath == JACC_FP_SMALL;
   vo += z0 * sz;
   if (ok) {
+#pragma unroll 3
     for (int j = 1; j <= L - 2; ++j) {
       if (!wait_full(j + 1)) {
         ok = false;
@@ -1690,12 +1712,13 @@ JD void heat3s_body(const T* __restrict__ u, T* __restrict__ v, const P& p, cons
               if (small) o = i64_bits(ce + fx_round_shift(fb * Ld, k));
               else o = i64_bits(ce + fx128_round_shift(mul_s64_u64(Ld, (u64)fw0), k));
             }
-            out[e] = in ? o : bnd_out(rcur[yy][e]);
+            if constexpr (RAW) out[e] = in ? o : bnd_out(rcur[yy][e]);
+            else out[e] = in ? o : as_out(ce);
             const u64 aL = (u64)(Ld ^ (Ld >> 63));
             rmax = (in && aL > rmax) ? aL : rmax;
           } else {
             const T o = ce + r * (sum - T(6) * ce);
-            out[e] = in ? o : rcur[yy][e];
+            out[e] = in ? o : ce;
             T dd = o - ce;
             dd = dd < T(0) ? -dd : dd;
             rmax = (in && dd > rmax) ? dd : rmax;
@@ -1714,17 +1737,17 @@ JD void heat3s_body(const T* __restrict__ u, T* __restrict__ v, const P& p, cons
         for (int e = 0; e < V; ++e) {
           zp[yy][e] = cur[yy][e];
           cur[yy][e] = zn[yy][e];
-          rcur[yy][e] = rzn[yy][e];
+          if constexpr (RAW) rcur[yy][e] = rzn[yy][e];
         }
     }
   }
-  if (ok && cz1 == nz) {  // boundary plane nz-1 = staged plane L-1, now in rcur
+  if (ok && cz1 == nz) {  // boundary plane nz-1 = staged plane L-1 (its working values in cur)
 #pragma unroll
     for (int yy = 0; yy < 2; ++yy)
       if (ay[yy]) {
         T t[V];
 #pragma unroll
-        for (int e = 0; e < V; ++e) t[e] = bnd_out(rcur[yy][e]);
+        for (int e = 0; e < V; ++e) t[e] = RAW ? bnd_out(rcur[yy][e]) : as_out(cur[yy][e]);
         stv<T, V>(vo + yy * nx, t);
       }
   }
