@@ -1536,17 +1536,28 @@ JD void heat3s_body(const T* __restrict__ u, T* __restrict__ v, const P& p, cons
   const i64 x0 = bx0 + (i64)tx * V, y0 = by0 + 2 * ty;
   const bool ax = x0 < nx;
   const bool ay[2] = {ax && y0 < ny, ax && y0 + 1 < ny};
-  const bool yi[2] = {y0 >= 1 && y0 <= ny - 2, y0 + 1 >= 1 && y0 + 1 <= ny - 2};
+  // interior mask of the thread's 2 x V points: bit yy * V + e
+  unsigned inm = 0;
+#pragma unroll
+  for (int yy = 0; yy < 2; ++yy)
+#pragma unroll
+    for (int e = 0; e < V; ++e)
+      if (y0 + yy >= 1 && y0 + yy <= ny - 2 && x0 + e >= 1 && x0 + e <= nx - 2) inm |= 1u << (yy * V + e);
   const i64 cz0 = (i64)blockIdx.z * ZC;
   const i64 cz1 = (cz0 + ZC < nz) ? cz0 + ZC : nz;
   const i64 z0 = cz0 < 1 ? 1 : cz0;
   const i64 z1 = cz1 > nz - 1 ? nz - 1 : cz1;
   const bool inf = FX && EDGE && (flags & JFX_IN_F64);
   const bool outf = FX && EDGE && (flags & JFX_OUT_F64);
-  // raw input word -> working value, and a boundary point's output word
+  // raw input word -> working value, working value -> output word, and a
+  // boundary point's output word from its raw input word
   auto cvt = [&](T raw) -> Wt {
     if constexpr (FX) return inf ? fx_from(raw, F) : bits_i64(raw);
     else return raw;
+  };
+  auto as_out = [&](Wt w) -> T {
+    if constexpr (FX) return i64_bits(w);
+    else return w;
   };
   auto bnd_out = [&](T raw) -> T {
     if constexpr (FX && EDGE) {
@@ -1582,174 +1593,180 @@ JD void heat3s_body(const T* __restrict__ u, T* __restrict__ v, const P& p, cons
     mbar_init_fence();
   }
   __syncthreads();
-  auto request = [&](int j) {
-    if (!(stall_cta && j == rt.stall_plane)) heat3s_issue<T, BX, BY>(sm, j % G::S, u, p, z0 - 1 + j, bx0, by0);
+  auto request = [&](int j, int s) {
+    if (!(stall_cta && j == rt.stall_plane)) heat3s_issue<T, BX, BY>(sm, s, u, p, z0 - 1 + j, bx0, by0);
   };
-  int issued = 0, consumed = 0;
+  int issued = 0, consumed = 0;  // warp 0: planes requested, planes waited for
   if (warp0)
-    for (; issued < G::S && issued < L; ++issued) request(issued);
-  bool ok = true;
-  auto wait_full = [&](int j) -> bool {
-    if (!mbar_wait(&sm.full[j % G::S], (u32)((j / G::S) & 1), lim)) return false;
-    consumed = j + 1;
+    for (; issued < G::S && issued < L; ++issued) request(issued, issued);
+  // ring cursors (stage, phase parity): cn the next plane to wait for, cq the
+  // plane whose stage warp 0 refills next
+  int cn_s = 0, cq_s = 0;
+  u32 cn_ph = 0, cq_ph = 0;
+  auto adv = [&](int& s, u32& ph) {
+    if (++s == G::S) {
+      s = 0;
+      ph ^= 1u;
+    }
+  };
+  auto wait_next = [&]() -> bool {
+    if (!mbar_wait(&sm.full[cn_s], cn_ph, lim)) return false;
+    ++consumed;
     return true;
   };
-  // release plane j (this warp has read it for the last time); warp 0 then
-  // refills the stage of plane j - D once every warp has released it
-  auto release = [&](int j) -> bool {
+  // this warp has read the plane in stage s for the last time (plane j);
+  // warp 0 then refills the stage of plane j - D once every warp released it
+  auto release = [&](int j, int s) -> bool {
     __syncwarp();
-    if ((tid & 31) == 0) mbar_arrive(&sm.empty[j % G::S]);
-    if (warp0 && j >= G::D && issued < L) {
-      const int q = j - G::D;
-      if (!mbar_wait(&sm.empty[q % G::S], (u32)((q / G::S) & 1), lim)) return false;
-      request(issued);
-      ++issued;
+    if ((tid & 31) == 0) mbar_arrive(&sm.empty[s]);
+    if (j >= G::D) {
+      if (warp0 && issued < L) {
+        if (!mbar_wait(&sm.empty[cq_s], cq_ph, lim)) return false;
+        request(issued, cq_s);
+        ++issued;
+      }
+      adv(cq_s, cq_ph);
     }
     return true;
   };
-  // own values of staged plane j (raw words), rows y0, y0+1
-  auto own = [&](int j, T (&raw)[2][V]) {
+  auto own = [&](int s, T (&raw)[2][V]) {
 #pragma unroll
-    for (int yy = 0; yy < 2; ++yy) lds_vec(&sm.st[j % G::S][2 * ty + 1 + yy][V + V * tx], raw[yy]);
+    for (int yy = 0; yy < 2; ++yy) lds_vec(&sm.st[s][2 * ty + 1 + yy][V + V * tx], raw[yy]);
   };
-  // rcur (raw words of plane z) is only needed where a boundary point's output
-  // differs from its working value: the converting (EDGE) fixed-point sweeps
-  constexpr bool RAW = FX && EDGE;
-  T rzp[2][V], rcur[2][V], rzn[2][V];
-  Wt zp[2][V], cur[2][V];
-  auto as_out = [&](Wt w) -> T {
-    if constexpr (FX) return i64_bits(w);
-    else return w;
+  auto store_bnd = [&](T* dst, const T (&raw)[2][V], const Wt (&w)[2][V]) {
+#pragma unroll
+    for (int yy = 0; yy < 2; ++yy)
+      if (ay[yy]) {
+        T t[V];
+#pragma unroll
+        for (int e = 0; e < V; ++e) t[e] = (FX && EDGE) ? bnd_out(raw[yy][e]) : as_out(w[yy][e]);
+        stv<T, V>(dst + yy * nx, t);
+      }
   };
+  constexpr bool RAW = FX && EDGE;  // raw words of plane z kept (converting sweeps only)
+  T rcur[2][V];
+  Wt wa[2][V], wb[2][V], wc[2][V];  // own values of planes z-1, z, z+1 (rotating roles)
   T* vo = v + y0 * nx + x0;
-  const i64 ri = (nx - 2) - x0;  // last interior column relative to x0
-  ok = wait_full(0);
-  if (ok) {
-    own(0, rzp);
-    if (cz0 == 0) {  // boundary plane 0
-#pragma unroll
-      for (int yy = 0; yy < 2; ++yy)
-        if (ay[yy]) {
-          T t[V];
-#pragma unroll
-          for (int e = 0; e < V; ++e) t[e] = bnd_out(rzp[yy][e]);
-          stv<T, V>(vo + yy * nx, t);
-        }
-    }
+  bool ok = wait_next();
+  if (ok) {  // plane z0-1
+    T r0[2][V];
+    own(cn_s, r0);
 #pragma unroll
     for (int yy = 0; yy < 2; ++yy)
 #pragma unroll
-      for (int e = 0; e < V; ++e) zp[yy][e] = cvt(rzp[yy][e]);
-    ok = release(0) && wait_full(1);
+      for (int e = 0; e < V; ++e) wa[yy][e] = cvt(r0[yy][e]);
+    if (cz0 == 0) store_bnd(vo, r0, wa);  // boundary plane 0
+    const int s0 = cn_s;
+    adv(cn_s, cn_ph);
+    ok = release(0, s0) && wait_next();
   }
-  if (ok) {
-    own(1, rcur);
+  int cc_s = cn_s;  // stage of the centre plane z
+  if (ok) {  // plane z0
+    own(cn_s, rcur);
 #pragma unroll
     for (int yy = 0; yy < 2; ++yy)
 #pragma unroll
-      for (int e = 0; e < V; ++e) cur[yy][e] = cvt(rcur[yy][e]);
+      for (int e = 0; e < V; ++e) wb[yy][e] = cvt(rcur[yy][e]);
+    adv(cn_s, cn_ph);
   }
   const T r = (T)p.c0;
   const i64 fb = p.fb, fw0 = p.fw0;
   const int k = p.fk;
   const bool small = p.fpath == JACC_FP_SMALL;
   vo += z0 * sz;
-  if (ok) {
-#pragma unroll 3
-    for (int j = 1; j <= L - 2; ++j) {
-      if (!wait_full(j + 1)) {
-        ok = false;
-        break;
-      }
-      own(j + 1, rzn);
-      const Wt(*pl)[G::W] = reinterpret_cast<const Wt(*)[G::W]>(sm.st[j % G::S]);
-      Wt ym[V], yp[V], xl[2], xr[2];
-      lds_vec(&pl[2 * ty][V + V * tx], ym);
-      lds_vec(&pl[2 * ty + 3][V + V * tx], yp);
+  // one output plane (staged plane j, 1 <= j <= L-2) from the own values of
+  // planes j-1 (zp) and j (cur); fills zn with those of plane j+1
+  auto step = [&](int j, const Wt (&zp)[2][V], const Wt (&cur)[2][V], Wt (&zn)[2][V]) -> bool {
+    if (!wait_next()) return false;
+    T rzn[2][V];
+    own(cn_s, rzn);
+    const Wt(*pl)[G::W] = reinterpret_cast<const Wt(*)[G::W]>(sm.st[cc_s]);
+    Wt ym[V], yp[V], xl[2], xr[2];
+    lds_vec(&pl[2 * ty][V + V * tx], ym);
+    lds_vec(&pl[2 * ty + 3][V + V * tx], yp);
 #pragma unroll
-      for (int yy = 0; yy < 2; ++yy) {
-        xl[yy] = pl[2 * ty + 1 + yy][V + V * tx - 1];
-        xr[yy] = pl[2 * ty + 1 + yy][V + V * tx + V];
-      }
-      if constexpr (FX && EDGE) {
-        if (inf) {
-#pragma unroll
-          for (int e = 0; e < V; ++e) {
-            ym[e] = fx_from(i64_bits(ym[e]), F);
-            yp[e] = fx_from(i64_bits(yp[e]), F);
-          }
-#pragma unroll
-          for (int yy = 0; yy < 2; ++yy) {
-            xl[yy] = fx_from(i64_bits(xl[yy]), F);
-            xr[yy] = fx_from(i64_bits(xr[yy]), F);
-          }
-        }
-      }
-      Wt zn[2][V];
-#pragma unroll
-      for (int yy = 0; yy < 2; ++yy)
-#pragma unroll
-        for (int e = 0; e < V; ++e) zn[yy][e] = cvt(rzn[yy][e]);
-#pragma unroll
-      for (int yy = 0; yy < 2; ++yy) {
-        T out[V];
-#pragma unroll
-        for (int e = 0; e < V; ++e) {
-          const bool in = yi[yy] && (x0 + e >= 1) && (e <= ri);
-          const Wt a = (e == 0) ? xl[yy] : cur[yy][e - 1];
-          const Wt b = (e == V - 1) ? xr[yy] : cur[yy][e + 1];
-          const Wt c = yy == 0 ? ym[e] : cur[0][e];
-          const Wt d = yy == 0 ? cur[1][e] : yp[e];
-          const Wt sum = ((a + b) + (c + d)) + (zp[yy][e] + zn[yy][e]);
-          const Wt ce = cur[yy][e];
-          if constexpr (FX) {
-            const i64 Ld = sum - 6 * ce;
-            double o;
-            if (outf) {
-              if (small) o = fx_to(ce * ((i64)1 << k) + fb * Ld, F + k);
-              else o = fx128_to(add128(from_s64_shl(ce, k), mul_s64_u64(Ld, (u64)fw0)), F + k);
-            } else {
-              if (small) o = i64_bits(ce + fx_round_shift(fb * Ld, k));
-              else o = i64_bits(ce + fx128_round_shift(mul_s64_u64(Ld, (u64)fw0), k));
-            }
-            if constexpr (RAW) out[e] = in ? o : bnd_out(rcur[yy][e]);
-            else out[e] = in ? o : as_out(ce);
-            const u64 aL = (u64)(Ld ^ (Ld >> 63));
-            rmax = (in && aL > rmax) ? aL : rmax;
-          } else {
-            const T o = ce + r * (sum - T(6) * ce);
-            out[e] = in ? o : ce;
-            T dd = o - ce;
-            dd = dd < T(0) ? -dd : dd;
-            rmax = (in && dd > rmax) ? dd : rmax;
-          }
-        }
-        if (ay[yy]) stv<T, V>(vo + yy * nx, out);
-      }
-      vo += sz;
-      if (!release(j)) {
-        ok = false;
-        break;
-      }
-#pragma unroll
-      for (int yy = 0; yy < 2; ++yy)
-#pragma unroll
-        for (int e = 0; e < V; ++e) {
-          zp[yy][e] = cur[yy][e];
-          cur[yy][e] = zn[yy][e];
-          if constexpr (RAW) rcur[yy][e] = rzn[yy][e];
-        }
+    for (int yy = 0; yy < 2; ++yy) {
+      xl[yy] = pl[2 * ty + 1 + yy][V + V * tx - 1];
+      xr[yy] = pl[2 * ty + 1 + yy][V + V * tx + V];
     }
-  }
-  if (ok && cz1 == nz) {  // boundary plane nz-1 = staged plane L-1 (its working values in cur)
+    if constexpr (FX && EDGE) {
+      if (inf) {
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+          ym[e] = fx_from(i64_bits(ym[e]), F);
+          yp[e] = fx_from(i64_bits(yp[e]), F);
+        }
+#pragma unroll
+        for (int yy = 0; yy < 2; ++yy) {
+          xl[yy] = fx_from(i64_bits(xl[yy]), F);
+          xr[yy] = fx_from(i64_bits(xr[yy]), F);
+        }
+      }
+    }
 #pragma unroll
     for (int yy = 0; yy < 2; ++yy)
-      if (ay[yy]) {
-        T t[V];
 #pragma unroll
-        for (int e = 0; e < V; ++e) t[e] = RAW ? bnd_out(rcur[yy][e]) : as_out(cur[yy][e]);
-        stv<T, V>(vo + yy * nx, t);
+      for (int e = 0; e < V; ++e) zn[yy][e] = cvt(rzn[yy][e]);
+#pragma unroll
+    for (int yy = 0; yy < 2; ++yy) {
+      T out[V];
+#pragma unroll
+      for (int e = 0; e < V; ++e) {
+        const bool in = (inm >> (yy * V + e)) & 1u;
+        const Wt a = (e == 0) ? xl[yy] : cur[yy][e - 1];
+        const Wt b = (e == V - 1) ? xr[yy] : cur[yy][e + 1];
+        const Wt c = yy == 0 ? ym[e] : cur[0][e];
+        const Wt d = yy == 0 ? cur[1][e] : yp[e];
+        const Wt sum = ((a + b) + (c + d)) + (zp[yy][e] + zn[yy][e]);
+        const Wt ce = cur[yy][e];
+        if constexpr (FX) {
+          const i64 Ld = sum - 6 * ce;
+          double o;
+          if (outf) {
+            if (small) o = fx_to(ce * ((i64)1 << k) + fb * Ld, F + k);
+            else o = fx128_to(add128(from_s64_shl(ce, k), mul_s64_u64(Ld, (u64)fw0)), F + k);
+          } else {
+            if (small) o = i64_bits(ce + fx_round_shift(fb * Ld, k));
+            else o = i64_bits(ce + fx128_round_shift(mul_s64_u64(Ld, (u64)fw0), k));
+          }
+          if constexpr (RAW) out[e] = in ? o : bnd_out(rcur[yy][e]);
+          else out[e] = in ? o : as_out(ce);
+          const u64 aL = (u64)(Ld ^ (Ld >> 63));
+          rmax = (in && aL > rmax) ? aL : rmax;
+        } else {
+          const T o = ce + r * (sum - T(6) * ce);
+          out[e] = in ? o : ce;
+          T dd = o - ce;
+          dd = dd < T(0) ? -dd : dd;
+          rmax = (in && dd > rmax) ? dd : rmax;
+        }
       }
+      if (ay[yy]) stv<T, V>(vo + yy * nx, out);
+    }
+    vo += sz;
+    if (j == L - 2 && cz1 == nz) store_bnd(vo, rzn, zn);  // boundary plane nz-1 = staged plane L-1
+    if (!release(j, cc_s)) return false;
+    cc_s = cn_s;
+    adv(cn_s, cn_ph);
+    if constexpr (RAW) {
+#pragma unroll
+      for (int yy = 0; yy < 2; ++yy)
+#pragma unroll
+        for (int e = 0; e < V; ++e) rcur[yy][e] = rzn[yy][e];
+    }
+    return true;
+  };
+  if (ok) {
+    // three steps per iteration: the buffers' roles rotate without copies
+    int j = 1;
+    for (; j + 2 <= L - 2; j += 3) {
+      if (!step(j, wa, wb, wc) || !step(j + 1, wb, wc, wa) || !step(j + 2, wc, wa, wb)) {
+        ok = false;
+        break;
+      }
+    }
+    if (ok && j <= L - 2) ok = step(j, wa, wb, wc);
+    if (ok && j + 1 <= L - 2) ok = step(j + 1, wb, wc, wa);
   }
   if (!ok) {
     if (rt.status) atomicExch(rt.status, JACC_DEV_TIMEOUT);
