@@ -967,83 +967,93 @@ JD double box27s_body(const float* __restrict__ u, float* __restrict__ v, const 
     i64 z = (z0 - 1 + j) % nz;
     return z < 0 ? z + nz : z;
   };
-  auto request = [&](int j) {
-    if (!(stall_cta && j == rt.stall_plane)) box27s_issue<BX, BY>(sm, j % G::S, u, p, plane_z(j), bx0, by0, weff);
+  auto request = [&](int j, int s) {
+    if (!(stall_cta && j == rt.stall_plane)) box27s_issue<BX, BY>(sm, s, u, p, plane_z(j), bx0, by0, weff);
   };
-  int issued = 0, consumed = 0;  // warp 0's counts of requested and waited planes
+  int issued = 0, consumed = 0;  // warp 0: planes requested, planes waited for
   if (warp0)
-    for (; issued < G::S && issued < L; ++issued) request(issued);
+    for (; issued < G::S && issued < L; ++issued) request(issued, issued);
 
   const float w0 = (float)p.c0, wf = (float)p.c1, we = (float)p.c2, wc = (float)p.c3;
   const i64 x0 = bx0 + 4 * tx, y0 = by0 + 2 * ty;
   const bool ax = x0 < nx, ay0 = ax && y0 < ny, ay1 = ax && y0 + 1 < ny;
   float* vo = v + y0 * nx + x0 + z0 * sz;
-  float Ac[2][4], Pz[2][4];
   float hi = 0.0f, lo = 0.0f;
-  bool ok = true;
+  // ring cursors (stage, phase parity): cn the next plane to wait for, cq
+  // the plane whose stage warp 0 refills next (one step behind)
+  int cn_s = 0, cq_s = 0;
+  u32 cn_ph = 0, cq_ph = 0;
+  auto adv = [&](int& s, u32& ph) {
+    if (++s == G::S) {
+      s = 0;
+      ph ^= 1u;
+    }
+  };
   // consume plane j: wait for it, form its terms, release its stage, and let
   // warp 0 refill the stage of plane j - 1
   auto consume = [&](int j, float (&A)[2][4], float (&B)[2][4]) -> bool {
-    const int s = j % G::S;
-    if (!mbar_wait(&sm.full[s], (u32)((j / G::S) & 1), lim)) return false;
-    consumed = j + 1;
-    box27s_terms<BX, BY>(sm.st[s], w0, wf, we, wc, A, B);
+    if (!mbar_wait(&sm.full[cn_s], cn_ph, lim)) return false;
+    ++consumed;
+    box27s_terms<BX, BY>(sm.st[cn_s], w0, wf, we, wc, A, B);
     __syncwarp();
-    if ((tid & 31) == 0) mbar_arrive(&sm.empty[s]);
-    if (warp0 && j >= 1 && issued < L) {
-      const int q = j - 1;
-      if (!mbar_wait(&sm.empty[q % G::S], (u32)((q / G::S) & 1), lim)) return false;
-      request(issued);
-      ++issued;
+    if ((tid & 31) == 0) mbar_arrive(&sm.empty[cn_s]);
+    adv(cn_s, cn_ph);
+    if (j >= 1) {
+      if (warp0 && issued < L) {
+        if (!mbar_wait(&sm.empty[cq_s], cq_ph, lim)) return false;
+        request(issued, cq_s);
+        ++issued;
+      }
+      adv(cq_s, cq_ph);
     }
     return true;
   };
-  {
-    float A[2][4], B[2][4];
-    ok = consume(0, A, B);
-    if (ok) {
+  // output plane of staged plane j - 1 from P = A(j-2) + B(j-1) and the
+  // terms of plane j; Anew receives A(j), Aold holds A(j-1)
+  float Pz[2][4];
+  auto step = [&](int j, float (&Anew)[2][4], const float (&Aold)[2][4]) -> bool {
+    float B[2][4];
+    if (!consume(j, Anew, B)) return false;
+    float o[2][4];
 #pragma unroll
-      for (int yy = 0; yy < 2; ++yy)
+    for (int yy = 0; yy < 2; ++yy)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) Ac[yy][e] = A[yy][e];
-      ok = consume(1, A, B);
+      for (int e = 0; e < 4; ++e) {
+        o[yy][e] = Pz[yy][e] + Anew[yy][e];
+        Pz[yy][e] = Aold[yy][e] + B[yy][e];
+      }
+    if (ay0) stv<float, 4>(vo, o[0]);
+    if (ay1) stv<float, 4>(vo + nx, o[1]);
+    vo += sz;
+    if (want_sum) {
+      const float t0 = ay0 ? (o[0][0] + o[0][1]) + (o[0][2] + o[0][3]) : 0.0f;
+      const float t1 = ay1 ? (o[1][0] + o[1][1]) + (o[1][2] + o[1][3]) : 0.0f;
+      two_sum_acc(hi, lo, t0 + t1);
     }
+    return true;
+  };
+  float Aa[2][4], Ab[2][4];
+  bool ok;
+  {
+    float B[2][4];
+    ok = consume(0, Aa, B) && consume(1, Ab, B);  // A of planes 0 and 1; B of plane 1
     if (ok) {
 #pragma unroll
       for (int yy = 0; yy < 2; ++yy)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          Pz[yy][e] = Ac[yy][e] + B[yy][e];
-          Ac[yy][e] = A[yy][e];
-        }
+        for (int e = 0; e < 4; ++e) Pz[yy][e] = Aa[yy][e] + B[yy][e];
     }
   }
   if (ok) {
-#pragma unroll 2
-    for (int j = 2; j < L; ++j) {
-      float A[2][4], B[2][4];
-      if (!consume(j, A, B)) {
+    // two steps per iteration: the A buffers swap roles without copies
+    int j = 2;
+    for (; j + 1 < L; j += 2) {
+      if (!step(j, Aa, Ab) || !step(j + 1, Ab, Aa)) {
         ok = false;
         break;
       }
-      float o[2][4];
-#pragma unroll
-      for (int yy = 0; yy < 2; ++yy)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          o[yy][e] = Pz[yy][e] + A[yy][e];
-          Pz[yy][e] = Ac[yy][e] + B[yy][e];
-          Ac[yy][e] = A[yy][e];
-        }
-      if (ay0) stv<float, 4>(vo, o[0]);
-      if (ay1) stv<float, 4>(vo + nx, o[1]);
-      vo += sz;
-      if (want_sum) {
-        const float t0 = ay0 ? (o[0][0] + o[0][1]) + (o[0][2] + o[0][3]) : 0.0f;
-        const float t1 = ay1 ? (o[1][0] + o[1][1]) + (o[1][2] + o[1][3]) : 0.0f;
-        two_sum_acc(hi, lo, t0 + t1);
-      }
     }
+    if (ok && j < L) ok = step(j, Aa, Ab);
   }
   if (!ok) {
     if (rt.status) atomicExch(rt.status, JACC_DEV_TIMEOUT);
