@@ -33,6 +33,10 @@ def set_size(n, sweeps):
     N, SWEEPS, LUP_PER_SWEEP = n, sweeps, (n - 2) ** 3
     WORKLOAD = f"heat3d 7-point FP64 {n}^3, r=0.125, zero Dirichlet, {sweeps} sweeps per CUDA graph"
 BYTES_PER_LUP = 16  # one FP64 read + one FP64 write per interior point
+# DRAM bytes (read + write) per update of the intermediate-sweep kernel, from
+# an ncu capture of the same kernel on a 384^3 grid (875.4 MB for 382^3
+# updates); scaled to a launch by its updates.
+DRAM_BYTES_PER_LUP = 15.71
 METRIC = "stencil GLUP/s"
 WORKLOAD = "heat3d 7-point FP64 512^3, r=0.125, zero Dirichlet, 200 sweeps per CUDA graph"
 
@@ -246,7 +250,10 @@ def run_gpu(args):
     peak, peak_kind = peaks()
     achieved = LUP_PER_SWEEP * BYTES_PER_LUP / (ms_step / SWEEPS * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": args.traffic, "peak_kind": peak_kind,
+            "traffic": args.traffic if args.traffic is not None else DRAM_BYTES_PER_LUP * LUP_PER_SWEEP,
+            "traffic_source": "command line" if args.traffic is not None else
+            "ncu dram read+write bytes of a 382^3 launch of the same kernel, 15.71 B per update, x updates per launch",
+            "peak_kind": peak_kind,
             "per_unit": f"16 B per interior point per sweep (8 B read + 8 B write), {N - 2}^3 points per launch"}
 
     # End to end through the public API with host buffers: pinned H2D of the
