@@ -349,9 +349,17 @@ def secondary(dev):
     for _ in range(1000):
         jacc.region_analyze([(1, 254, 1), (1, 254, 1)], refs, [[256, 256], [256, 256]])
     ra_us = (time.perf_counter() - t0) * 1e3
+    # the same sequence in one cluster-resident launch (fields in distributed shared memory)
+    kc = jacc.Kernel(5, 64, 256, 256, 1, cluster=True)
+    a.copy_(torch.from_numpy(u))
+    msc = _time_ms(lambda: jacc.sweep(kc, a, b, 100, res), reps=10)
     out["jacobi2d_256_x100"] = {"ms": ms, "us_per_sweep": 1e3 * ms / 100, "GLUP/s": 254 * 254 * 100 / ms / 1e6,
-                                "tile": k.info()["tile_id"], "region_analysis_us_via_python": ra_us}
+                                "tile": k.info()["tile_id"], "cluster_ms": msc,
+                                "cluster_us_per_sweep": 1e3 * msc / 100,
+                                "cluster_GLUP/s": 254 * 254 * 100 / msc / 1e6,
+                                "region_analysis_us_via_python": ra_us}
     k.release()
+    kc.release()
     # 64 batched grids x 500 sweeps: one persistent launch vs 64 plain graph launches
     shapes = inputs.batched_shapes(64, seed=3)
     hosts = inputs.batched_fields(shapes, seed=4)

@@ -140,6 +140,13 @@ jacc_status jacc_region_analyze(int32_t nloops, const jacc_loop* loops, int32_t 
  * folded in as constants (NVRTC, sm_103a; cached in memory and, if the
  * environment variable JACC_CACHE_DIR names a directory, on disk).  Without
  * it the handle uses a precompiled kernel that takes them as arguments.
+ * JACC_SPEC_CLUSTER (5PT FP64 only; no counterpart in the paper): jacc_sweep
+ * runs the whole sequence in one launch of one thread-block cluster (16 or 8
+ * CTAs) that keeps both fields in its distributed shared memory; it suits
+ * grids of up to about 10^5 points, whose sweeps are otherwise bound by
+ * launch latency.  Fields, residuals and the other buffer are bit-identical
+ * to the launch-per-sweep sequence; jacc_launch still runs the tile kernel.
+ * JACC_ERR_UNSUPPORTED if the grid does not fit a cluster the device can run.
  *
  * tblock (27PT only): temporal-blocking depth T >= 1.  Each launch then
  * performs T sweeps; jacc_sweep accounts for this.
@@ -156,6 +163,7 @@ jacc_status jacc_region_analyze(int32_t nloops, const jacc_loop* loops, int32_t 
 #define JACC_ARITH_AUTO 0
 #define JACC_ARITH_NATIVE 1
 #define JACC_SPEC_JIT 1u
+#define JACC_SPEC_CLUSTER 2u
 #define JACC_NUM_TILES 24
 
 typedef struct {
@@ -237,6 +245,27 @@ jacc_status jacc_launch(jacc_kernel k, const void* u_in, void* u_out, double* re
 #define JACC_SWEEP_GRAPH 1u
 jacc_status jacc_sweep(jacc_kernel k, void* u0, void* u1, int32_t nsweeps, double* resid_dev, uint32_t flags,
                        uintptr_t stream, int32_t* final_buf);
+
+/* jacc_sweep_until (no counterpart in the paper, which runs a fixed iteration
+ * count; §5.2 notes that Himeno reduces its error each iteration): sweeps
+ * u0 -> u1 -> u0 ... until a sweep's residual is <= tol or max_sweeps sweeps
+ * ran, with the loop and its exit test on the device: one CUDA graph (cached
+ * per kernel, fields, max_sweeps, tol and output arrays, dropped by
+ * jacc_release) whose WHILE conditional node runs the sweeps, each followed by
+ * a one-thread kernel that stores the residual and sets the loop condition;
+ * the host never waits.  5PT and 7PT only (their residual is max |v - u|);
+ * 27PT is JACC_ERR_UNSUPPORTED.  tol finite and >= 0, max_sweeps >= 1.
+ *   resid_dev  (device, max_sweeps doubles, required): resid_dev[i] for each
+ *              sweep i that ran; later slots are untouched.
+ *   status_dev (device, 2 int32, required): [0] sweeps run n, [1] the buffer
+ *              holding the result (0: u0, 1: u1), written when the loop ends.
+ * Fields, residuals and the other buffer are bit-identical to
+ * jacc_sweep(k, u0, u1, n, ...): for FP64 fixed-point kernels the loop keeps
+ * the resident form and the last sweep is run once more from the state before
+ * it with FP64 output (so the result is the exact stencil value rounded once).
+ * Asynchronous on `stream`. */
+jacc_status jacc_sweep_until(jacc_kernel k, void* u0, void* u1, int32_t max_sweeps, double tol, double* resid_dev,
+                             int32_t* status_dev, uintptr_t stream);
 
 /* ---------------------------------------------------------- autotuner
  * Exhaustive search over the JACC_NUM_TILES tile configurations for one

@@ -36,6 +36,14 @@ struct SweepGraph {
 
 using GraphKey = std::tuple<const void*, const void*, int32_t, const double*>;
 
+// One cached jacc_sweep_until graph (device-side loop with conditional nodes).
+struct UntilGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  u64* scratch = nullptr;  // [0] max-abs word, [1] residual slot, [2] sweep counter, [3] spare residual slot
+};
+using UntilKey = std::tuple<const void*, const void*, int32_t, double, const double*, const int32_t*>;
+
 // A specialised kernel (the object behind a jacc_kernel handle).
 struct Kernel {
   jacc_kernel_desc desc{};
@@ -51,10 +59,22 @@ struct Kernel {
   cudaLibrary_t lib = nullptr;  // NVRTC module, if jit
   dim3 grid, block;
   int tblock = 1;
+  int cluster_nc = 0;           // JACC_SPEC_CLUSTER: CTAs of the cluster-resident sweep launch
   int refcount = 0;
   u64* scratch = nullptr;       // max-abs word for direct launches (device)
   std::map<GraphKey, SweepGraph> graphs;
+  std::map<UntilKey, UntilGraph> until_graphs;
 };
+
+// Validates a pair of field pointers for kernel k (non-null, 16-byte aligned,
+// not overlapping).
+jacc_status check_buffers(const Kernel& k, const void* a, const void* b);
+// Destroys k's cached jacc_sweep_until graphs.
+void free_until_graphs(Kernel& k);
+cudaError_t launch_until_check(double* slot, int* counter, double* resid, double tol, int max_sweeps,
+                               cudaGraphConditionalHandle h_loop, cudaGraphConditionalHandle h_odd, cudaStream_t s);
+cudaError_t launch_until_final(const int* counter, int* status, int recompute, cudaGraphConditionalHandle h_final,
+                               cudaStream_t s);
 
 // Launch one sweep of `k` (no validation).  maxword may be null.  flags:
 // JFX_* bits (first sweep of a sequence reads FP64, last writes FP64).

@@ -16,6 +16,7 @@
 
 #include "../kernels/tiles.h"
 #include "jacc_internal.h"
+#include "../kernels/jacobi_cluster.h"
 
 extern "C" const void* const jacc_tab_5_64[JACC_NTILES];
 extern "C" const void* const jacc_tab_5_32[JACC_NTILES];
@@ -143,7 +144,9 @@ static jacc_status validate(const jacc_kernel_desc& d) {
   if (d.dtype != JACC_F32 && d.dtype != JACC_F64) return fail(JACC_ERR_INVALID_ARG, "dtype must be 32 or 64");
   if (d.tile_id < -1 || d.tile_id >= JACC_NTILES) return fail(JACC_ERR_INVALID_ARG, "tile_id out of range");
   if (d.arith != JACC_ARITH_AUTO && d.arith != JACC_ARITH_NATIVE) return fail(JACC_ERR_INVALID_ARG, "bad arith");
-  if (d.flags & ~JACC_SPEC_JIT) return fail(JACC_ERR_INVALID_ARG, "unknown specialisation flags");
+  if (d.flags & ~(JACC_SPEC_JIT | JACC_SPEC_CLUSTER)) return fail(JACC_ERR_INVALID_ARG, "unknown specialisation flags");
+  if ((d.flags & JACC_SPEC_CLUSTER) && (d.stencil != 5 || d.dtype != JACC_F64))
+    return fail(JACC_ERR_UNSUPPORTED, "JACC_SPEC_CLUSTER: 5-point FP64 only");
   if (d.nx < 3 || d.ny < 3 || d.nz < 1) return fail(JACC_ERR_INVALID_ARG, "extents must be >= 3");
   if (d.stencil == 5) {
     if (d.nz != 1) return fail(JACC_ERR_INVALID_ARG, "5-point stencil is 2D: nz must be 1");
@@ -167,11 +170,25 @@ static jacc_status validate(const jacc_kernel_desc& d) {
   return ok();
 }
 
+// The default tile, from the autotuner's timing tables on GB300 (5/7/27-point,
+// FP32 and FP64, sides 256-1024), by size class.  3D: 32 x 4 threads with
+// 16-byte columns; a 64-plane march (tile 3) when it still yields at least
+// 1024 CTAs, else a 16-plane march (tile 1) for more CTAs on small grids.
+// 2D: 128 x 2 threads, 16-byte columns, 16-row march (tile 17) from 2^19
+// points; 64 x 4 threads, scalar columns, 4-row march (tile 8) below, where
+// the grid lives in L2 and more, shorter CTAs hide latency better.  Scalar
+// 3D variants (2, 0) when nx is not a multiple of the vector width.
 int default_tile(const jacc_kernel_desc& d) {
   const int V = d.dtype == 64 ? 2 : 4;
   const bool vec_ok = (d.nx % V) == 0;
-  if (d.stencil == 5) return vec_ok ? 5 : 4;
-  return vec_ok ? 15 : 14;
+  if (d.stencil == 5) {
+    if (d.nx * d.ny < (int64_t(1) << 19)) return 8;
+    return vec_ok ? 17 : 16;
+  }
+  const int64_t w = 32 * (vec_ok ? V : 1);  // columns of a 32 x 4 tile
+  const int64_t ctas_long = ((d.nx + w - 1) / w) * ((d.ny + 7) / 8) * ((d.nz + 63) / 64);
+  if (ctas_long >= 1024) return vec_ok ? 3 : 2;
+  return vec_ok ? 1 : 0;
 }
 
 bool staged_tile(const jacc_kernel_desc& d, int t) {
@@ -238,6 +255,7 @@ static void free_kernel(Kernel* k) {
     if (g.second.scratch) cudaFree(g.second.scratch);
   }
   k->graphs.clear();
+  free_until_graphs(*k);
   if (k->scratch) cudaFree(k->scratch);
   if (k->lib) cudaLibraryUnload(k->lib);
   delete k;
@@ -328,6 +346,14 @@ extern "C" jacc_status jacc_specialize(const jacc_kernel_desc* desc, jacc_kernel
     k->func_out = table_entry(desc->stencil, desc->dtype, tile, true);
     if (!k->func || !k->func_out) return fail(JACC_ERR_UNSUPPORTED, "no precompiled kernel for this descriptor");
   }
+  if (desc->flags & JACC_SPEC_CLUSTER) {
+    int nc = 0;
+    if (!jacobi_cluster_plan(desc->nx, desc->ny, &nc)) {
+      if (k->lib) cudaLibraryUnload(k->lib);
+      return fail(JACC_ERR_UNSUPPORTED, "JACC_SPEC_CLUSTER: the grid does not fit one cluster's shared memory");
+    }
+    k->cluster_nc = nc;
+  }
   // scratch words: [0] max|u| bits of direct FP64 fixed-point launches, [1] the
   // device status word of bounded waits (JACC_DEV_TIMEOUT)
   st = cuda_check(cudaMalloc(reinterpret_cast<void**>(&k->scratch), 256), "cudaMalloc(scratch)");
@@ -374,6 +400,7 @@ extern "C" jacc_status jacc_kernel_set_wait(jacc_kernel h, int32_t timeout_ms, i
     if (g.second.scratch) cudaFree(g.second.scratch);
   }
   k.graphs.clear();
+  free_until_graphs(k);
   return ok();
 }
 
@@ -424,9 +451,7 @@ cudaError_t launch_sweep_kernel(const Kernel& k, const void* u, void* v, double*
   return cudaLaunchKernel((flags & (kFxIn | kFxOut)) ? k.func_out : k.func, k.grid, k.block, const_cast<void**>(args), 0, s);
 }
 
-}  // namespace jacc
-
-static jacc_status check_buffers(const Kernel& k, const void* a, const void* b) {
+jacc_status check_buffers(const Kernel& k, const void* a, const void* b) {
   if (!a || !b) return fail(JACC_ERR_INVALID_ARG, "NULL field pointer");
   if ((reinterpret_cast<uintptr_t>(a) % 16) || (reinterpret_cast<uintptr_t>(b) % 16))
     return fail(JACC_ERR_INVALID_ARG, "field pointers must be 16-byte aligned");
@@ -435,6 +460,8 @@ static jacc_status check_buffers(const Kernel& k, const void* a, const void* b) 
   if (pa < pb + bytes && pb < pa + bytes) return fail(JACC_ERR_INVALID_ARG, "input and output fields overlap");
   return ok();
 }
+
+}  // namespace jacc
 
 // Enqueue one sweep with its pre-pass (fixed point) and residual zeroing.
 static jacc_status enqueue_one(const Kernel& k, const void* u, void* v, double* resid, u64* scratch, cudaStream_t s) {
@@ -509,6 +536,21 @@ extern "C" jacc_status jacc_sweep(jacc_kernel h, void* u0, void* u1, int32_t nsw
   }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (final_buf) *final_buf = (nsweeps / (k.tblock > 1 ? k.tblock : 1)) % 2;
+  if (k.cluster_nc > 0) {  // the whole sequence in one cluster launch (it writes every residual slot)
+    JClusterArgs a = {};
+    a.u = static_cast<const double*>(u0);
+    a.res = static_cast<double*>((nsweeps & 1) ? u1 : u0);
+    a.oth = static_cast<double*>((nsweeps & 1) ? u0 : u1);
+    a.resid = resid_dev;
+    a.nx = k.desc.nx;
+    a.ny = k.desc.ny;
+    a.nsweeps = nsweeps;
+    a.native = k.params.fpath == JACC_FP_NONE ? 1 : 0;
+    st = cuda_check(launch_jacobi_cluster(a, k.cluster_nc, s), "cluster sweep launch");
+    if (st) return st;
+    if (final_buf) *final_buf = (nsweeps & 1) ? 1 : 0;
+    return ok();
+  }
   if (!(flags & JACC_SWEEP_GRAPH)) return enqueue_sweeps(k, u0, u1, nsweeps, resid_dev, k.scratch, s);
 
   std::lock_guard<std::mutex> lock(global_mutex());

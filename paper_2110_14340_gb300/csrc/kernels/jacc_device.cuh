@@ -1304,6 +1304,134 @@ JD void jacobi_fx_march(const double* __restrict__ u, double* __restrict__ v, i6
   }
 }
 
+// ---------------------------------------------------------------- 5-point Jacobi, prefetching march
+//
+// The march of jacobi_march / jacobi_fx_march with loads issued PD rows
+// ahead: a register ring holds the raw rows y+2 .. y+PD+1 in flight, and the
+// x-edge values of lanes 0 and 31 (one column left of the warp's chunk for
+// lane 0, one right for lane 31) for rows y+1 .. y+PD-1, so no load is
+// consumed in the iteration that issues it.  The ring is indexed with
+// compile-time slots (the row loop is unrolled by PD).  Rows past ye (the
+// march end) are not prefetched beyond the one halo row the last step needs.
+// FX: resident 64-bit fixed point (EDGE as for jacobi_fx_march); otherwise
+// native arithmetic on T.
+template <class T, int V, bool CG, bool FX, bool EDGE, int PD>
+JD void jacobi_march_pf(const T* __restrict__ u, T* __restrict__ v, i64 nx, i64 ny, i64 x0, i64 ys, i64 ye, int F,
+                        int flags, typename RT<T, FX ? JM_FIXED : JM_NATIVE>::type& rmax) {
+  typedef typename WT<T, FX ? JM_FIXED : JM_NATIVE>::type W;
+  const int lane = threadIdx.x & 31;
+  const bool xin = x0 < nx;
+  const bool inf = FX && EDGE && (flags & JFX_IN_F64);
+  const bool outf = FX && EDGE && (flags & JFX_OUT_F64);
+  // this lane's x-edge column (lane 0: x0 - 1, lane 31: x0 + V), if any
+  const bool has_edge = xin && ((lane == 0 && x0 >= 1) || (lane == 31 && x0 + V < nx));
+  const T* ecol = u + (lane == 0 ? x0 - 1 : x0 + V);
+  const T* col = u + x0;
+  auto cvt = [&](T raw) -> W {
+    if constexpr (FX) return inf ? fx_from(raw, F) : bits_i64(raw);
+    else return raw;
+  };
+  auto bnd_out = [&](T raw, W w) -> T {
+    if constexpr (FX) {
+      if constexpr (!EDGE) return i64_bits(w);
+      if (inf && outf) return raw;
+      if (outf) return fx_to(w, F);
+      return i64_bits(w);
+    } else {
+      return raw;
+    }
+  };
+  unsigned intm, bndm;
+  col_masks<V>(x0, nx, intm, bndm);
+  T ring[PD][V];  // slot j % PD: raw row ys + 1 + j (the "down" row of step j)
+  T eg[PD];       // slot j % PD: this lane's x-edge value of row ys + j
+  T rcur[V];
+  W up[V], cur[V];
+  {
+    T t[V];
+#pragma unroll
+    for (int e = 0; e < V; ++e) t[e] = rcur[e] = T(0);
+    if (xin) {
+      if (ys >= 1) ldv<T, V, CG>(col + (ys - 1) * nx, t);
+      ldv<T, V, CG>(col + ys * nx, rcur);
+    }
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      up[e] = cvt(t[e]);
+      cur[e] = cvt(rcur[e]);
+    }
+#pragma unroll
+    for (int k = 0; k < PD; ++k) {
+      const i64 r = ys + 1 + k;
+#pragma unroll
+      for (int e = 0; e < V; ++e) ring[k][e] = T(0);
+      if (xin && r <= ye && r < ny) ldv<T, V, CG>(col + r * nx, ring[k]);
+      eg[k] = T(0);
+      if (has_edge && ys + k < ye) eg[k] = ld1<CG>(ecol + (ys + k) * nx);
+    }
+  }
+  const i64 n = ye - ys;
+  for (i64 j0 = 0; j0 < n; j0 += PD) {
+#pragma unroll
+    for (int i = 0; i < PD; ++i) {
+      const i64 j = j0 + i;
+      if (j >= n) break;
+      const i64 y = ys + j;
+      // consume slot i: the down row and this lane's edge of row y; refill it
+      T rdn[V];
+#pragma unroll
+      for (int e = 0; e < V; ++e) rdn[e] = ring[i][e];
+      const T edge = eg[i];
+      {
+        const i64 r = y + 1 + PD;
+#pragma unroll
+        for (int e = 0; e < V; ++e) ring[i][e] = T(0);
+        if (xin && r <= ye && r < ny) ldv<T, V, CG>(col + r * nx, ring[i]);
+        if (has_edge && y + PD < ye) eg[i] = ld1<CG>(ecol + (y + PD) * nx);
+      }
+      W dn[V];
+#pragma unroll
+      for (int e = 0; e < V; ++e) dn[e] = cvt(rdn[e]);
+      W left = __shfl_up_sync(0xffffffffu, cur[V - 1], 1);
+      W right = __shfl_down_sync(0xffffffffu, cur[0], 1);
+      if (has_edge) {
+        if (lane == 0) left = cvt(edge);
+        else right = cvt(edge);
+      }
+      const bool yint = (y >= 1) && (y <= ny - 2);
+      T out[V];
+#pragma unroll
+      for (int e = 0; e < V; ++e) {
+        const W xl = (e == 0) ? left : cur[e - 1];
+        const W xr = (e == V - 1) ? right : cur[e + 1];
+        const bool in = yint && ((intm >> e) & 1u);
+        if constexpr (FX) {
+          const i64 s = (up[e] + dn[e]) + (xl + xr);
+          const T o = outf ? fx_to(s, F + 2) : i64_bits((s + 2) >> 2);
+          out[e] = in ? o : bnd_out(rcur[e], cur[e]);
+          const i64 d = s - cur[e] * 4;
+          const u64 ad = (u64)(d ^ (d >> 63));  // |d| (one less for negative d: below the tolerance by 2^-F)
+          rmax = (in && ad > rmax) ? ad : rmax;
+        } else {
+          const T s = (up[e] + dn[e]) + (xl + xr);
+          const T r = T(0.25) * s;
+          out[e] = in ? r : rcur[e];
+          T d = r - rcur[e];
+          d = d < T(0) ? -d : d;
+          rmax = (in && d > rmax) ? d : rmax;
+        }
+      }
+      if (xin) stv<T, V>(v + y * nx + x0, out);
+#pragma unroll
+      for (int e = 0; e < V; ++e) {
+        up[e] = cur[e];
+        cur[e] = dn[e];
+        rcur[e] = rdn[e];
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------- 7-point heat, resident fixed point
 //
 // S = the six faces, L = S - 6u (exact, scale F):
@@ -1919,16 +2047,16 @@ JD void jacobi2d_entry(const T* __restrict__ u, T* __restrict__ v, const P& p, c
     const int F = (maxword && p.fpath != JACC_FP_NONE) ? fx_frac_bits(*maxword) : -1;
     if (F >= 0) {
       u64 m = 0;
-      if (ys < p.ny) jacobi_fx_march<V, false, EDGE>(u, v, p.nx, p.ny, x0, ys, ye, F, flags, m);
+      if (ys < p.ny) jacobi_march_pf<double, V, false, true, EDGE, 4>(u, v, p.nx, p.ny, x0, ys, ye, F, flags, m);
       bits = dbits(fx_to_u(m, F + 2));
     } else {
       double m = 0.0;
-      if (ys < p.ny) jacobi_march<T, V, JM_NATIVE, false>(u, v, p.nx, p.ny, x0, ys, ye, -1, m);
+      if (ys < p.ny) jacobi_march_pf<T, V, false, false, false, 4>(u, v, p.nx, p.ny, x0, ys, ye, -1, 0, m);
       bits = dbits(m);
     }
   } else {
     T m = T(0);
-    if (ys < p.ny) jacobi_march<T, V, JM_NATIVE, false>(u, v, p.nx, p.ny, x0, ys, ye, -1, m);
+    if (ys < p.ny) jacobi_march_pf<T, V, false, false, false, 4>(u, v, p.nx, p.ny, x0, ys, ye, -1, 0, m);
     bits = dbits((double)m);
   }
   block_max_to<BX * BY>(bits, resid);

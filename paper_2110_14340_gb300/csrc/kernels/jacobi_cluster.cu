@@ -1,0 +1,339 @@
+// jacobi_cluster.cu - all sweeps of a small 5-point FP64 grid in one launch of
+// one thread-block cluster, the field resident in the cluster's shared memory.
+//
+// A 256 x 256 FP64 grid is 512 KB per field: too large for one SM, small
+// enough for the distributed shared memory of a cluster of 8 or 16 CTAs.  A
+// sweep of such a grid is a few microseconds of launch latency and a fraction
+// of that of work, so one launch per sweep (even replayed from a CUDA graph)
+// is latency-bound.  Here CTA r of the cluster keeps rows [r*rows, (r+1)*rows)
+// of both ping-pong fields plus one halo row above and below in its shared
+// memory.  A sweep writes its first and last own rows also into the
+// neighbours' halo rows (st.shared::cluster), then one cluster barrier
+// (release/acquire) orders every CTA's writes before the next sweep; the
+// residual of a sweep is reduced from per-warp partials after that barrier,
+// so a sweep costs one barrier and no other synchronisation.  HBM is touched
+// once to load the field and once to store the result.
+//
+// The arithmetic is that of the resident fixed-point path (and of its native
+// FP64 fallback) bit for bit: max|u| over the grid picks F, the first sweep
+// converts on load, intermediate sweeps keep v 2^F = (S + 2) >> 2, the last
+// writes fx_to(S, F + 2) and, if there were two sweeps or more, the other
+// buffer receives sweep n-1 in the internal form, exactly as jacc_sweep's
+// launch-per-sweep sequence leaves it.
+#include "jacc_device.cuh"
+
+#include <cuda_runtime.h>
+
+#include "jacobi_cluster.h"
+
+namespace {
+
+constexpr int kThreads = 1024;
+constexpr int kResChunk = 512;  // sweeps whose residuals are held in shared memory before a flush
+
+JD u32 cluster_rank() {
+  u32 r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// All threads of all CTAs of the cluster; orders shared and global memory.
+JD void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Shared-memory address of `p` (this CTA) in CTA `rank` of the cluster.
+JD u32 map_rank(const void* p, u32 rank) {
+  u32 out;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(out) : "r"(smem_u32(p)), "r"(rank));
+  return out;
+}
+JD void st_cluster_u64(u32 addr, u64 v) {
+  asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(addr), "l"(v) : "memory");
+}
+JD u64 ld_cluster_u64(u32 addr) {
+  u64 v;
+  asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(addr) : "memory");
+  return v;
+}
+
+template <int NC>
+__global__ void __launch_bounds__(kThreads) jacc_k_jacobi_cluster(JClusterArgs a) {
+  extern __shared__ __align__(16) u64 smem[];
+  __shared__ u64 part_max;
+  const i64 nx = a.nx, ny = a.ny, rows = a.rows, pitch = a.pitch;
+  const int t = threadIdx.x;
+  const u32 rank = cluster_rank();
+  const i64 r0 = (i64)rank * rows;
+  const i64 r1 = (r0 + rows < ny) ? r0 + rows : ny;
+  const i64 nr = (r1 > r0) ? r1 - r0 : 0;  // own rows (0 for a CTA past the grid)
+  u64* const bufA = smem;                       // local row lr <-> grid row r0 - 1 + lr
+  u64* const bufB = smem + (rows + 2) * pitch;
+
+  // max |u| over the grid: this CTA's rows, then every CTA's partial
+  u64 m = 0;
+  for (i64 i = t; i < nr * nx; i += kThreads) {
+    const u64 b = dbits(a.u[r0 * nx + i]) & 0x7fffffffffffffffull;
+    m = b > m ? b : m;
+  }
+  m = warp_max_u64(m);
+  __shared__ u64 red[kThreads / 32];
+  if ((t & 31) == 0) red[t >> 5] = m;
+  __syncthreads();
+  if (t == 0) {
+    u64 w = 0;
+    for (int k = 0; k < kThreads / 32; ++k) w = red[k] > w ? red[k] : w;
+    part_max = w;
+  }
+  cluster_sync();
+  u64 gmax = 0;
+  for (int k = 0; k < NC; ++k) {
+    const u64 w = ld_cluster_u64(map_rank(&part_max, (u32)k));
+    gmax = w > gmax ? w : gmax;
+  }
+  const int F = a.native ? -1 : fx_frac_bits(gmax);
+  const bool fixed = F >= 0;
+
+  // load own rows and the two halo rows, converted to the working form
+  for (i64 lr = 0; lr < nr + 2; ++lr) {
+    const i64 g = r0 - 1 + lr;
+    if (g < 0 || g >= ny) continue;
+    for (i64 x = t; x < nx; x += kThreads) {
+      const double d = a.u[g * nx + x];
+      bufA[lr * pitch + x] = fixed ? (u64)fx_from(d, F) : dbits(d);
+    }
+  }
+  __syncthreads();
+
+  const int n = a.nsweeps;
+  // this thread's items: column pair cp of local row lr, advanced by
+  // kThreads items per step (32-bit index arithmetic, no division per item)
+  const int half = (int)((nx + 1) / 2);  // column pairs per row
+  const int step_rows = kThreads / half, step_cols = kThreads % half;
+  const int nitems = (int)nr * half;
+  // x-neighbour rows of the cluster neighbours, for pushing edge rows
+  const bool push_up = rank > 0 && nr > 0 && r0 >= 1;  // first own row -> previous CTA's lower halo row
+  const bool push_dn = nr > 0 && r1 < ny;              // last own row -> next CTA's upper halo row
+  __shared__ u64 wred[2][kThreads / 32];               // per-warp residual partials, by sweep parity
+  __shared__ u64 rres[kResChunk];                      // this CTA's residual maxima of the current chunk
+  for (int k = 0; k < n; ++k) {
+    const u64* src = (k & 1) ? bufB : bufA;
+    u64* dst = (k & 1) ? bufA : bufB;
+    const bool last = k == n - 1;
+    u64 rmax_fx = 0;
+    double rmax_nat = 0.0;
+    int lr = 1 + t / half, cp = t % half;
+    if (fixed && !last) {
+      // intermediate fixed-point sweeps: a column pair per item, 16-byte
+      // shared-memory accesses (pitch is even, so every pair is aligned; an
+      // odd nx pads each row by one word, which is written but never used)
+      for (int it = t; it < nitems; it += kThreads) {
+        const i64 x0 = 2 * (i64)cp;
+        const i64 g = r0 - 1 + lr;
+        const bool yin = g >= 1 && g <= ny - 2;
+        const bool in0 = yin && x0 >= 1 && x0 <= nx - 2, in1 = yin && x0 + 1 <= nx - 2;
+        const u64* rc = src + lr * pitch + x0;
+        const longlong2 c = *reinterpret_cast<const longlong2*>(rc);
+        const longlong2 up = *reinterpret_cast<const longlong2*>(rc - pitch);
+        const longlong2 dn = *reinterpret_cast<const longlong2*>(rc + pitch);
+        const i64 xl = (i64)rc[-1], xr = (i64)rc[2];
+        const i64 s0 = (up.x + dn.x) + (xl + c.y);
+        const i64 s1 = (up.y + dn.y) + (c.x + xr);
+        longlong2 v;
+        v.x = in0 ? (s0 + 2) >> 2 : c.x;
+        v.y = in1 ? (s1 + 2) >> 2 : c.y;
+        const i64 d0 = s0 - c.x * 4, d1 = s1 - c.y * 4;
+        const u64 a0 = (u64)(d0 ^ (d0 >> 63)), a1 = (u64)(d1 ^ (d1 >> 63));  // |d| (one less if negative)
+        rmax_fx = (in0 && a0 > rmax_fx) ? a0 : rmax_fx;
+        rmax_fx = (in1 && a1 > rmax_fx) ? a1 : rmax_fx;
+        *reinterpret_cast<longlong2*>(dst + lr * pitch + x0) = v;
+        // edge rows also go straight into the neighbours' halo rows
+        if (push_up && lr == 1) {
+          const u32 ra = map_rank(dst + (rows + 1) * pitch + x0, rank - 1);
+          st_cluster_u64(ra, (u64)v.x);
+          st_cluster_u64(ra + 8, (u64)v.y);
+        }
+        if (push_dn && lr == nr) {
+          const u32 ra = map_rank(dst + x0, rank + 1);
+          st_cluster_u64(ra, (u64)v.x);
+          st_cluster_u64(ra + 8, (u64)v.y);
+        }
+        cp += step_cols;
+        lr += step_rows;
+        if (cp >= half) {
+          cp -= half;
+          ++lr;
+        }
+      }
+    } else {
+      for (int it = t; it < nitems; it += kThreads) {
+        const i64 x0 = 2 * (i64)cp;
+        const i64 g = r0 - 1 + lr;
+        const bool yin = g >= 1 && g <= ny - 2;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const i64 x = x0 + e;
+          if (x >= nx) break;
+          const bool in = yin && x >= 1 && x <= nx - 2;
+          const u64 cw = src[lr * pitch + x];
+          u64 vw = cw;       // next working word (boundary: unchanged)
+          double out = 0.0;  // FP64 result (last sweep)
+          if (fixed) {
+            const i64 c = (i64)cw;
+            if (in) {
+              const i64 s = ((i64)src[(lr - 1) * pitch + x] + (i64)src[(lr + 1) * pitch + x]) +
+                            ((i64)src[lr * pitch + x - 1] + (i64)src[lr * pitch + x + 1]);
+              vw = (u64)((s + 2) >> 2);
+              if (last) out = fx_to(s, F + 2);
+              const i64 d = s - c * 4;
+              const u64 ad = (u64)(d ^ (d >> 63));  // |d| (one less for negative d), as the sweep kernels
+              rmax_fx = ad > rmax_fx ? ad : rmax_fx;
+            } else if (last) {
+              out = (n == 1) ? a.u[g * nx + x] : fx_to(c, F);
+            }
+          } else {
+            const double c = __longlong_as_double((i64)cw);
+            if (in) {
+              const double s = (__longlong_as_double((i64)src[(lr - 1) * pitch + x]) +
+                                __longlong_as_double((i64)src[(lr + 1) * pitch + x])) +
+                               (__longlong_as_double((i64)src[lr * pitch + x - 1]) +
+                                __longlong_as_double((i64)src[lr * pitch + x + 1]));
+              const double r = 0.25 * s;
+              vw = dbits(r);
+              out = r;
+              double d = r - c;
+              d = d < 0.0 ? -d : d;
+              rmax_nat = d > rmax_nat ? d : rmax_nat;
+            } else {
+              out = c;
+            }
+          }
+          if (last) {
+            a.res[g * nx + x] = out;
+            if (n >= 2) a.oth[g * nx + x] = __longlong_as_double((i64)cw);
+          } else {
+            dst[lr * pitch + x] = vw;
+            // edge rows also go straight into the neighbours' halo rows
+            if (push_up && lr == 1) st_cluster_u64(map_rank(dst + (rows + 1) * pitch + x, rank - 1), vw);
+            if (push_dn && lr == nr) st_cluster_u64(map_rank(dst + x, rank + 1), vw);
+          }
+        }
+        cp += step_cols;
+        lr += step_rows;
+        if (cp >= half) {
+          cp -= half;
+          ++lr;
+        }
+      }
+    }
+    const u64 bits = warp_max_u64(fixed ? dbits(fx_to_u(rmax_fx, F + 2)) : dbits(rmax_nat));
+    if ((t & 31) == 0) wred[k & 1][t >> 5] = bits;
+    // orders this sweep's shared-memory writes (local and pushed) before any
+    // CTA's next sweep, and keeps every CTA's shared memory alive
+    cluster_sync();
+    if (t < 32) {  // this CTA's residual of sweep k; wred[k & 1] is next written two sweeps later
+      u64 w = t < kThreads / 32 ? wred[k & 1][t] : 0ull;
+      w = warp_max_u64(w);
+      if (t == 0) rres[k % kResChunk] = w;
+    }
+    // Residuals leave the cluster in chunks: a global write before a barrier
+    // would make the barrier's release wait for it, so each sweep's CTA
+    // maxima stay in shared memory until the chunk ends; then CTA 0 takes
+    // the maximum over the cluster and stores it (plain stores, no atomics).
+    if (k % kResChunk == kResChunk - 1 || last) {
+      cluster_sync();  // every CTA's maxima of this chunk are written
+      const int k0 = k - k % kResChunk;
+      if (rank == 0 && a.resid) {
+        for (int i = t; i <= k - k0; i += kThreads) {
+          u64 w = 0;
+          for (int r = 0; r < NC; ++r) {
+            const u64 v = ld_cluster_u64(map_rank(&rres[i], (u32)r));
+            w = v > w ? v : w;
+          }
+          a.resid[k0 + i] = __longlong_as_double((i64)w);
+        }
+      }
+      if (last) cluster_sync();  // CTA 0's remote reads precede every exit
+    }
+  }
+}
+
+template <int NC> cudaError_t launch_nc(const JClusterArgs& a, size_t smem, cudaStream_t s) {
+  const void* f = (const void*)jacc_k_jacobi_cluster<NC>;
+  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (NC > 8) {
+    e = cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(NC, 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = NC;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, jacc_k_jacobi_cluster<NC>, a);
+}
+
+template <int NC> bool fits_nc(const JClusterArgs& a, size_t smem) {
+  const void* f = (const void*)jacc_k_jacobi_cluster<NC>;
+  if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return false;
+  if (NC > 8 && cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) return false;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(NC, 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = NC;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, f, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return clusters >= 1;
+}
+
+size_t smem_bytes(i64 ny, i64 pitch, int nc, i64* rows) {
+  *rows = (ny + nc - 1) / nc;
+  return (size_t)(2 * (*rows + 2) * pitch) * sizeof(u64);
+}
+
+}  // namespace
+
+int jacobi_cluster_plan(long long nx, long long ny, int* nc_out) {
+  const i64 pitch = (nx + 1) & ~1ll;
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
+  const size_t budget = (size_t)optin - 8192;  // static shared memory of the kernel
+  for (int nc : {16, 8}) {
+    i64 rows = 0;
+    const size_t smem = smem_bytes(ny, pitch, nc, &rows);
+    if (smem > budget || rows < 1) continue;
+    JClusterArgs a = {};
+    a.nx = nx;
+    a.ny = ny;
+    a.rows = rows;
+    a.pitch = pitch;
+    if (nc == 16 ? fits_nc<16>(a, smem) : fits_nc<8>(a, smem)) {
+      *nc_out = nc;
+      return 1;
+    }
+  }
+  return 0;
+}
+
+cudaError_t launch_jacobi_cluster(JClusterArgs a, int nc, cudaStream_t s) {
+  a.pitch = (a.nx + 1) & ~1ll;
+  const size_t smem = smem_bytes(a.ny, a.pitch, nc, &a.rows);
+  return nc == 16 ? launch_nc<16>(a, smem, s) : launch_nc<8>(a, smem, s);
+}

@@ -26,6 +26,7 @@ F32, F64 = 32, 64
 DIRICHLET, PERIODIC = 0, 1
 ARITH_AUTO, ARITH_NATIVE = 0, 1
 SPEC_JIT = 1
+SPEC_CLUSTER = 2
 SWEEP_GRAPH = 1
 
 
@@ -99,6 +100,7 @@ SIGNATURES = {
     "jacc_launch": ([P, P, P, P, C.c_size_t], C.c_int32),
     "jacc_launch_static": ([P, P, P, P, C.c_size_t], C.c_int32),
     "jacc_sweep": ([P, P, P, C.c_int32, P, C.c_uint32, C.c_size_t, P], C.c_int32),
+    "jacc_sweep_until": ([P, P, P, C.c_int32, C.c_double, P, P, C.c_size_t], C.c_int32),
     "jacc_shutdown": ([], C.c_int32),
     "jacc_batch_create": ([C.c_int32, P, P, P], C.c_int32),
     "jacc_batch_configure": ([P, P], C.c_int32),
@@ -198,7 +200,7 @@ class Desc:
     """A kernel descriptor (jacc_kernel_desc) and the field shape it implies."""
 
     def __init__(self, stencil, dtype, nx, ny, nz=1, coeffs=(0.0, 0.0, 0.0, 0.0), tile_id=-1, jit=False,
-                 arith=ARITH_AUTO, boundary=None, tblock=0):
+                 arith=ARITH_AUTO, boundary=None, tblock=0, cluster=False):
         d = KernelDesc()
         d.stencil = stencil
         d.dtype = dtype
@@ -209,7 +211,7 @@ class Desc:
         for j in range(4):
             d.coeffs[j] = float(cs[j])
         d.arith = arith
-        d.flags = SPEC_JIT if jit else 0
+        d.flags = (SPEC_JIT if jit else 0) | (SPEC_CLUSTER if cluster else 0)
         d.tblock = tblock
         self.desc = d
         self.shape = (ny, nx) if stencil == STENCIL_5PT else (nz, ny, nx)
@@ -298,6 +300,21 @@ def sweep(k, u0, u1, nsweeps, resid=None, graph=True, stream=None):
     _check(lib().jacc_sweep(k.handle, _field(k, u0, "u0"), _field(k, u1, "u1"), nsweeps, _resid(resid),
                             SWEEP_GRAPH if graph else 0, _stream(stream), C.byref(fb)))
     return fb.value
+
+
+def sweep_until(k, u0, u1, max_sweeps, tol, resid, status, stream=None):
+    """Sweeps until a residual <= tol or max_sweeps; device-side loop (no host wait).
+
+    resid: CUDA float64 tensor of >= max_sweeps elements; status: CUDA int32
+    tensor of >= 2 elements, receiving (sweeps run, result buffer 0/1)."""
+    import torch
+    if resid.numel() < max_sweeps:
+        raise ValueError("resid needs max_sweeps elements")
+    if not (isinstance(status, torch.Tensor) and status.is_cuda and status.dtype == torch.int32
+            and status.is_contiguous() and status.numel() >= 2):
+        raise ValueError("status must be a contiguous CUDA int32 tensor of >= 2 elements")
+    _check(lib().jacc_sweep_until(k.handle, _field(k, u0, "u0"), _field(k, u1, "u1"), int(max_sweeps), float(tol),
+                                  _resid(resid), status.data_ptr(), _stream(stream)))
 
 
 def shutdown():

@@ -97,6 +97,56 @@ def test_jacobi2d_full_size_256_100_sweeps(orc):
     assert np.all(gr[1:] <= gr[:-1] + 1e-15)
 
 
+def run_both(k, u, nsweeps):
+    """Both buffers and the residuals after a sweep sequence."""
+    a = torch.from_numpy(np.ascontiguousarray(u)).to(DEV)
+    b = torch.zeros_like(a)
+    res = torch.full((nsweeps,), -1.0, dtype=torch.float64, device=DEV)
+    fb = jacc.sweep(k, a, b, nsweeps, res)
+    torch.cuda.synchronize()
+    return fb, a.cpu().numpy(), b.cpu().numpy(), res.cpu().numpy()
+
+
+@pytest.mark.parametrize("shape,nsweeps,arith", [
+    ((256, 256), 100, jacc.ARITH_AUTO), ((130, 37), 7, jacc.ARITH_AUTO), ((3, 3), 1, jacc.ARITH_AUTO),
+    ((17, 255), 2, jacc.ARITH_AUTO), ((64, 41), 1, jacc.ARITH_AUTO), ((101, 37), 5, jacc.ARITH_NATIVE),
+    ((320, 300), 3, jacc.ARITH_AUTO)])
+def test_jacobi2d_cluster_resident_bit_identical_to_per_sweep(orc, shape, nsweeps, arith):
+    # the whole sequence in one cluster launch: result buffer, the other
+    # buffer (sweep n-1 in the internal form) and residuals equal the
+    # launch-per-sweep sequence bit for bit
+    ny, nx = shape
+    u = inputs.jacobi2d_field(nx, ny, seed=21)
+    kc = jacc.Kernel(jacc.STENCIL_5PT, jacc.F64, nx, ny, 1, arith=arith, cluster=True)
+    kp = jacc.Kernel(jacc.STENCIL_5PT, jacc.F64, nx, ny, 1, arith=arith)
+    fc, ac, bc, rc = run_both(kc, u, nsweeps)
+    fp, ap, bp, rp = run_both(kp, u, nsweeps)
+    assert fc == fp == nsweeps % 2
+    assert np.array_equal(ac.view(np.int64), ap.view(np.int64))
+    assert np.array_equal(bc.view(np.int64), bp.view(np.int64))
+    assert np.array_equal(rc, rp)
+    o, orr = orc.jacobi2d_run(u, nsweeps)
+    assert nerr(bc if fc else ac, o) <= TOL64
+    assert np.max(np.abs(rc - orr)) <= TOL64
+
+
+def test_jacobi2d_cluster_nonfinite_input_and_limits(orc):
+    ny, nx = 40, 52
+    u = inputs.jacobi2d_field(nx, ny, seed=22)
+    u[10, 11] = np.inf  # routes the sequence to native FP64, as in the per-sweep path
+    kc = jacc.Kernel(jacc.STENCIL_5PT, jacc.F64, nx, ny, 1, cluster=True)
+    kp = jacc.Kernel(jacc.STENCIL_5PT, jacc.F64, nx, ny, 1)
+    fc, ac, bc, rc = run_both(kc, u, 4)
+    fp, ap, bp, rp = run_both(kp, u, 4)
+    assert np.array_equal(ac.view(np.int64), ap.view(np.int64)) and np.array_equal(rc.view(np.int64), rp.view(np.int64))
+    with pytest.raises(RuntimeError, match="UNSUPPORTED"):
+        jacc.Kernel(jacc.STENCIL_5PT, jacc.F32, nx, ny, 1, cluster=True)
+    with pytest.raises(RuntimeError, match="UNSUPPORTED"):
+        jacc.Kernel(jacc.STENCIL_5PT, jacc.F64, 4096, 4096, 1, cluster=True)
+    with pytest.raises(RuntimeError, match="UNSUPPORTED"):
+        jacc.Kernel(jacc.STENCIL_7PT, jacc.F64, 16, 16, 16, coeffs=(0.1,), cluster=True)
+
+
 # ----------------------------------------------------------------------------- 7-point heat
 
 @pytest.mark.parametrize("tile", range(24))
