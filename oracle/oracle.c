@@ -254,6 +254,47 @@ int orc_heat3d_run(int64_t nx, int64_t ny, int64_t nz, double r, double* u0, dou
   return (nsweeps % 2 == 0) ? 0 : 1;
 }
 
+/* Variable-coefficient 19-point Jacobi step (see oracle.h for the formula). */
+double orc_var19_sweep(int64_t nx, int64_t ny, int64_t nz, float omega, const float* const* c, const float* p,
+                       float* v) {
+  const int64_t sy = nx, sz = nx * ny;
+  const float *a0 = c[0], *a1 = c[1], *a2 = c[2], *a3 = c[3], *b0 = c[4], *b1 = c[5], *b2 = c[6];
+  const float *c0 = c[7], *c1 = c[8], *c2 = c[9], *wrk1 = c[10], *bnd = c[11];
+  double gosa = 0.0;
+  for (int64_t z = 0; z < nz; ++z)
+    for (int64_t y = 0; y < ny; ++y)
+      for (int64_t x = 0; x < nx; ++x) {
+        const int64_t i = z * sz + y * sy + x;
+        if (z == 0 || z == nz - 1 || y == 0 || y == ny - 1 || x == 0 || x == nx - 1) {
+          v[i] = p[i];
+          continue;
+        }
+        float s0 = a0[i] * p[i + 1] + a1[i] * p[i + sy] + a2[i] * p[i + sz];
+        s0 = s0 + b0[i] * (p[i + 1 + sy] - p[i + 1 - sy] - p[i - 1 + sy] + p[i - 1 - sy]);
+        s0 = s0 + b1[i] * (p[i + sy + sz] - p[i - sy + sz] - p[i + sy - sz] + p[i - sy - sz]);
+        s0 = s0 + b2[i] * (p[i + 1 + sz] - p[i - 1 + sz] - p[i + 1 - sz] + p[i - 1 - sz]);
+        s0 = s0 + c0[i] * p[i - 1] + c1[i] * p[i - sy] + c2[i] * p[i - sz] + wrk1[i];
+        const float ss = (s0 * a3[i] - p[i]) * bnd[i];
+        v[i] = p[i] + omega * ss;
+        gosa += (double)ss * (double)ss;
+      }
+  return gosa;
+}
+
+int orc_var19_run(int64_t nx, int64_t ny, int64_t nz, float omega, const float* const* c, float* u0, float* u1,
+                  int32_t nsweeps, double* resid) {
+  float* a = u0;
+  float* b = u1;
+  for (int32_t k = 0; k < nsweeps; ++k) {
+    const double g = orc_var19_sweep(nx, ny, nz, omega, c, a, b);
+    if (resid) resid[k] = g;
+    float* t = a;
+    a = b;
+    b = t;
+  }
+  return (nsweeps % 2 == 0) ? 0 : 1;
+}
+
 /* 27-point periodic stencil in FP32.  Offsets (dx,dy,dz) in {-1,0,1}^3 are
  * classed by how many are non-zero: 0 centre, 1 face (6), 2 edge (12),
  * 3 corner (8).  v = w0*centre + wf*F + we*E + wc*C, where F, E, C are the

@@ -82,6 +82,24 @@ int orc_box27_run_f64(int64_t nx, int64_t ny, int64_t nz, const double w[4], dou
 int orc_box27_run(int64_t nx, int64_t ny, int64_t nz, const float w[4], float* u0, float* u1, int32_t nsweeps,
                   double* sums);
 
+/* Variable-coefficient 19-point Jacobi step in FP32 (the iteration of the
+ * paper's Himeno workload, §5.2; written from the stencil's definition).
+ * Fields are [nz][ny][nx] (x fastest); c[0..11] are the coefficient fields
+ * a0 a1 a2 a3 b0 b1 b2 c0 c1 c2 wrk1 bnd.  For each interior point, with
+ * p(dx,dy,dz) the neighbour at that offset:
+ *   s0 = a0 p(+x) + a1 p(+y) + a2 p(+z)
+ *      + b0 (p(+x+y) - p(+x-y) - p(-x+y) + p(-x-y))
+ *      + b1 (p(+y+z) - p(-y+z) - p(+y-z) + p(-y-z))
+ *      + b2 (p(+x+z) - p(-x+z) - p(+x-z) + p(-x-z))
+ *      + c0 p(-x) + c1 p(-y) + c2 p(-z) + wrk1
+ *   ss = (s0 a3 - p) bnd,   v = p + omega ss
+ * evaluated left to right in FP32; boundary points keep p.  Returns the FP64
+ * sum of ss^2 (each ss^2 formed in FP64) over the interior. */
+double orc_var19_sweep(int64_t nx, int64_t ny, int64_t nz, float omega, const float* const* c, const float* p,
+                       float* v);
+int orc_var19_run(int64_t nx, int64_t ny, int64_t nz, float omega, const float* const* c, float* u0, float* u1,
+                  int32_t nsweeps, double* resid);
+
 /* Reductions (FP64 accumulation). */
 double orc_maxabs_diff(const double* a, const double* b, int64_t n);
 double orc_sum_f64(const double* a, int64_t n);

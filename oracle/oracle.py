@@ -64,6 +64,10 @@ def lib():
         L.orc_box27_sweep_f64.argtypes = [C.c_int64, C.c_int64, C.c_int64, P, P, P]
         L.orc_box27_run_f64.restype = C.c_int
         L.orc_box27_run_f64.argtypes = [C.c_int64, C.c_int64, C.c_int64, P, P, P, C.c_int32, P]
+        L.orc_var19_sweep.restype = C.c_double
+        L.orc_var19_sweep.argtypes = [C.c_int64, C.c_int64, C.c_int64, C.c_float, P, P, P]
+        L.orc_var19_run.restype = C.c_int
+        L.orc_var19_run.argtypes = [C.c_int64, C.c_int64, C.c_int64, C.c_float, P, P, P, C.c_int32, P]
         L.orc_maxabs_diff.restype = C.c_double
         L.orc_maxabs_diff.argtypes = [P, P, C.c_int64]
         L.orc_sum_f64.restype = C.c_double
@@ -203,6 +207,38 @@ def box27_run_f64(u, w, nsweeps):
     sums = np.zeros(max(1, nsweeps), dtype=np.float64)
     par = lib().orc_box27_run_f64(nx, ny, nz, _ptr(w), _ptr(a), _ptr(b), nsweeps, _ptr(sums))
     return (a if par == 0 else b), sums[:nsweeps]
+
+
+def _coeff_ptrs(coeffs, shape):
+    """12 coefficient fields (a0 a1 a2 a3 b0 b1 b2 c0 c1 c2 wrk1 bnd) -> kept arrays + pointer table."""
+    if len(coeffs) != 12:
+        raise ValueError("12 coefficient fields")
+    keep = [_c(f, np.float32) for f in coeffs]
+    for f in keep:
+        if f.shape != shape:
+            raise ValueError("coefficient field shape mismatch")
+    table = (C.c_void_p * 12)(*[f.ctypes.data for f in keep])
+    return keep, table
+
+
+def var19_sweep(p, coeffs, omega):
+    """One variable-coefficient 19-point step (FP32); returns (v, sum of ss^2)."""
+    a = _c(p, np.float32)
+    v = np.empty_like(a)
+    nz, ny, nx = a.shape
+    keep, table = _coeff_ptrs(coeffs, a.shape)
+    g = lib().orc_var19_sweep(nx, ny, nz, float(omega), table, _ptr(a), _ptr(v))
+    return v, g
+
+
+def var19_run(p, coeffs, omega, nsweeps):
+    a = _c(p, np.float32).copy()
+    b = np.empty_like(a)
+    nz, ny, nx = a.shape
+    keep, table = _coeff_ptrs(coeffs, a.shape)
+    res = np.zeros(max(1, nsweeps), dtype=np.float64)
+    par = lib().orc_var19_run(nx, ny, nz, float(omega), table, _ptr(a), _ptr(b), nsweeps, _ptr(res))
+    return (a if par == 0 else b), res[:nsweeps]
 
 
 # ----------------------------------------------------------------------------- reductions
