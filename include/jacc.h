@@ -117,10 +117,22 @@ jacc_status jacc_region_analyze(int32_t nloops, const jacc_loop* loops, int32_t 
  *   JACC_STENCIL_7PT  (3D): v = u + r * (sum of the 6 face neighbours - 6 u),  r = coeffs[0]
  *   JACC_STENCIL_27PT (3D): v = w0*centre + wf*faces + we*edges + wc*corners,
  *                           (w0, wf, we, wc) = coeffs[0..3]
+ *   JACC_STENCIL_19PT (3D, FP32, variable coefficients; swept with
+ *                 jacc_sweep_coeffs): the Jacobi step of the paper's Himeno
+ *                 workload (§5.2), coeffs[0] = omega, twelve coefficient
+ *                 fields a0 a1 a2 a3 b0 b1 b2 c0 c1 c2 wrk1 bnd:
+ *       s0 = a0 u(+x) + a1 u(+y) + a2 u(+z)
+ *          + b0 (u(+x+y) - u(+x-y) - u(-x+y) + u(-x-y))
+ *          + b1 (u(+y+z) - u(-y+z) - u(+y-z) + u(-y-z))
+ *          + b2 (u(+x+z) - u(-x+z) - u(+x-z) + u(-x-z))
+ *          + c0 u(-x) + c1 u(-y) + c2 u(-z) + wrk1
+ *       ss = (s0 a3 - u) bnd,   v = u + omega ss
+ *     (u(+x-y) is the neighbour at x+1, y-1, and so on).
  * Fused reduction written per sweep into resid_dev[k] (FP64):
  *   5PT and 7PT : max over interior points of |v - u| (the change made by
  *                 the sweep);
- *   27PT        : the sum of the output field (every materialised sweep).
+ *   27PT        : the sum of the output field (every materialised sweep);
+ *   19PT        : the sum over interior points of ss^2.
  *
  * dtype JACC_F64 stores FP64.  Its arithmetic (arith):
  *   JACC_ARITH_AUTO    exact 64-bit fixed-point integer arithmetic when the
@@ -156,6 +168,7 @@ jacc_status jacc_region_analyze(int32_t nloops, const jacc_loop* loops, int32_t 
 #define JACC_STENCIL_5PT 5
 #define JACC_STENCIL_7PT 7
 #define JACC_STENCIL_27PT 27
+#define JACC_STENCIL_19PT 19
 #define JACC_F32 32
 #define JACC_F64 64
 #define JACC_DIRICHLET 0
@@ -245,6 +258,19 @@ jacc_status jacc_launch(jacc_kernel k, const void* u_in, void* u_out, double* re
 #define JACC_SWEEP_GRAPH 1u
 jacc_status jacc_sweep(jacc_kernel k, void* u0, void* u1, int32_t nsweeps, double* resid_dev, uint32_t flags,
                        uintptr_t stream, int32_t* final_buf);
+
+/* jacc_sweep_coeffs: nsweeps ping-pong sweeps of a JACC_STENCIL_19PT kernel,
+ * as jacc_sweep (resid_dev, flags, stream and final_buf alike), with its
+ * twelve coefficient fields: fields[0..11] = a0 a1 a2 a3 b0 b1 b2 c0 c1 c2
+ * wrk1 bnd, each nx*ny*nz FP32 values in device memory, 16-byte aligned,
+ * caller-owned, read-only during the call and not overlapping u0 or u1
+ * (nfields must be 12).  Graphs (JACC_SWEEP_GRAPH) are cached by every
+ * pointer of the call.  The 19-point kernel has one tile (32 x 4 threads,
+ * 16-byte columns, input planes staged by bulk copies, 64-plane march); nx
+ * must be a multiple of 4.  jacc_launch and jacc_sweep reject 19PT handles. */
+jacc_status jacc_sweep_coeffs(jacc_kernel k, void* u0, void* u1, int32_t nsweeps, const void* const* fields,
+                              int32_t nfields, double* resid_dev, uint32_t flags, uintptr_t stream,
+                              int32_t* final_buf);
 
 /* jacc_sweep_until (no counterpart in the paper, which runs a fixed iteration
  * count; §5.2 notes that Himeno reduces its error each iteration): sweeps

@@ -64,7 +64,13 @@ struct Kernel {
   u64* scratch = nullptr;       // max-abs word for direct launches (device)
   std::map<GraphKey, SweepGraph> graphs;
   std::map<UntilKey, UntilGraph> until_graphs;
+  std::map<std::string, SweepGraph> coeff_graphs;  // jacc_sweep_coeffs graphs, keyed by all pointers
 };
+
+// The variable-coefficient 19-point kernel (one fixed tile).
+void var19_geometry(long long nx, long long ny, long long nz, dim3* grid, dim3* block);
+cudaError_t launch_var19(const float* u, float* v, const JParams& p, double* resid, dim3 grid, dim3 block,
+                         cudaStream_t s);
 
 // Validates a pair of field pointers for kernel k (non-null, 16-byte aligned,
 // not overlapping).

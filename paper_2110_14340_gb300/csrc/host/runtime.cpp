@@ -140,7 +140,16 @@ static int plan_fixed(const jacc_kernel_desc& d, JParams& p) {
 }
 
 static jacc_status validate(const jacc_kernel_desc& d) {
-  if (d.stencil != 5 && d.stencil != 7 && d.stencil != 27) return fail(JACC_ERR_INVALID_ARG, "unknown stencil");
+  if (d.stencil != 5 && d.stencil != 7 && d.stencil != 27 && d.stencil != 19)
+    return fail(JACC_ERR_INVALID_ARG, "unknown stencil");
+  if (d.stencil == 19) {
+    if (d.dtype != JACC_F32) return fail(JACC_ERR_UNSUPPORTED, "19-point variable-coefficient stencil: FP32 only");
+    if (d.boundary != JACC_DIRICHLET) return fail(JACC_ERR_UNSUPPORTED, "19-point: Dirichlet only");
+    if (d.nx % 4) return fail(JACC_ERR_UNSUPPORTED, "19-point: nx must be a multiple of 4 (16-byte rows)");
+    if (d.flags) return fail(JACC_ERR_UNSUPPORTED, "19-point: no JIT or cluster variant");
+    if (d.tblock > 1) return fail(JACC_ERR_UNSUPPORTED, "19-point: no temporal blocking");
+    if (d.tile_id != -1) return fail(JACC_ERR_INVALID_ARG, "19-point: one fixed tile (tile_id must be -1)");
+  }
   if (d.dtype != JACC_F32 && d.dtype != JACC_F64) return fail(JACC_ERR_INVALID_ARG, "dtype must be 32 or 64");
   if (d.tile_id < -1 || d.tile_id >= JACC_NTILES) return fail(JACC_ERR_INVALID_ARG, "tile_id out of range");
   if (d.arith != JACC_ARITH_AUTO && d.arith != JACC_ARITH_NATIVE) return fail(JACC_ERR_INVALID_ARG, "bad arith");
@@ -255,6 +264,11 @@ static void free_kernel(Kernel* k) {
     if (g.second.scratch) cudaFree(g.second.scratch);
   }
   k->graphs.clear();
+  for (auto& g : k->coeff_graphs) {
+    if (g.second.exec) cudaGraphExecDestroy(g.second.exec);
+    if (g.second.graph) cudaGraphDestroy(g.second.graph);
+  }
+  k->coeff_graphs.clear();
   free_until_graphs(*k);
   if (k->scratch) cudaFree(k->scratch);
   if (k->lib) cudaLibraryUnload(k->lib);
@@ -280,7 +294,9 @@ extern "C" jacc_status jacc_specialize(const jacc_kernel_desc* desc, jacc_kernel
   jacc_status st = validate(*desc);
   if (st) return st;
   int tile = desc->tile_id;
-  if (tile < 0) {
+  if (desc->stencil == 19) {
+    tile = 3;  // the kernel's one configuration: 32 x 4 threads, 16-byte columns, 64-plane march
+  } else if (tile < 0) {
     tile = tuned_tile(*desc);
     if (tile < 0 || !tile_valid(*desc, tile)) tile = default_tile(*desc);
   }
@@ -322,7 +338,10 @@ extern "C" jacc_status jacc_specialize(const jacc_kernel_desc* desc, jacc_kernel
     k->grid = dim3(static_cast<unsigned>((desc->nx + tx - 1) / tx), static_cast<unsigned>((desc->ny + ty - 1) / ty),
                    static_cast<unsigned>((desc->nz + c.zc - 1) / c.zc));
   }
-  if (desc->tblock > 1) {
+  if (desc->stencil == 19) {
+    var19_geometry(desc->nx, desc->ny, desc->nz, &k->grid, &k->block);
+    k->func = k->func_out = nullptr;  // launched by jacc_sweep_coeffs only
+  } else if (desc->tblock > 1) {
     // temporally blocked 27-point kernel: 32 x 16 threads over a 128 x 16 region,
     // output tile 120 x (16 - 2T), 64-plane chunks
     const int T = desc->tblock;
@@ -483,6 +502,7 @@ static jacc_status enqueue_one(const Kernel& k, const void* u, void* v, double* 
 extern "C" jacc_status jacc_launch(jacc_kernel h, const void* u_in, void* u_out, double* resid_dev, uintptr_t stream) {
   if (!h) return fail(JACC_ERR_INVALID_ARG, "NULL handle");
   const Kernel& k = *reinterpret_cast<Kernel*>(h);
+  if (k.desc.stencil == 19) return fail(JACC_ERR_INVALID_ARG, "19-point stencil: use jacc_sweep_coeffs");
   jacc_status st = check_buffers(k, u_in, u_out);
   if (st) return st;
   return enqueue_one(k, u_in, u_out, resid_dev, k.scratch, reinterpret_cast<cudaStream_t>(stream));
@@ -524,6 +544,7 @@ extern "C" jacc_status jacc_sweep(jacc_kernel h, void* u0, void* u1, int32_t nsw
   if (nsweeps < 1) return fail(JACC_ERR_INVALID_ARG, "nsweeps must be >= 1");
   if (flags & ~JACC_SWEEP_GRAPH) return fail(JACC_ERR_INVALID_ARG, "unknown sweep flags");
   Kernel& k = *reinterpret_cast<Kernel*>(h);
+  if (k.desc.stencil == 19) return fail(JACC_ERR_INVALID_ARG, "19-point stencil: use jacc_sweep_coeffs");
   jacc_status st = check_buffers(k, u0, u1);
   if (st) return st;
   if (k.tblock > 1 && nsweeps % k.tblock)

@@ -162,6 +162,7 @@ extern "C" jacc_status jacc_sweep_until(jacc_kernel h, void* u0, void* u1, int32
                                         double* resid_dev, int32_t* status_dev, uintptr_t stream) {
   if (!h) return fail(JACC_ERR_INVALID_ARG, "NULL handle");
   Kernel& k = *reinterpret_cast<Kernel*>(h);
+  if (k.desc.stencil == 19) return fail(JACC_ERR_UNSUPPORTED, "jacc_sweep_until: 5-point and 7-point only");
   if (k.desc.stencil == 27)
     return fail(JACC_ERR_UNSUPPORTED, "jacc_sweep_until: the 27-point reduction is a sum, not a convergence measure");
   if (max_sweeps < 1) return fail(JACC_ERR_INVALID_ARG, "max_sweeps must be >= 1");

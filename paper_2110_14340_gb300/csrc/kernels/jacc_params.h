@@ -27,6 +27,10 @@ struct JParams {
   i64 timeout_ns;
   int stall_plane;
   int reserved;
+  // The twelve coefficient fields of the variable-coefficient 19-point
+  // stencil (a0 a1 a2 a3 b0 b1 b2 c0 c1 c2 wrk1 bnd; FP32, device), set per
+  // call; unused by the other stencils.
+  const float* cf[12];
 };
 
 #define JACC_DEV_TIMEOUT (-6)  // the value of JACC_ERR_TIMEOUT

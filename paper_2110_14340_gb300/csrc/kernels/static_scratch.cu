@@ -55,6 +55,7 @@ extern "C" jacc_status jacc_launch_static(jacc_kernel h, const void* u_in, void*
   using jacc::fail;
   if (!h) return fail(JACC_ERR_INVALID_ARG, "NULL handle");
   const jacc::Kernel& k = *reinterpret_cast<jacc::Kernel*>(h);
+  if (k.desc.stencil == 19) return fail(JACC_ERR_INVALID_ARG, "19-point stencil: use jacc_sweep_coeffs");
   if (!u_in || !u_out) return fail(JACC_ERR_INVALID_ARG, "NULL field pointer");
   if ((reinterpret_cast<uintptr_t>(u_in) % 16) || (reinterpret_cast<uintptr_t>(u_out) % 16))
     return fail(JACC_ERR_INVALID_ARG, "field pointers must be 16-byte aligned");

@@ -141,6 +141,30 @@ def box27_field(nx, ny=None, nz=None, seed=6):
     return (np.float32(2.0) * u - np.float32(1.0)).astype(np.float32).reshape(nz, ny, nx)
 
 
+def var19_problem(nx, ny, nz, seed=7):
+    """Synthetic input of the variable-coefficient 19-point stencil: the iterate
+    p ~ U[0,1) and the twelve coefficient fields (a0 a1 a2 a3 b0 b1 b2 c0 c1 c2
+    wrk1 bnd), all FP32 of shape (nz, ny, nx).  Face coefficients a_i, c_i =
+    1 + 0.1 U[-1,1); cross coefficients b_i = 0.05 U[-1,1); a3 = 1 / (sum of
+    the six face coefficients), so s0 a3 is close to a weighted average; source
+    wrk1 = 0.01 U[-1,1); bnd = 1.  Stream k of the generator fills field k."""
+    n = nx * ny * nz
+    shape = (nz, ny, nx)
+
+    def sym(stream, scale):
+        return (np.float32(scale) * (np.float32(2.0) * uniform32(seed, n, stream) - np.float32(1.0))).reshape(shape)
+
+    p = uniform32(seed, n, 0).reshape(shape)
+    a = [(np.float32(1.0) + sym(1 + i, 0.1)).astype(np.float32) for i in range(3)]
+    c = [(np.float32(1.0) + sym(4 + i, 0.1)).astype(np.float32) for i in range(3)]
+    b = [sym(7 + i, 0.05).astype(np.float32) for i in range(3)]
+    tot = a[0] + a[1] + a[2] + c[0] + c[1] + c[2]
+    a3 = (np.float32(1.0) / tot).astype(np.float32)
+    wrk1 = sym(10, 0.01).astype(np.float32)
+    bnd = np.ones(shape, dtype=np.float32)
+    return p.astype(np.float32), [a[0], a[1], a[2], a3, b[0], b[1], b[2], c[0], c[1], c[2], wrk1, bnd]
+
+
 def batched_shapes(ngrids=64, seed=3, lo=128, hi=2048):
     u = uniform64(seed, 2 * ngrids)
     a, b = math.log(lo), math.log(hi)

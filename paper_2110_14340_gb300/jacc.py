@@ -21,7 +21,7 @@ ERR_COMPILE, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_NOMEM = -5, -6, -7, -8
 STATUS_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OUT_OF_BOUNDS", -3: "OVERFLOW", -4: "CUDA", -5: "COMPILE",
                 -6: "TIMEOUT", -7: "UNSUPPORTED", -8: "NOMEM"}
 
-STENCIL_5PT, STENCIL_7PT, STENCIL_27PT = 5, 7, 27
+STENCIL_5PT, STENCIL_7PT, STENCIL_27PT, STENCIL_19PT = 5, 7, 27, 19
 F32, F64 = 32, 64
 DIRICHLET, PERIODIC = 0, 1
 ARITH_AUTO, ARITH_NATIVE = 0, 1
@@ -101,6 +101,7 @@ SIGNATURES = {
     "jacc_launch_static": ([P, P, P, P, C.c_size_t], C.c_int32),
     "jacc_sweep": ([P, P, P, C.c_int32, P, C.c_uint32, C.c_size_t, P], C.c_int32),
     "jacc_sweep_until": ([P, P, P, C.c_int32, C.c_double, P, P, C.c_size_t], C.c_int32),
+    "jacc_sweep_coeffs": ([P, P, P, C.c_int32, P, C.c_int32, P, C.c_uint32, C.c_size_t, P], C.c_int32),
     "jacc_shutdown": ([], C.c_int32),
     "jacc_batch_create": ([C.c_int32, P, P, P], C.c_int32),
     "jacc_batch_configure": ([P, P], C.c_int32),
@@ -299,6 +300,26 @@ def sweep(k, u0, u1, nsweeps, resid=None, graph=True, stream=None):
     fb = C.c_int32(-1)
     _check(lib().jacc_sweep(k.handle, _field(k, u0, "u0"), _field(k, u1, "u1"), nsweeps, _resid(resid),
                             SWEEP_GRAPH if graph else 0, _stream(stream), C.byref(fb)))
+    return fb.value
+
+
+def sweep_coeffs(k, u0, u1, nsweeps, fields, resid=None, graph=True, stream=None):
+    """Sweeps of a 19-point variable-coefficient kernel with its 12 coefficient fields
+    (a0 a1 a2 a3 b0 b1 b2 c0 c1 c2 wrk1 bnd: contiguous CUDA float32 tensors of the field's
+    shape).  Returns 0 if the result is in u0, 1 if in u1."""
+    import torch
+    if len(fields) != 12:
+        raise ValueError("twelve coefficient fields")
+    for f in fields:
+        if (not isinstance(f, torch.Tensor) or not f.is_cuda or f.dtype != torch.float32 or not f.is_contiguous()
+                or tuple(f.shape) != tuple(k.shape)):
+            raise ValueError("coefficient fields must be contiguous CUDA float32 tensors of the field's shape")
+    if resid is not None and resid.numel() < nsweeps:
+        raise ValueError("resid needs nsweeps elements")
+    table = (C.c_void_p * 12)(*[f.data_ptr() for f in fields])
+    fb = C.c_int32(-1)
+    _check(lib().jacc_sweep_coeffs(k.handle, _field(k, u0, "u0"), _field(k, u1, "u1"), nsweeps, table, 12,
+                                   _resid(resid), SWEEP_GRAPH if graph else 0, _stream(stream), C.byref(fb)))
     return fb.value
 
 
