@@ -326,8 +326,9 @@ def _time_ms(fn, reps=3):
 
 def secondary(dev):
     """The other workloads of the path, measured on the same GPU (not part of the timed step):
-    Jacobi 256^2 x100, 64 batched Jacobi grids x500 (persistent vs 64 plain graphs), and the
-    27-point FP32 1024^3 x100 periodic stencil (plain vs temporally blocked)."""
+    Jacobi 256^2 x100 (graph and cluster-resident), 64 batched Jacobi grids x500 (persistent vs
+    64 plain graphs), the 27-point FP32 1024^3 x100 periodic stencil (plain vs temporally
+    blocked), and the variable-coefficient 19-point FP32 stencil on a 512 x 512 x 1024 grid."""
     import numpy as np
     import torch
 
@@ -412,6 +413,24 @@ def secondary(dev):
     c5["sum_check_tolerance"] = 1e-6
     kp.release()
     out["box27_f32_1024_x100"] = c5
+    del a, b
+    torch.cuda.empty_cache()
+    # variable-coefficient 19-point (Himeno-like) FP32, the paper's XL grid size
+    # (512 x 512 x 1024 points, 14 fields = 15 GB), 20 graph-launched sweeps
+    nx, ny, nz = 512, 512, 1024
+    p, fields = inputs.var19_problem_torch(nx, ny, nz, dev, seed=7)
+    q = torch.empty_like(p)
+    k19 = jacc.Kernel(jacc.STENCIL_19PT, jacc.F32, nx, ny, nz, coeffs=(0.8,))
+    r19 = torch.zeros(20, dtype=torch.float64, device=dev)
+    ms19 = _time_ms(lambda: jacc.sweep_coeffs(k19, p, q, 20, fields, r19), reps=3) / 20
+    lup19 = (nx - 2) * (ny - 2) * (nz - 2)
+    out["var19_f32_512x512x1024_x20"] = {
+        "ms_per_sweep": ms19, "GLUP/s": lup19 / ms19 / 1e6,
+        "GB/s_56B_per_update": lup19 * 56 / ms19 / 1e6,
+        "frac_of_measured_hbm": lup19 * 56 / ms19 / 1e6 / 6775.9,
+        "residual_first_last": [float(r19[0]), float(r19[-1])]}
+    k19.release()
+    del p, q, fields
     return out
 
 

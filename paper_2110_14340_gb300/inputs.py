@@ -165,6 +165,26 @@ def var19_problem(nx, ny, nz, seed=7):
     return p.astype(np.float32), [a[0], a[1], a[2], a3, b[0], b[1], b[2], c[0], c[1], c[2], wrk1, bnd]
 
 
+def var19_problem_torch(nx, ny, nz, device, seed=7):
+    """var19_problem's fields generated on `device` with torch (same numbers)."""
+    import torch
+    n = nx * ny * nz
+    shape = (nz, ny, nx)
+
+    def sym(stream, scale):
+        u = uniform_torch(seed, n, device, torch.float32, stream)
+        return (scale * (2.0 * u - 1.0)).view(shape)
+
+    p = uniform_torch(seed, n, device, torch.float32, 0).view(shape)
+    a = [1.0 + sym(1 + i, 0.1) for i in range(3)]
+    c = [1.0 + sym(4 + i, 0.1) for i in range(3)]
+    b = [sym(7 + i, 0.05) for i in range(3)]
+    a3 = 1.0 / (((((a[0] + a[1]) + a[2]) + c[0]) + c[1]) + c[2])
+    wrk1 = sym(10, 0.01)
+    bnd = torch.ones(shape, dtype=torch.float32, device=device)
+    return p, [a[0], a[1], a[2], a3, b[0], b[1], b[2], c[0], c[1], c[2], wrk1, bnd]
+
+
 def batched_shapes(ngrids=64, seed=3, lo=128, hi=2048):
     u = uniform64(seed, 2 * ngrids)
     a, b = math.log(lo), math.log(hi)
