@@ -435,12 +435,24 @@ def secondary(dev):
 
 
 def profile_case(args):
-    """A 27-point FP32 periodic sweep sequence on an n^3 cube, nothing else (for ncu captures)."""
+    """A 27-point FP32 periodic (or 19-point variable-coefficient) sweep sequence on an n^3 cube,
+    nothing else (for ncu captures)."""
     import torch
 
     from paper_2110_14340_gb300 import build, inputs, jacc
     build.build()
     n = args.n
+    if args.profile_case == "var19":
+        p, fields = inputs.var19_problem_torch(n, n, n, "cuda", seed=7)
+        q = torch.empty_like(p)
+        k = jacc.Kernel(jacc.STENCIL_19PT, jacc.F32, n, n, n, coeffs=(0.8,))
+        res = torch.zeros(args.sweeps, dtype=torch.float64, device="cuda")
+        for _ in range(args.warmup + args.steps):
+            jacc.sweep_coeffs(k, p, q, args.sweeps, fields, res)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": args.profile_case, "n": n, "sweeps": args.sweeps,
+                          "runs": args.warmup + args.steps}))
+        return
     w = tuple(float(x) for x in inputs.box27_weights())
     a = inputs.uniform_torch(6, n ** 3, "cuda", torch.float32).mul_(2).sub_(1).view(n, n, n)
     b = torch.empty_like(a)
@@ -464,8 +476,8 @@ def main():
     ap.add_argument("--no-jit", action="store_true", help="use the precompiled kernel instead of the NVRTC variant")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner; use the library's default tile")
     ap.add_argument("--no-secondary", action="store_true", help="skip the other workloads' measurements")
-    ap.add_argument("--profile-case", choices=["box27", "box27-tb2"], default=None,
-                    help="run only a 27-point FP32 sweep sequence on an --n cube (for profilers) and exit")
+    ap.add_argument("--profile-case", choices=["box27", "box27-tb2", "var19"], default=None,
+                    help="run only a 27-point FP32 (or 19-point variable-coefficient) sweep sequence on an --n cube (for profilers) and exit")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the sweep kernel, if captured for this build")
     ap.add_argument("--no-cpu-baseline", action="store_true")

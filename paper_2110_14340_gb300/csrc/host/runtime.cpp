@@ -228,7 +228,7 @@ static std::string key_of(const jacc_kernel_desc& d, int tile) {
 static std::string jit_source(const Kernel& k) {
   const JParams& p = k.params;
   const TileCfg& c = kTiles[k.tile];
-  char buf[2048];
+  char buf[4096];
   const char* T = k.desc.dtype == 64 ? "double" : "float";
   const char* entry = k.desc.stencil == 5 ? "jacobi2d_entry" : (k.desc.stencil == 7 ? "heat3d_entry" : "box27_entry");
   const int zc = k.desc.stencil == 5 ? c.zc / 4 : c.zc;
@@ -240,6 +240,7 @@ static std::string jit_source(const Kernel& k) {
                 "  static constexpr i64 fw0 = %lldll, fw1 = %lldll, fw2 = %lldll, fw3 = %lldll;\n"
                 "  static constexpr int fk = %d, fpath = %d;\n"
                 "};\n"
+                "template <> struct JacobiPrefetch<JFold> { static constexpr bool value = %s; };\n"
                 "extern \"C\" __global__ void __launch_bounds__(%d) jacc_jit(const %s* __restrict__ u, "
                 "%s* __restrict__ v, JParams rt, double* resid, const u64* maxword, int flags) {\n"
                 "  const JFold f{};\n"
@@ -252,6 +253,8 @@ static std::string jit_source(const Kernel& k) {
                 "}\n",
                 (long long)p.nx, (long long)p.ny, (long long)p.nz, p.c0, p.c1, p.c2, p.c3, (long long)p.fa,
                 (long long)p.fb, (long long)p.fw0, (long long)p.fw1, (long long)p.fw2, (long long)p.fw3, p.fk, p.fpath,
+                // small (L2-resident) 2D grids: the prefetching march
+                (k.desc.stencil == 5 && k.desc.nx * k.desc.ny <= (int64_t(1) << 17)) ? "true" : "false",
                 c.bx * c.by, T, T, entry, T, c.bx, c.by, k.vec, zc, c.bx * c.by, T, T, entry, T, c.bx, c.by, k.vec, zc,
                 k.desc.dtype == 64 ? "true" : "false");
   return std::string(device_source()) + buf;

@@ -74,7 +74,7 @@ JD void run_band(const JBGrid& G, const double* src, double* dst, i64 r0, i64 r1
   }
 }
 
-__global__ void __launch_bounds__(kThreads) jacc_k_batched(JBatchParams bp) {
+__global__ void __launch_bounds__(kThreads, 3) jacc_k_batched(JBatchParams bp) {
   __shared__ long long s_ticket;
   __shared__ int s_stop;
   const long long total = (long long)bp.total_items * bp.nsweeps;

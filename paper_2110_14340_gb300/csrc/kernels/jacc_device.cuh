@@ -246,12 +246,25 @@ JD void jacobi_march(const T* __restrict__ u, T* __restrict__ v, i64 nx, i64 ny,
     cur[e] = cvt_in<T, MODE>(rcur[e], F);
     dn[e] = cvt_in<T, MODE>(rdn[e], F);
   }
+  // lanes 0 and 31 read the column beyond the warp's chunk two rows ahead
+  const bool has_edge = xin && ((lane == 0 && x0 >= 1) || (lane == 31 && x0 + V < nx));
+  const T* ecol = u + (lane == 0 ? x0 - 1 : x0 + V);
+  T e0 = T(0), e1 = T(0);
+  if (has_edge) {
+    e0 = ld1<CG>(ecol + ys * nx);
+    if (ys + 1 < ye) e1 = ld1<CG>(ecol + (ys + 1) * nx);
+  }
   for (i64 y = ys; y < ye; ++y) {
     // x neighbours of the row
     W left = __shfl_up_sync(0xffffffffu, cur[V - 1], 1);
     W right = __shfl_down_sync(0xffffffffu, cur[0], 1);
-    if (lane == 0 && xin && x0 >= 1) left = cvt_in<T, MODE>(ld1<CG>(u + y * nx + x0 - 1), F);
-    if (lane == 31 && xin && x0 + V < nx) right = cvt_in<T, MODE>(ld1<CG>(u + y * nx + x0 + V), F);
+    const T edge = e0;
+    e0 = e1;
+    if (has_edge && y + 2 < ye) e1 = ld1<CG>(ecol + (y + 2) * nx);
+    if (has_edge) {
+      if (lane == 0) left = cvt_in<T, MODE>(edge, F);
+      else right = cvt_in<T, MODE>(edge, F);
+    }
     // prefetch row y+3
     T rnn[V];
 #pragma unroll
@@ -1268,11 +1281,24 @@ JD void jacobi_fx_march(const double* __restrict__ u, double* __restrict__ v, i6
     cur[e] = cvt(rcur[e]);
     dn[e] = cvt(rdn[e]);
   }
+  // lanes 0 and 31 read the column beyond the warp's chunk two rows ahead
+  const bool has_edge = xin && ((lane == 0 && x0 >= 1) || (lane == 31 && x0 + V < nx));
+  const double* ecol = u + (lane == 0 ? x0 - 1 : x0 + V);
+  double e0 = 0.0, e1 = 0.0;
+  if (has_edge) {
+    e0 = ld1<CG>(ecol + ys * nx);
+    if (ys + 1 < ye) e1 = ld1<CG>(ecol + (ys + 1) * nx);
+  }
   for (i64 y = ys; y < ye; ++y) {
     i64 left = __shfl_up_sync(0xffffffffu, cur[V - 1], 1);
     i64 right = __shfl_down_sync(0xffffffffu, cur[0], 1);
-    if (lane == 0 && xin && x0 >= 1) left = cvt(ld1<CG>(u + y * nx + x0 - 1));
-    if (lane == 31 && xin && x0 + V < nx) right = cvt(ld1<CG>(u + y * nx + x0 + V));
+    const double edge = e0;
+    e0 = e1;
+    if (has_edge && y + 2 < ye) e1 = ld1<CG>(ecol + (y + 2) * nx);
+    if (has_edge) {
+      if (lane == 0) left = cvt(edge);
+      else right = cvt(edge);
+    }
     double rnn[V];
 #pragma unroll
     for (int e = 0; e < V; ++e) rnn[e] = 0.0;
@@ -2036,6 +2062,13 @@ JD void box27_fx_body(const double* __restrict__ u, double* __restrict__ v, cons
 // sequence and contain no conversion code; EDGE = true ones run the first and
 // last sweeps and single launches.
 
+// Whether the 5-point march prefetches rows and x-edges several rows ahead
+// (jacobi_march_pf).  That pays on small, L2-resident grids, whose sweeps are
+// latency-bound; on large grids its registers cost more occupancy than it
+// gains, so the precompiled kernels (P = JParams) use the plain march and a
+// constant-folded variant opts in by specialising this for its own P.
+template <class P> struct JacobiPrefetch { static constexpr bool value = false; };
+
 template <class T, int BX, int BY, int V, int ZC, bool EDGE, class P>
 JD void jacobi2d_entry(const T* __restrict__ u, T* __restrict__ v, const P& p, const JParams& rt, double* resid,
                        const u64* maxword, int flags) {
@@ -2047,16 +2080,31 @@ JD void jacobi2d_entry(const T* __restrict__ u, T* __restrict__ v, const P& p, c
     const int F = (maxword && p.fpath != JACC_FP_NONE) ? fx_frac_bits(*maxword) : -1;
     if (F >= 0) {
       u64 m = 0;
-      if (ys < p.ny) jacobi_march_pf<double, V, false, true, EDGE, 4>(u, v, p.nx, p.ny, x0, ys, ye, F, flags, m);
+      if (ys < p.ny) {
+        if constexpr (JacobiPrefetch<P>::value)
+          jacobi_march_pf<double, V, false, true, EDGE, 4>(u, v, p.nx, p.ny, x0, ys, ye, F, flags, m);
+        else
+          jacobi_fx_march<V, false, EDGE>(u, v, p.nx, p.ny, x0, ys, ye, F, flags, m);
+      }
       bits = dbits(fx_to_u(m, F + 2));
     } else {
       double m = 0.0;
-      if (ys < p.ny) jacobi_march_pf<T, V, false, false, false, 4>(u, v, p.nx, p.ny, x0, ys, ye, -1, 0, m);
+      if (ys < p.ny) {
+        if constexpr (JacobiPrefetch<P>::value)
+          jacobi_march_pf<T, V, false, false, false, 4>(u, v, p.nx, p.ny, x0, ys, ye, -1, 0, m);
+        else
+          jacobi_march<T, V, JM_NATIVE, false>(u, v, p.nx, p.ny, x0, ys, ye, -1, m);
+      }
       bits = dbits(m);
     }
   } else {
     T m = T(0);
-    if (ys < p.ny) jacobi_march_pf<T, V, false, false, false, 4>(u, v, p.nx, p.ny, x0, ys, ye, -1, 0, m);
+    if (ys < p.ny) {
+      if constexpr (JacobiPrefetch<P>::value)
+        jacobi_march_pf<T, V, false, false, false, 4>(u, v, p.nx, p.ny, x0, ys, ye, -1, 0, m);
+      else
+        jacobi_march<T, V, JM_NATIVE, false>(u, v, p.nx, p.ny, x0, ys, ye, -1, m);
+    }
     bits = dbits((double)m);
   }
   block_max_to<BX * BY>(bits, resid);
