@@ -246,25 +246,12 @@ JD void jacobi_march(const T* __restrict__ u, T* __restrict__ v, i64 nx, i64 ny,
     cur[e] = cvt_in<T, MODE>(rcur[e], F);
     dn[e] = cvt_in<T, MODE>(rdn[e], F);
   }
-  // lanes 0 and 31 read the column beyond the warp's chunk two rows ahead
-  const bool has_edge = xin && ((lane == 0 && x0 >= 1) || (lane == 31 && x0 + V < nx));
-  const T* ecol = u + (lane == 0 ? x0 - 1 : x0 + V);
-  T e0 = T(0), e1 = T(0);
-  if (has_edge) {
-    e0 = ld1<CG>(ecol + ys * nx);
-    if (ys + 1 < ye) e1 = ld1<CG>(ecol + (ys + 1) * nx);
-  }
   for (i64 y = ys; y < ye; ++y) {
     // x neighbours of the row
     W left = __shfl_up_sync(0xffffffffu, cur[V - 1], 1);
     W right = __shfl_down_sync(0xffffffffu, cur[0], 1);
-    const T edge = e0;
-    e0 = e1;
-    if (has_edge && y + 2 < ye) e1 = ld1<CG>(ecol + (y + 2) * nx);
-    if (has_edge) {
-      if (lane == 0) left = cvt_in<T, MODE>(edge, F);
-      else right = cvt_in<T, MODE>(edge, F);
-    }
+    if (lane == 0 && xin && x0 >= 1) left = cvt_in<T, MODE>(ld1<CG>(u + y * nx + x0 - 1), F);
+    if (lane == 31 && xin && x0 + V < nx) right = cvt_in<T, MODE>(ld1<CG>(u + y * nx + x0 + V), F);
     // prefetch row y+3
     T rnn[V];
 #pragma unroll
@@ -1281,24 +1268,11 @@ JD void jacobi_fx_march(const double* __restrict__ u, double* __restrict__ v, i6
     cur[e] = cvt(rcur[e]);
     dn[e] = cvt(rdn[e]);
   }
-  // lanes 0 and 31 read the column beyond the warp's chunk two rows ahead
-  const bool has_edge = xin && ((lane == 0 && x0 >= 1) || (lane == 31 && x0 + V < nx));
-  const double* ecol = u + (lane == 0 ? x0 - 1 : x0 + V);
-  double e0 = 0.0, e1 = 0.0;
-  if (has_edge) {
-    e0 = ld1<CG>(ecol + ys * nx);
-    if (ys + 1 < ye) e1 = ld1<CG>(ecol + (ys + 1) * nx);
-  }
   for (i64 y = ys; y < ye; ++y) {
     i64 left = __shfl_up_sync(0xffffffffu, cur[V - 1], 1);
     i64 right = __shfl_down_sync(0xffffffffu, cur[0], 1);
-    const double edge = e0;
-    e0 = e1;
-    if (has_edge && y + 2 < ye) e1 = ld1<CG>(ecol + (y + 2) * nx);
-    if (has_edge) {
-      if (lane == 0) left = cvt(edge);
-      else right = cvt(edge);
-    }
+    if (lane == 0 && xin && x0 >= 1) left = cvt(ld1<CG>(u + y * nx + x0 - 1));
+    if (lane == 31 && xin && x0 + V < nx) right = cvt(ld1<CG>(u + y * nx + x0 + V));
     double rnn[V];
 #pragma unroll
     for (int e = 0; e < V; ++e) rnn[e] = 0.0;
