@@ -415,6 +415,30 @@ def secondary(dev):
     out["box27_f32_1024_x100"] = c5
     del a, b
     torch.cuda.empty_cache()
+    # region-driven scheduler: 32 independent 32^3 heat grids x 40 sweeps, one
+    # stream back to back vs spread over 8 streams (no conflicts between them)
+    side, ns, G = 32, 40, 32
+    hosts = [inputs.heat3d_field(side, seed=90 + g) for g in range(G)]
+    k7 = jacc.Kernel(7, 64, side, side, side, coeffs=(0.125,))
+    sb = [(torch.from_numpy(h).to(dev), torch.empty((side,) * 3, dtype=torch.float64, device=dev)) for h in hosts]
+
+    def seq():
+        for u0, u1 in sb:
+            jacc.sweep(k7, u0, u1, ns)
+
+    def sched():
+        sc = jacc.Sched(nstreams=8)
+        for u0, u1 in sb:
+            sc.sweep(k7, u0, u1, ns)
+        sc.join()
+        sc.release()
+
+    out["sched_32_grids_32cubed_x40"] = {"one_stream_ms": _time_ms(seq, reps=3),
+                                          "scheduled_8_streams_ms": _time_ms(sched, reps=3)}
+    out["sched_32_grids_32cubed_x40"]["speedup"] = (out["sched_32_grids_32cubed_x40"]["one_stream_ms"]
+                                                    / out["sched_32_grids_32cubed_x40"]["scheduled_8_streams_ms"])
+    k7.release()
+    del sb
     # variable-coefficient 19-point (Himeno-like) FP32, the paper's XL grid size
     # (512 x 512 x 1024 points, 14 fields = 15 GB), 20 graph-launched sweeps
     nx, ny, nz = 512, 512, 1024

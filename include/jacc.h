@@ -293,6 +293,52 @@ jacc_status jacc_sweep_coeffs(jacc_kernel k, void* u0, void* u1, int32_t nsweeps
 jacc_status jacc_sweep_until(jacc_kernel k, void* u0, void* u1, int32_t max_sweeps, double tol, double* resid_dev,
                              int32_t* status_dev, uintptr_t stream);
 
+/* ------------------------------------------- region-driven async scheduler
+ * The runtime's asynchronous execution (§3.2.1 tracks the data range each
+ * kernel touches; §4 runs kernels without host synchronisation; §6.1 uses 16
+ * queues): a scheduler owns a pool of nstreams CUDA streams (1..64) and runs
+ * each submitted task on one of them after cudaStreamWaitEvent on every
+ * earlier task whose memory ranges conflict with its own (read after write,
+ * write after read, write after write on overlapping bytes); tasks without a
+ * conflict run concurrently.  A task that depends on the last task of a
+ * stream continues that stream; others take the next stream round-robin.
+ * The pool starts after the work queued on `origin` when it is created;
+ * jacc_sched_join makes a stream wait for every task.  Tasks completed on the
+ * device are retired and wait for nothing.  Not thread-safe across
+ * schedulers sharing fields.
+ * JACC_SCHED_DRY_RUN: no CUDA call at all; tasks only record their
+ * dependencies and stream (jacc_sched_task_info), for checking the
+ * dependency logic on a host.  Task ids count from 0 in submission order. */
+#define JACC_SCHED_DRY_RUN 1u
+typedef struct jacc_sched_s* jacc_sched;
+jacc_status jacc_sched_create(int32_t nstreams, uint32_t flags, uintptr_t origin, jacc_sched* out);
+/* A jacc_sweep sequence (graph-launched) as a task: it reads u0 and writes
+ * u1 (nsweeps = 1) or reads and writes both, and writes resid_dev. */
+jacc_status jacc_sched_sweep(jacc_sched s, jacc_kernel k, void* u0, void* u1, int32_t nsweeps, double* resid_dev,
+                             int32_t* task_id);
+/* A device-to-device copy of `bytes` bytes as a task (no overlap). */
+jacc_status jacc_sched_copy(jacc_sched s, void* dst, const void* src, uint64_t bytes, int32_t* task_id);
+/* A task for the caller's own device work, described by its loop nest:
+ * jacc_region_analyze(nloops, loops, nrefs, refs, narrays, arrays) gives each
+ * array's read and written flattened-offset extremes, mapped to bytes through
+ * base[a] (device address of array a's element 0) and elem_bytes[a].  The
+ * caller enqueues the work on *stream_out, then calls jacc_sched_nest_end;
+ * errors of the analysis are returned unchanged. */
+jacc_status jacc_sched_nest_begin(jacc_sched s, int32_t nloops, const jacc_loop* loops, int32_t nrefs,
+                                  const jacc_ref* refs, int32_t narrays, const jacc_array* arrays,
+                                  const uint64_t* base, const int32_t* elem_bytes, int32_t* task_id,
+                                  uintptr_t* stream_out);
+jacc_status jacc_sched_nest_end(jacc_sched s, int32_t task_id);
+/* The tasks task_id waited for (first max_deps of *ndeps, in id order) and
+ * the index of its pool stream.  In live mode a conflicting task that had
+ * already completed on the device when task_id was submitted is not listed
+ * (it needed no wait); dry-run mode lists every conflicting earlier task. */
+jacc_status jacc_sched_task_info(jacc_sched s, int32_t task_id, int32_t* deps, int32_t max_deps, int32_t* ndeps,
+                                 int32_t* stream_index);
+jacc_status jacc_sched_join(jacc_sched s, uintptr_t stream);
+/* Waits for the pool's streams, then frees the scheduler. */
+jacc_status jacc_sched_release(jacc_sched s);
+
 /* ---------------------------------------------------------- autotuner
  * Exhaustive search over the JACC_NUM_TILES tile configurations for one
  * descriptor (the paper names auto-tuning as future work, §8, and cites

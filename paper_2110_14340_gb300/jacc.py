@@ -102,6 +102,14 @@ SIGNATURES = {
     "jacc_sweep": ([P, P, P, C.c_int32, P, C.c_uint32, C.c_size_t, P], C.c_int32),
     "jacc_sweep_until": ([P, P, P, C.c_int32, C.c_double, P, P, C.c_size_t], C.c_int32),
     "jacc_sweep_coeffs": ([P, P, P, C.c_int32, P, C.c_int32, P, C.c_uint32, C.c_size_t, P], C.c_int32),
+    "jacc_sched_create": ([C.c_int32, C.c_uint32, C.c_size_t, P], C.c_int32),
+    "jacc_sched_sweep": ([P, P, P, P, C.c_int32, P, P], C.c_int32),
+    "jacc_sched_copy": ([P, P, P, C.c_uint64, P], C.c_int32),
+    "jacc_sched_nest_begin": ([P, C.c_int32, P, C.c_int32, P, C.c_int32, P, P, P, P, P], C.c_int32),
+    "jacc_sched_nest_end": ([P, C.c_int32], C.c_int32),
+    "jacc_sched_task_info": ([P, C.c_int32, P, C.c_int32, P, P], C.c_int32),
+    "jacc_sched_join": ([P, C.c_size_t], C.c_int32),
+    "jacc_sched_release": ([P], C.c_int32),
     "jacc_shutdown": ([], C.c_int32),
     "jacc_batch_create": ([C.c_int32, P, P, P], C.c_int32),
     "jacc_batch_configure": ([P, P], C.c_int32),
@@ -156,8 +164,9 @@ def version():
 
 # ----------------------------------------------------------------------------- region analysis
 
-def region_analyze(loops, refs, arrays):
-    """Same argument format as the oracle's region_analyze; returns (status, [dict per array])."""
+def _nest(loops, refs, arrays):
+    """ctypes arrays for a loop nest: loops [(lo, hi, step)], refs [dict(array, coef, off, write)],
+    arrays [extents]."""
     L = (Loop * max(1, len(loops)))()
     for k, (lo, hi, st) in enumerate(loops):
         L[k].lo, L[k].hi, L[k].step = lo, hi, st
@@ -176,6 +185,12 @@ def region_analyze(loops, refs, arrays):
         A[a].ndim = len(ext)
         for d, e in enumerate(ext):
             A[a].extent[d] = e
+    return L, R, A
+
+
+def region_analyze(loops, refs, arrays):
+    """Same argument format as the oracle's region_analyze; returns (status, [dict per array])."""
+    L, R, A = _nest(loops, refs, arrays)
     O = (Region * max(1, len(arrays)))()
     st = lib().jacc_region_analyze(len(loops), C.cast(L, P), len(refs), C.cast(R, P), len(arrays), C.cast(A, P),
                                    C.cast(O, P))
@@ -341,6 +356,66 @@ def sweep_until(k, u0, u1, max_sweeps, tol, resid, status, stream=None):
 def shutdown():
     if _lib is not None:
         _check(_lib.jacc_shutdown())
+
+
+# ----------------------------------------------------------------------------- async scheduler
+
+SCHED_DRY_RUN = 1
+
+
+class Sched:
+    """Region-driven asynchronous scheduler over a pool of streams (dry_run: no CUDA call)."""
+
+    def __init__(self, nstreams=8, dry_run=False, origin=None):
+        h = C.c_void_p()
+        _check(lib().jacc_sched_create(int(nstreams), SCHED_DRY_RUN if dry_run else 0,
+                                       0 if dry_run else _stream(origin), C.byref(h)))
+        self.handle = h
+
+    def sweep(self, k, u0, u1, nsweeps, resid=None):
+        t = C.c_int32(-1)
+        _check(lib().jacc_sched_sweep(self.handle, k.handle, _field(k, u0, "u0"), _field(k, u1, "u1"), nsweeps,
+                                      _resid(resid), C.byref(t)))
+        return t.value
+
+    def copy(self, dst, src, nbytes):
+        """dst, src: device addresses (ints) or CUDA tensors."""
+        d = dst.data_ptr() if hasattr(dst, "data_ptr") else int(dst)
+        c = src.data_ptr() if hasattr(src, "data_ptr") else int(src)
+        t = C.c_int32(-1)
+        _check(lib().jacc_sched_copy(self.handle, C.c_void_p(d), C.c_void_p(c), C.c_uint64(int(nbytes)),
+                                     C.byref(t)))
+        return t.value
+
+    def nest_begin(self, loops, refs, arrays, bases, elem_bytes):
+        """A task described by its loop nest; returns (task id, stream handle as int)."""
+        L, R, A = _nest(loops, refs, arrays)
+        B = (C.c_uint64 * max(1, len(arrays)))(*[int(b) for b in bases])
+        E = (C.c_int32 * max(1, len(arrays)))(*[int(e) for e in elem_bytes])
+        t = C.c_int32(-1)
+        st = C.c_size_t(0)
+        _check(lib().jacc_sched_nest_begin(self.handle, len(loops), C.cast(L, P), len(refs), C.cast(R, P),
+                                           len(arrays), C.cast(A, P), C.cast(B, P), C.cast(E, P), C.byref(t),
+                                           C.byref(st)))
+        return t.value, st.value
+
+    def nest_end(self, task):
+        _check(lib().jacc_sched_nest_end(self.handle, int(task)))
+
+    def info(self, task, max_deps=4096):
+        d = (C.c_int32 * max_deps)()
+        n = C.c_int32(0)
+        s = C.c_int32(-1)
+        _check(lib().jacc_sched_task_info(self.handle, int(task), d, max_deps, C.byref(n), C.byref(s)))
+        return list(d[:min(n.value, max_deps)]), s.value
+
+    def join(self, stream=None):
+        _check(lib().jacc_sched_join(self.handle, _stream(stream)))
+
+    def release(self):
+        if self.handle:
+            _check(lib().jacc_sched_release(self.handle))
+            self.handle = None
 
 
 # ----------------------------------------------------------------------------- batched sweeps
