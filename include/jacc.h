@@ -105,6 +105,51 @@ typedef struct {
 jacc_status jacc_region_analyze(int32_t nloops, const jacc_loop* loops, int32_t nrefs, const jacc_ref* refs,
                                 int32_t narrays, const jacc_array* arrays, jacc_region* out /* [narrays] */);
 
+/* Triangular (affine-bounded) nests.  Loop k runs i_k = lo_k, lo_k + 1, ...,
+ * hi_k with lo_k = lo + sum_{m<k} lo_coef[m] i_m and hi_k likewise, so inner
+ * bounds may follow outer indices (j = i .. n-1, k = 0 .. i + j, ...);
+ * lo_coef[m] and hi_coef[m] must be 0 for m >= k.  The result is that of
+ * jacc_region_analyze (exact hulls and flattened-offset extremes over the
+ * iterations that run), computed by eliminating the loops from the innermost
+ * out: the extreme of c i_k over [lo_k, hi_k] is c hi_k or c lo_k, an affine
+ * form in the outer indices (the paper's analysis covers rectangular ranges,
+ * §4.1; this extends it to the nests its future work names).  An empty
+ * outermost loop touches nothing.  JACC_ERR_UNSUPPORTED if some inner loop
+ * is empty for some iteration of its outer loops (the elimination would then
+ * need the loop's emptiness as a constraint); other errors as for
+ * jacc_region_analyze, plus JACC_ERR_OVERFLOW when an eliminated form leaves
+ * int64. */
+typedef struct {
+  int64_t lo, hi;
+  int64_t lo_coef[JACC_MAX_LOOPS];
+  int64_t hi_coef[JACC_MAX_LOOPS];
+} jacc_loop_affine;
+jacc_status jacc_region_analyze_affine(int32_t nloops, const jacc_loop_affine* loops, int32_t nrefs,
+                                       const jacc_ref* refs, int32_t narrays, const jacc_array* arrays,
+                                       jacc_region* out /* [narrays] */);
+
+/* Touched sets as a union of boxes (rectangular nests).  Each reference
+ * contributes the box of its per-dimension hull; boxes of the same array and
+ * access kind that lie inside another are dropped, duplicates kept once.
+ * exact = 1 when the reference's touched set is its whole box: every
+ * subscript depends on at most one loop, with coefficient +-1 and a loop step
+ * of +-1, and no two dimensions depend on the same loop.  When every box of
+ * an array and kind is exact their union is the exact touched set (a 5-point
+ * read set is a cross, not its hull).  At most max_boxes are written; *nboxes
+ * is the number the union has (JACC_ERR_INVALID_ARG if it exceeds max_boxes,
+ * the first max_boxes being written).  Errors otherwise as for
+ * jacc_region_analyze. */
+typedef struct {
+  int32_t array_id;
+  int32_t is_write;
+  int32_t exact;
+  int32_t reserved;
+  int64_t lo[JACC_MAX_DIMS], hi[JACC_MAX_DIMS];
+} jacc_box;
+jacc_status jacc_region_boxes(int32_t nloops, const jacc_loop* loops, int32_t nrefs, const jacc_ref* refs,
+                              int32_t narrays, const jacc_array* arrays, jacc_box* boxes, int32_t max_boxes,
+                              int32_t* nboxes);
+
 /* ---------------------------------------------------------- specialisation
  * A kernel descriptor names one stencil sweep.  jacc_specialize returns a
  * handle to a compiled kernel plus its launch configuration, from a cache

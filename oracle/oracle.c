@@ -84,6 +84,77 @@ static int affine_extremes(int32_t nloops, const i128* first, const i128* last, 
   return ORC_OK;
 }
 
+/* Visit every iteration of an affine-bounded nest, recording each
+ * reference's subscripts and flattened offset. */
+typedef struct {
+  int32_t nloops, nrefs;
+  const orc_loop_affine* loops;
+  const orc_ref* refs;
+  const orc_array* arrays;
+  orc_region* out;
+  int64_t idx[ORC_MAX_LOOPS];
+  int64_t visits;
+} enum_state;
+
+static void enum_touch(enum_state* S) {
+  for (int r = 0; r < S->nrefs; ++r) {
+    const orc_ref* R = &S->refs[r];
+    const orc_array* A = &S->arrays[R->array_id];
+    orc_region* O = &S->out[R->array_id];
+    const int w = R->is_write != 0;
+    int64_t* lo = w ? O->wlo : O->rlo;
+    int64_t* hi = w ? O->whi : O->rhi;
+    int64_t* llo = w ? &O->wlin_lo : &O->rlin_lo;
+    int64_t* lhi = w ? &O->wlin_hi : &O->rlin_hi;
+    int32_t* has = w ? &O->has_write : &O->has_read;
+    int64_t flat = 0;
+    for (int d = 0; d < R->ndim; ++d) {
+      int64_t e = R->off[d];
+      for (int k = 0; k < S->nloops; ++k) e += R->coef[d][k] * S->idx[k];
+      if (!*has || e < lo[d]) lo[d] = e;
+      if (!*has || e > hi[d]) hi[d] = e;
+      flat = flat * (d == 0 ? 1 : A->extent[d]) + e;
+    }
+    if (!*has || flat < *llo) *llo = flat;
+    if (!*has || flat > *lhi) *lhi = flat;
+    *has = 1;
+  }
+}
+
+static void enum_loop(enum_state* S, int k) {
+  if (k == S->nloops) {
+    ++S->visits;
+    enum_touch(S);
+    return;
+  }
+  const orc_loop_affine* L = &S->loops[k];
+  int64_t lo = L->lo, hi = L->hi;
+  for (int m = 0; m < k; ++m) {
+    lo += L->lo_coef[m] * S->idx[m];
+    hi += L->hi_coef[m] * S->idx[m];
+  }
+  for (int64_t i = lo; i <= hi && S->visits < (1 << 22); ++i) {
+    S->idx[k] = i;
+    enum_loop(S, k + 1);
+  }
+}
+
+int orc_region_enumerate_affine(int32_t nloops, const orc_loop_affine* loops, int32_t nrefs, const orc_ref* refs,
+                                int32_t narrays, const orc_array* arrays, orc_region* out) {
+  if (nloops < 0 || nloops > ORC_MAX_LOOPS || nrefs < 0 || narrays < 0) return ORC_ERR_INVALID_ARG;
+  for (int a = 0; a < narrays; ++a) memset(&out[a], 0, sizeof(orc_region));
+  enum_state S;
+  S.nloops = nloops;
+  S.nrefs = nrefs;
+  S.loops = loops;
+  S.refs = refs;
+  S.arrays = arrays;
+  S.out = out;
+  S.visits = 0;
+  enum_loop(&S, 0);
+  return S.visits >= (1 << 22) ? ORC_ERR_INVALID_ARG : ORC_OK;
+}
+
 int orc_region_analyze(int32_t nloops, const orc_loop* loops, int32_t nrefs, const orc_ref* refs,
                        int32_t narrays, const orc_array* arrays, orc_region* out) {
   if (nloops < 0 || nloops > ORC_MAX_LOOPS || nrefs < 0 || narrays < 0) return ORC_ERR_INVALID_ARG;

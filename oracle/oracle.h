@@ -54,6 +54,20 @@ typedef struct {
   int64_t rlin_lo, rlin_hi, wlin_lo, wlin_hi;
 } orc_region;
 
+/* A loop with affine bounds: i_k = lo_k .. hi_k step 1, lo_k = lo + sum_{m<k}
+ * lo_coef[m] i_m, hi_k likewise (the layout of jacc_loop_affine). */
+typedef struct {
+  int64_t lo, hi;
+  int64_t lo_coef[ORC_MAX_LOOPS];
+  int64_t hi_coef[ORC_MAX_LOOPS];
+} orc_loop_affine;
+
+/* Region of an affine-bounded nest by enumerating every iteration (small
+ * nests only: at most 2^22 iterations, else ORC_ERR_INVALID_ARG).  Same
+ * output as orc_region_analyze; no bounds check. */
+int orc_region_enumerate_affine(int32_t nloops, const orc_loop_affine* loops, int32_t nrefs, const orc_ref* refs,
+                                int32_t narrays, const orc_array* arrays, orc_region* out);
+
 int orc_region_analyze(int32_t nloops, const orc_loop* loops, int32_t nrefs, const orc_ref* refs,
                        int32_t narrays, const orc_array* arrays, orc_region* out);
 

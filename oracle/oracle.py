@@ -30,6 +30,11 @@ class Array(C.Structure):
     _fields_ = [("ndim", C.c_int32), ("pad_", C.c_int32), ("extent", C.c_int64 * MAX_DIMS)]
 
 
+class LoopAffine(C.Structure):
+    _fields_ = [("lo", C.c_int64), ("hi", C.c_int64), ("lo_coef", C.c_int64 * MAX_LOOPS),
+                ("hi_coef", C.c_int64 * MAX_LOOPS)]
+
+
 class Region(C.Structure):
     _fields_ = [("has_read", C.c_int32), ("has_write", C.c_int32),
                 ("rlo", C.c_int64 * MAX_DIMS), ("rhi", C.c_int64 * MAX_DIMS),
@@ -64,6 +69,8 @@ def lib():
         L.orc_box27_sweep_f64.argtypes = [C.c_int64, C.c_int64, C.c_int64, P, P, P]
         L.orc_box27_run_f64.restype = C.c_int
         L.orc_box27_run_f64.argtypes = [C.c_int64, C.c_int64, C.c_int64, P, P, P, C.c_int32, P]
+        L.orc_region_enumerate_affine.restype = C.c_int
+        L.orc_region_enumerate_affine.argtypes = [C.c_int32, P, C.c_int32, P, C.c_int32, P, P]
         L.orc_var19_sweep.restype = C.c_double
         L.orc_var19_sweep.argtypes = [C.c_int64, C.c_int64, C.c_int64, C.c_float, P, P, P]
         L.orc_var19_run.restype = C.c_int
@@ -140,6 +147,33 @@ def region_analyze(loops, refs, arrays):
                         rlo=list(o.rlo[:nd]), rhi=list(o.rhi[:nd]), wlo=list(o.wlo[:nd]), whi=list(o.whi[:nd]),
                         rlin=(o.rlin_lo, o.rlin_hi), wlin=(o.wlin_lo, o.wlin_hi)))
     return st, out
+
+
+def _regions(O, arrays):
+    out = []
+    for a, ext in enumerate(arrays):
+        nd = len(ext)
+        o = O[a]
+        out.append(dict(has_read=bool(o.has_read), has_write=bool(o.has_write),
+                        rlo=list(o.rlo[:nd]), rhi=list(o.rhi[:nd]), wlo=list(o.wlo[:nd]), whi=list(o.whi[:nd]),
+                        rlin=(o.rlin_lo, o.rlin_hi), wlin=(o.wlin_lo, o.wlin_hi)))
+    return out
+
+
+def region_enumerate_affine(loops, refs, arrays):
+    """Affine-bounded nest by enumeration.  loops: [(lo, hi, lo_coef[], hi_coef[])] (step 1)."""
+    L = (LoopAffine * max(1, len(loops)))()
+    for k, (lo, hi, lc, hc) in enumerate(loops):
+        L[k].lo, L[k].hi = lo, hi
+        for m, c in enumerate(lc):
+            L[k].lo_coef[m] = c
+        for m, c in enumerate(hc):
+            L[k].hi_coef[m] = c
+    _, R, A = make_nest([(0, 0, 1)] * len(loops), refs, arrays)
+    O = (Region * max(1, len(arrays)))()
+    st = lib().orc_region_enumerate_affine(len(loops), C.cast(L, C.c_void_p), len(refs), C.cast(R, C.c_void_p),
+                                           len(arrays), C.cast(A, C.c_void_p), C.cast(O, C.c_void_p))
+    return st, _regions(O, arrays)
 
 
 # ----------------------------------------------------------------------------- stencils

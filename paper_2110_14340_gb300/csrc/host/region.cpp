@@ -8,6 +8,8 @@
 // the iteration domain are the sums of per-loop extremes, and each per-loop
 // extreme sits at the loop's first or last iterate.
 #include <cstring>
+#include <string>
+#include <vector>
 
 #include "jacc_internal.h"
 
@@ -158,5 +160,220 @@ extern "C" jacc_status jacc_region_analyze(int32_t nloops, const jacc_loop* loop
         return fail(JACC_ERR_OUT_OF_BOUNDS, "touched region leaves array " + std::to_string(a));
     }
   }
+  return jacc::ok();
+}
+
+namespace {
+
+// Shared checks of references and arrays (jacc_region_analyze's rules).
+jacc_status check_refs(int32_t nrefs, const jacc_ref* refs, int32_t narrays, const jacc_array* arrays) {
+  using jacc::fail;
+  for (int a = 0; a < narrays; ++a) {
+    if (arrays[a].ndim < 1 || arrays[a].ndim > JACC_MAX_DIMS)
+      return fail(JACC_ERR_INVALID_ARG, "array ndim outside [1, JACC_MAX_DIMS]");
+    for (int d = 0; d < arrays[a].ndim; ++d)
+      if (arrays[a].extent[d] < 0) return fail(JACC_ERR_INVALID_ARG, "negative extent");
+  }
+  for (int r = 0; r < nrefs; ++r) {
+    if (refs[r].array_id < 0 || refs[r].array_id >= narrays)
+      return fail(JACC_ERR_INVALID_ARG, "reference array_id out of range");
+    if (refs[r].ndim != arrays[refs[r].array_id].ndim)
+      return fail(JACC_ERR_INVALID_ARG, "reference ndim differs from its array");
+  }
+  return jacc::ok();
+}
+
+// The flattened row-major offset of a reference as an affine form.
+bool flatten(const jacc_ref& R, const jacc_array& A, int nloops, wide* fc, wide* foff) {
+  const int nd = R.ndim;
+  wide stride = 1;
+  for (int k = 0; k < nloops; ++k) fc[k] = 0;
+  *foff = 0;
+  for (int d = nd - 1; d >= 0; --d) {
+    if (d < nd - 1) {
+      stride *= A.extent[d + 1];
+      if (!in64(stride)) return false;
+    }
+    for (int k = 0; k < nloops; ++k) {
+      const wide t = stride * R.coef[d][k];
+      if (!in64(t)) return false;
+      fc[k] += t;
+      if (!in64(fc[k])) return false;
+    }
+    const wide t = stride * R.off[d];
+    if (!in64(t)) return false;
+    *foff += t;
+    if (!in64(*foff)) return false;
+  }
+  return true;
+}
+
+// Max (want_max) or min of off + sum_k c[k] i_k over an affine nest whose
+// loops never run empty: eliminate the loops from the innermost out, the
+// extreme of c i_k over [lo_k, hi_k] being c at hi_k or lo_k, an affine form
+// in the outer indices.  False when a coefficient or constant leaves int64.
+bool affine_extreme(const jacc_loop_affine* L, int n, const wide* c_in, wide off, bool want_max, wide* out) {
+  wide c[JACC_MAX_LOOPS];
+  for (int k = 0; k < n; ++k) c[k] = c_in[k];
+  wide k0 = off;
+  for (int k = n - 1; k >= 0; --k) {
+    const wide a = c[k];
+    if (a == 0) continue;
+    const bool use_hi = (a > 0) == want_max;
+    const int64_t base = use_hi ? L[k].hi : L[k].lo;
+    const int64_t* bc = use_hi ? L[k].hi_coef : L[k].lo_coef;
+    k0 += a * base;
+    if (!in64(k0)) return false;
+    for (int m = 0; m < k; ++m) {
+      c[m] += a * bc[m];
+      if (!in64(c[m])) return false;
+    }
+    c[k] = 0;
+  }
+  *out = k0;
+  return true;
+}
+
+jacc_status bounds_check(const jacc_region* out, int32_t narrays, const jacc_array* arrays) {
+  for (int a = 0; a < narrays; ++a) {
+    const jacc_region& O = out[a];
+    for (int d = 0; d < arrays[a].ndim; ++d) {
+      const int64_t last = arrays[a].extent[d] - 1;
+      if ((O.has_read && (O.rlo[d] < 0 || O.rhi[d] > last)) || (O.has_write && (O.wlo[d] < 0 || O.whi[d] > last)))
+        return jacc::fail(JACC_ERR_OUT_OF_BOUNDS, "touched region leaves array " + std::to_string(a));
+    }
+  }
+  return jacc::ok();
+}
+
+}  // namespace
+
+extern "C" jacc_status jacc_region_analyze_affine(int32_t nloops, const jacc_loop_affine* loops, int32_t nrefs,
+                                                  const jacc_ref* refs, int32_t narrays, const jacc_array* arrays,
+                                                  jacc_region* out) {
+  using jacc::fail;
+  if (nloops < 0 || nloops > JACC_MAX_LOOPS) return fail(JACC_ERR_INVALID_ARG, "nloops outside [0, JACC_MAX_LOOPS]");
+  if (nrefs < 0 || narrays < 0) return fail(JACC_ERR_INVALID_ARG, "negative reference or array count");
+  if ((nloops && !loops) || (nrefs && !refs) || (narrays && (!arrays || !out)))
+    return fail(JACC_ERR_INVALID_ARG, "NULL array with a non-zero count");
+  for (int k = 0; k < nloops; ++k)
+    for (int m = k; m < JACC_MAX_LOOPS; ++m)
+      if (loops[k].lo_coef[m] || loops[k].hi_coef[m])
+        return fail(JACC_ERR_INVALID_ARG, "a loop bound may depend only on outer loops");
+  jacc_status st = check_refs(nrefs, refs, narrays, arrays);
+  if (st) return st;
+  std::memset(out, 0, sizeof(jacc_region) * static_cast<size_t>(narrays));
+  if (nloops > 0 && loops[0].hi < loops[0].lo) return jacc::ok();  // the nest never runs
+  // every inner loop must run for every iteration of its outer loops
+  for (int k = 1; k < nloops; ++k) {
+    wide d[JACC_MAX_LOOPS];
+    for (int m = 0; m < k; ++m) d[m] = static_cast<wide>(loops[k].hi_coef[m]) - loops[k].lo_coef[m];
+    wide mn;
+    if (!affine_extreme(loops, k, d, static_cast<wide>(loops[k].hi) - loops[k].lo, false, &mn))
+      return fail(JACC_ERR_OVERFLOW, "loop extent bound overflows int64");
+    if (mn < 0)
+      return fail(JACC_ERR_UNSUPPORTED, "loop " + std::to_string(k) + " is empty for some outer iterations");
+  }
+  for (int r = 0; r < nrefs; ++r) {
+    const jacc_ref& R = refs[r];
+    const jacc_array& A = arrays[R.array_id];
+    const int nd = R.ndim;
+    int64_t lo[JACC_MAX_DIMS], hi[JACC_MAX_DIMS];
+    for (int d = 0; d < nd; ++d) {
+      wide c[JACC_MAX_LOOPS];
+      for (int k = 0; k < nloops; ++k) c[k] = R.coef[d][k];
+      wide a, b;
+      if (!affine_extreme(loops, nloops, c, R.off[d], false, &a) || !affine_extreme(loops, nloops, c, R.off[d], true, &b))
+        return fail(JACC_ERR_OVERFLOW, "subscript bound overflows int64");
+      lo[d] = static_cast<int64_t>(a);
+      hi[d] = static_cast<int64_t>(b);
+    }
+    wide fc[JACC_MAX_LOOPS], foff, fa, fb;
+    if (!flatten(R, A, nloops, fc, &foff) || !affine_extreme(loops, nloops, fc, foff, false, &fa) ||
+        !affine_extreme(loops, nloops, fc, foff, true, &fb))
+      return fail(JACC_ERR_OVERFLOW, "flattened bound overflows int64");
+    jacc_region& O = out[R.array_id];
+    if (R.is_write) {
+      widen(&O.has_write, O.wlo, O.whi, nd, lo, hi);
+      if (!O.has_write || fa < O.wlin_lo) O.wlin_lo = static_cast<int64_t>(fa);
+      if (!O.has_write || fb > O.wlin_hi) O.wlin_hi = static_cast<int64_t>(fb);
+      O.has_write = 1;
+    } else {
+      widen(&O.has_read, O.rlo, O.rhi, nd, lo, hi);
+      if (!O.has_read || fa < O.rlin_lo) O.rlin_lo = static_cast<int64_t>(fa);
+      if (!O.has_read || fb > O.rlin_hi) O.rlin_hi = static_cast<int64_t>(fb);
+      O.has_read = 1;
+    }
+  }
+  return bounds_check(out, narrays, arrays);
+}
+
+extern "C" jacc_status jacc_region_boxes(int32_t nloops, const jacc_loop* loops, int32_t nrefs, const jacc_ref* refs,
+                                         int32_t narrays, const jacc_array* arrays, jacc_box* boxes, int32_t max_boxes,
+                                         int32_t* nboxes) {
+  using jacc::fail;
+  if (!nboxes || max_boxes < 0 || (max_boxes > 0 && !boxes)) return fail(JACC_ERR_INVALID_ARG, "NULL output");
+  if (nloops < 0 || nloops > JACC_MAX_LOOPS) return fail(JACC_ERR_INVALID_ARG, "nloops outside [0, JACC_MAX_LOOPS]");
+  if (nrefs < 0 || narrays < 0) return fail(JACC_ERR_INVALID_ARG, "negative reference or array count");
+  if ((nloops && !loops) || (nrefs && !refs) || (narrays && !arrays))
+    return fail(JACC_ERR_INVALID_ARG, "NULL array with a non-zero count");
+  for (int k = 0; k < nloops; ++k)
+    if (loops[k].step == 0) return fail(JACC_ERR_INVALID_ARG, "loop step 0");
+  jacc_status st = check_refs(nrefs, refs, narrays, arrays);
+  if (st) return st;
+  *nboxes = 0;
+  Span sp[JACC_MAX_LOOPS];
+  for (int k = 0; k < nloops; ++k) {
+    sp[k] = span_of(loops[k]);
+    if (sp[k].empty) return jacc::ok();
+  }
+  std::vector<jacc_box> all;
+  for (int r = 0; r < nrefs; ++r) {
+    const jacc_ref& R = refs[r];
+    jacc_box b{};
+    b.array_id = R.array_id;
+    b.is_write = R.is_write ? 1 : 0;
+    bool exact = true;
+    unsigned used = 0;  // loops a subscript of this reference depends on
+    for (int d = 0; d < R.ndim; ++d) {
+      if (!extremes(sp, nloops, R.coef[d], R.off[d], &b.lo[d], &b.hi[d]))
+        return fail(JACC_ERR_OVERFLOW, "subscript bound overflows int64");
+      int nz = 0, kk = -1;
+      for (int k = 0; k < nloops; ++k)
+        if (R.coef[d][k]) {
+          ++nz;
+          kk = k;
+        }
+      if (nz > 1) exact = false;
+      if (nz == 1) {
+        const int64_t c = R.coef[d][kk];
+        if ((c != 1 && c != -1) || (loops[kk].step != 1 && loops[kk].step != -1) || (used >> kk & 1u)) exact = false;
+        used |= 1u << kk;
+      }
+      const int64_t last = arrays[R.array_id].extent[d] - 1;
+      if (b.lo[d] < 0 || b.hi[d] > last)
+        return fail(JACC_ERR_OUT_OF_BOUNDS, "touched region leaves array " + std::to_string(R.array_id));
+    }
+    b.exact = exact ? 1 : 0;
+    all.push_back(b);
+  }
+  // drop boxes inside another box of the same array and kind (keep the first of equals)
+  auto inside = [&](const jacc_box& a, const jacc_box& b) {
+    for (int d = 0; d < arrays[a.array_id].ndim; ++d)
+      if (a.lo[d] < b.lo[d] || a.hi[d] > b.hi[d]) return false;
+    return true;
+  };
+  std::vector<jacc_box> keep;
+  for (size_t i = 0; i < all.size(); ++i) {
+    bool drop = false;
+    for (size_t j = 0; j < all.size() && !drop; ++j) {
+      if (i == j || all[i].array_id != all[j].array_id || all[i].is_write != all[j].is_write) continue;
+      if (inside(all[i], all[j]) && (!inside(all[j], all[i]) || j < i)) drop = true;
+    }
+    if (!drop) keep.push_back(all[i]);
+  }
+  *nboxes = static_cast<int32_t>(keep.size());
+  for (int32_t i = 0; i < *nboxes && i < max_boxes; ++i) boxes[i] = keep[static_cast<size_t>(i)];
+  if (*nboxes > max_boxes) return fail(JACC_ERR_INVALID_ARG, "more boxes than max_boxes");
   return jacc::ok();
 }

@@ -81,6 +81,16 @@ class TuneResult(C.Structure):
                 ("reserved", C.c_int32), ("best_ms", C.c_double)]
 
 
+class LoopAffine(C.Structure):
+    _fields_ = [("lo", C.c_int64), ("hi", C.c_int64), ("lo_coef", C.c_int64 * MAX_LOOPS),
+                ("hi_coef", C.c_int64 * MAX_LOOPS)]
+
+
+class Box(C.Structure):
+    _fields_ = [("array_id", C.c_int32), ("is_write", C.c_int32), ("exact", C.c_int32), ("reserved", C.c_int32),
+                ("lo", C.c_int64 * MAX_DIMS), ("hi", C.c_int64 * MAX_DIMS)]
+
+
 class Tile(C.Structure):
     _fields_ = [("bx", C.c_int32), ("by", C.c_int32), ("vec16", C.c_int32), ("zc", C.c_int32)]
 
@@ -91,6 +101,8 @@ SIGNATURES = {
     "jacc_last_error": ([], C.c_char_p),
     "jacc_version": ([], C.c_char_p),
     "jacc_region_analyze": ([C.c_int32, P, C.c_int32, P, C.c_int32, P, P], C.c_int32),
+    "jacc_region_analyze_affine": ([C.c_int32, P, C.c_int32, P, C.c_int32, P, P], C.c_int32),
+    "jacc_region_boxes": ([C.c_int32, P, C.c_int32, P, C.c_int32, P, P, C.c_int32, P], C.c_int32),
     "jacc_specialize": ([P, P], C.c_int32),
     "jacc_kernel_info": ([P, P], C.c_int32),
     "jacc_release": ([P], C.c_int32),
@@ -201,6 +213,49 @@ def region_analyze(loops, refs, arrays):
         out.append(dict(has_read=bool(o.has_read), has_write=bool(o.has_write),
                         rlo=list(o.rlo[:nd]), rhi=list(o.rhi[:nd]), wlo=list(o.wlo[:nd]), whi=list(o.whi[:nd]),
                         rlin=(o.rlin_lo, o.rlin_hi), wlin=(o.wlin_lo, o.wlin_hi)))
+    return st, out
+
+
+def _region_list(O, arrays):
+    out = []
+    for a, ext in enumerate(arrays):
+        nd = len(ext)
+        o = O[a]
+        out.append(dict(has_read=bool(o.has_read), has_write=bool(o.has_write),
+                        rlo=list(o.rlo[:nd]), rhi=list(o.rhi[:nd]), wlo=list(o.wlo[:nd]), whi=list(o.whi[:nd]),
+                        rlin=(o.rlin_lo, o.rlin_hi), wlin=(o.wlin_lo, o.wlin_hi)))
+    return out
+
+
+def region_analyze_affine(loops, refs, arrays):
+    """Triangular nests: loops [(lo, hi, lo_coef[], hi_coef[])], step 1; returns (status, [dict per array])."""
+    L = (LoopAffine * max(1, len(loops)))()
+    for k, (lo, hi, lc, hc) in enumerate(loops):
+        L[k].lo, L[k].hi = lo, hi
+        for m, c in enumerate(lc):
+            L[k].lo_coef[m] = c
+        for m, c in enumerate(hc):
+            L[k].hi_coef[m] = c
+    _, R, A = _nest([(0, 0, 1)] * len(loops), refs, arrays)
+    O = (Region * max(1, len(arrays)))()
+    st = lib().jacc_region_analyze_affine(len(loops), C.cast(L, P), len(refs), C.cast(R, P), len(arrays),
+                                          C.cast(A, P), C.cast(O, P))
+    return st, _region_list(O, arrays)
+
+
+def region_boxes(loops, refs, arrays, max_boxes=256):
+    """Touched sets as a union of boxes; returns (status, [dict(array, write, exact, lo, hi)])."""
+    L, R, A = _nest(loops, refs, arrays)
+    B = (Box * max(1, max_boxes))()
+    n = C.c_int32(0)
+    st = lib().jacc_region_boxes(len(loops), C.cast(L, P), len(refs), C.cast(R, P), len(arrays), C.cast(A, P),
+                                 C.cast(B, P), max_boxes, C.byref(n))
+    out = []
+    for i in range(min(n.value, max_boxes)):
+        b = B[i]
+        nd = len(arrays[b.array_id])
+        out.append(dict(array=b.array_id, write=bool(b.is_write), exact=bool(b.exact), lo=list(b.lo[:nd]),
+                        hi=list(b.hi[:nd])))
     return st, out
 
 
