@@ -470,7 +470,20 @@ cudaError_t launch_sweep_kernel(const Kernel& k, const void* u, void* v, double*
                                 cudaStream_t s) {
   JParams p = k.params;
   const void* args[] = {&u, &v, &p, &resid, &maxword, &flags};
-  return cudaLaunchKernel((flags & (kFxIn | kFxOut)) ? k.func_out : k.func, k.grid, k.block, const_cast<void**>(args), 0, s);
+  // programmatic dependent launch: the kernel may start while the previous
+  // sweep finishes; every sweep kernel waits (griddepcontrol.wait) for the
+  // previous grid before it touches a field
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = k.grid;
+  cfg.blockDim = k.block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, (flags & (kFxIn | kFxOut)) ? k.func_out : k.func, const_cast<void**>(args));
 }
 
 jacc_status check_buffers(const Kernel& k, const void* a, const void* b) {

@@ -205,6 +205,13 @@ template <int NT> JD void block_sum_to(double s, double* out) {
 }
 
 JD u64 dbits(double d) { return (u64)__double_as_longlong(d); }
+
+// Programmatic dependent launch: a sweep kernel may be launched while the
+// previous one still runs (its CTAs fill the SMs the previous grid frees);
+// this waits until the previous grid has completed and its memory is
+// visible, before the kernel touches any field.  A no-op when the launch
+// did not ask for programmatic serialisation.
+JD void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 JD double fabs_bits_free(double d) { return __longlong_as_double(__double_as_longlong(d) & 0x7fffffffffffffffLL); }
 
 // FP32 error-free sum (Knuth TwoSum) accumulated as hi + lo.
@@ -1177,6 +1184,7 @@ JD void box27_tb_body(const float* __restrict__ u, float* __restrict__ v, const 
 
 template <int RY, int TT, int ZC, class P>
 JD void box27_tb_entry(const float* __restrict__ u, float* __restrict__ v, const P& p, double* resid) {
+  griddep_wait();
   __shared__ TbPlane<RY> sm[TT];
   SumAcc<float> acc;
   box27_tb_body<RY, TT, ZC>(u, v, p, acc, resid != nullptr, sm);
@@ -2046,6 +2054,7 @@ template <class P> struct JacobiPrefetch { static constexpr bool value = false; 
 template <class T, int BX, int BY, int V, int ZC, bool EDGE, class P>
 JD void jacobi2d_entry(const T* __restrict__ u, T* __restrict__ v, const P& p, const JParams& rt, double* resid,
                        const u64* maxword, int flags) {
+  griddep_wait();
   u64 bits = 0;
   const i64 x0 = (i64)blockIdx.x * (BX * V) + (i64)threadIdx.x * V;
   const i64 ys = ((i64)blockIdx.y * BY + threadIdx.y) * ZC;
@@ -2087,6 +2096,7 @@ JD void jacobi2d_entry(const T* __restrict__ u, T* __restrict__ v, const P& p, c
 template <class T, int BX, int BY, int V, int ZC, bool EDGE, class P>
 JD void heat3d_entry(const T* __restrict__ u, T* __restrict__ v, const P& p, const JParams& rt, double* resid,
                      const u64* maxword, int flags) {
+  griddep_wait();
   u64 bits = 0;
   if constexpr (sizeof(T) == 8) {
     // 16-byte columns: the staged kernel (2 rows per thread, so a CTA covers
@@ -2129,6 +2139,7 @@ JD void heat3d_entry(const T* __restrict__ u, T* __restrict__ v, const P& p, con
 template <class T, int BX, int BY, int V, int ZC, bool EDGE, class P>
 JD void box27_entry(const T* __restrict__ u, T* __restrict__ v, const P& p, const JParams& rt, double* resid,
                     const u64* maxword, int flags) {
+  griddep_wait();
   double total = 0.0;
   if constexpr (sizeof(T) == 8) {
     const int F = (maxword && p.fpath != JACC_FP_NONE) ? fx_frac_bits(*maxword) : -1;
@@ -2158,6 +2169,7 @@ JD void box27_entry(const T* __restrict__ u, T* __restrict__ v, const P& p, cons
 // Pre-pass: atomicMax of the bit pattern of |u[i]| over n doubles.
 // Any NaN orders above +Inf, so a NaN input selects the native path.
 __global__ void __launch_bounds__(256) jacc_k_maxabs(const double* __restrict__ u, i64 n, u64* maxword) {
+  griddep_wait();
   u64 m = 0;
   const i64 stride = (i64)gridDim.x * blockDim.x;
   const i64 n2 = n / 2;
