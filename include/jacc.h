@@ -413,10 +413,8 @@ jacc_status jacc_autotune_forget(void);
  * the features of (stencil, side, dtype, tile) to the natural log of the sweep
  * time in microseconds.  No counterpart in the paper.  Features
  * (jacc_costmodel_features): [points / 27, log2(side) / 10, dtype bits / 64,
- * rank / 23], side = the grid side (square root of the area for 2D, cube
- * root of the volume for 3D), rank = 12 vec16 + 6 long_march + shape: the
- * tile in an order that keeps tiles of the same vector width and march
- * length adjacent (tile_id = 4 shape + 2 long_march + vec16).
+ * tile / 23], side = the grid side (square root of the area for 2D, cube
+ * root of the volume for 3D).
  *
  * create      : parameters from `init_params` (host, 8705 floats) or, if
  *               NULL, Kaiming-uniform from `seed`; Adam state zeroed.

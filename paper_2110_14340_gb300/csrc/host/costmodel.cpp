@@ -101,11 +101,7 @@ extern "C" jacc_status jacc_costmodel_features(int32_t stencil, double side, int
   out4[0] = static_cast<float>(stencil / 27.0);
   out4[1] = static_cast<float>(std::log2(side) / 10.0);
   out4[2] = static_cast<float>(dtype / 64.0);
-  // the tile as one number, in an order that keeps similar tiles adjacent:
-  // vector width, then march length, then thread shape (the tile id itself,
-  // 4 * shape + 2 * march + vec, alternates vector and scalar tiles)
-  const int shape = tile / 4, march = (tile / 2) % 2, vec = tile % 2;
-  out4[3] = static_cast<float>((vec * 12 + march * 6 + shape) / 23.0);
+  out4[3] = static_cast<float>(tile / 23.0);
   return ok();
 }
 
