@@ -34,9 +34,9 @@ def set_size(n, sweeps):
     WORKLOAD = f"heat3d 7-point FP64 {n}^3, r=0.125, zero Dirichlet, {sweeps} sweeps per CUDA graph"
 BYTES_PER_LUP = 16  # one FP64 read + one FP64 write per interior point
 # DRAM bytes (read + write) per update of the intermediate-sweep kernel, from
-# an ncu capture of the same kernel on a 384^3 grid (875.4 MB for 382^3
+# an ncu capture of the same kernel on a 384^3 grid (875.2 MB for 382^3
 # updates); scaled to a launch by its updates.
-DRAM_BYTES_PER_LUP = 15.71
+DRAM_BYTES_PER_LUP = 15.70
 METRIC = "stencil GLUP/s"
 WORKLOAD = "heat3d 7-point FP64 512^3, r=0.125, zero Dirichlet, 200 sweeps per CUDA graph"
 
@@ -252,7 +252,7 @@ def run_gpu(args):
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": args.traffic if args.traffic is not None else DRAM_BYTES_PER_LUP * LUP_PER_SWEEP,
             "traffic_source": "command line" if args.traffic is not None else
-            "ncu dram read+write bytes of a 382^3 launch of the same kernel, 15.71 B per update, x updates per launch",
+            "ncu dram read+write bytes of a 382^3 launch of the same kernel, 15.70 B per update, x updates per launch",
             "peak_kind": peak_kind,
             "per_unit": f"16 B per interior point per sweep (8 B read + 8 B write), {N - 2}^3 points per launch"}
 
@@ -466,6 +466,20 @@ def profile_case(args):
     from paper_2110_14340_gb300 import build, inputs, jacc
     build.build()
     n = args.n
+    if args.profile_case == "jacobi2d":
+        u = inputs.jacobi2d_field(n, n, seed=1)
+        a = torch.from_numpy(u).to("cuda")
+        b = torch.empty_like(a)
+        k = jacc.Kernel(5, 64, n, n, 1, tile_id=args.tile, jit=True)
+        kc = jacc.Kernel(5, 64, n, n, 1, cluster=True)
+        res = torch.zeros(args.sweeps, dtype=torch.float64, device="cuda")
+        for _ in range(args.warmup + args.steps):
+            jacc.sweep(k, a, b, args.sweeps, res)
+            jacc.sweep(kc, a, b, args.sweeps, res)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": args.profile_case, "n": n, "sweeps": args.sweeps,
+                          "runs": args.warmup + args.steps, "tile": k.info()["tile_id"]}))
+        return
     if args.profile_case == "var19":
         p, fields = inputs.var19_problem_torch(n, n, n, "cuda", seed=7)
         q = torch.empty_like(p)
@@ -500,8 +514,8 @@ def main():
     ap.add_argument("--no-jit", action="store_true", help="use the precompiled kernel instead of the NVRTC variant")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner; use the library's default tile")
     ap.add_argument("--no-secondary", action="store_true", help="skip the other workloads' measurements")
-    ap.add_argument("--profile-case", choices=["box27", "box27-tb2", "var19"], default=None,
-                    help="run only a 27-point FP32 (or 19-point variable-coefficient) sweep sequence on an --n cube (for profilers) and exit")
+    ap.add_argument("--profile-case", choices=["box27", "box27-tb2", "var19", "jacobi2d"], default=None,
+                    help="run only one sweep sequence (27-point FP32 or 19-point on an --n cube; jacobi2d: 5-point FP64 --n squared, graph and cluster launch) for profilers, and exit")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the sweep kernel, if captured for this build")
     ap.add_argument("--no-cpu-baseline", action="store_true")

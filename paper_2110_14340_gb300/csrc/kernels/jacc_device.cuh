@@ -492,6 +492,17 @@ JD void heat3d_body(const T* __restrict__ u, T* __restrict__ v, const P& p, int 
 }
 
 // Residual of the heat sweep from max |L|: r max|L| scaled.
+// r = fb 2^-k with 1 <= k <= 4 and fb <= 2 (r = 1/8, 1/16, ...): the staged
+// fixed-point heat kernels form v 2^F directly as
+// (fb S + (2^k - 6 fb) c + 2^(k-1)) >> k, which equals c + round(r L 2^F) bit
+// for bit (2^k c is a multiple of 2^k), and take the residual from v - c in
+// every sweep of a sequence (converting or not), so residuals do not depend on
+// which kernel ran a sweep.  Every term stays below 2^62 for |c| < 2^57 and
+// |S| < 6 * 2^57.
+template <class P> JD bool heat_fold(const P& p) {
+  return p.fpath == JACC_FP_SMALL && p.fk >= 1 && p.fk <= 4 && p.fb >= 1 && p.fb <= 2;
+}
+
 template <class P> JD double heat_resid_fixed(const P& p, u64 maxL, int F) {
   const u64 m = (p.fpath == JACC_FP_SMALL) ? (u64)p.fb : (u64)p.fw0;
   return fx128_to(mul_s64_u64((i64)maxL, m), F + p.fk);
@@ -1819,6 +1830,7 @@ JD void heat3s_body(const T* __restrict__ u, T* __restrict__ v, const P& p, cons
   const i64 fb = p.fb, fw0 = p.fw0;
   const int k = p.fk;
   const bool small = p.fpath == JACC_FP_SMALL;
+  const bool fold = heat_fold(p);
   vo += z0 * sz;
   // one output plane (staged plane j, 1 <= j <= L-2) from the own values of
   // planes j-1 (zp) and j (cur); fills zn with those of plane j+1
@@ -1866,18 +1878,27 @@ JD void heat3s_body(const T* __restrict__ u, T* __restrict__ v, const P& p, cons
         const Wt sum = ((a + b) + (c + d)) + (zp[yy][e] + zn[yy][e]);
         const Wt ce = cur[yy][e];
         if constexpr (FX) {
-          const i64 Ld = sum - 6 * ce;
           double o;
-          if (outf) {
-            if (small) o = fx_to(ce * ((i64)1 << k) + fb * Ld, F + k);
-            else o = fx128_to(add128(from_s64_shl(ce, k), mul_s64_u64(Ld, (u64)fw0)), F + k);
+          u64 aL;
+          if (fold) {
+            const i64 vn = (fb * sum + ((((i64)1 << k) - 6 * fb) * ce + ((i64)1 << (k - 1)))) >> k;
+            const i64 dv = vn - ce;
+            aL = (u64)(dv ^ (dv >> 63));  // |v - c| (one less if negative)
+            if (outf) o = fx_to(ce * ((i64)1 << k) + fb * (sum - 6 * ce), F + k);
+            else o = i64_bits(vn);
           } else {
-            if (small) o = i64_bits(ce + fx_round_shift(fb * Ld, k));
-            else o = i64_bits(ce + fx128_round_shift(mul_s64_u64(Ld, (u64)fw0), k));
+            const i64 Ld = sum - 6 * ce;
+            if (outf) {
+              if (small) o = fx_to(ce * ((i64)1 << k) + fb * Ld, F + k);
+              else o = fx128_to(add128(from_s64_shl(ce, k), mul_s64_u64(Ld, (u64)fw0)), F + k);
+            } else {
+              if (small) o = i64_bits(ce + fx_round_shift(fb * Ld, k));
+              else o = i64_bits(ce + fx128_round_shift(mul_s64_u64(Ld, (u64)fw0), k));
+            }
+            aL = (u64)(Ld ^ (Ld >> 63));
           }
           if constexpr (RAW) out[e] = in ? o : bnd_out(rcur[yy][e]);
           else out[e] = in ? o : as_out(ce);
-          const u64 aL = (u64)(Ld ^ (Ld >> 63));
           rmax = (in && aL > rmax) ? aL : rmax;
         } else {
           const T o = ce + r * (sum - T(6) * ce);
@@ -2113,7 +2134,8 @@ JD void heat3d_entry(const T* __restrict__ u, T* __restrict__ v, const P& p, con
                                                     *reinterpret_cast<Heat3SSmem<double, BX, BY>*>(raw));
       else
         heat3d_fx_body<EDGE, BX, BY, V, ZC>(u, v, p, F, flags, m, *reinterpret_cast<Plane<i64, BX, BY, V>*>(raw));
-      bits = dbits(heat_resid_fixed(p, m, F));
+      // the staged kernels with a folded r hold max |v - c|, the others max |L|
+      bits = dbits((STAGED && heat_fold(p)) ? fx_to_u(m, F) : heat_resid_fixed(p, m, F));
     } else {
       double m = 0.0;
 #pragma unroll 1
@@ -2174,12 +2196,21 @@ __global__ void __launch_bounds__(256) jacc_k_maxabs(const double* __restrict__ 
   const i64 stride = (i64)gridDim.x * blockDim.x;
   const i64 n2 = n / 2;
   const double2* u2 = reinterpret_cast<const double2*>(u);
-  for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
-    double2 t = __ldg(u2 + i);
-    u64 a = dbits(t.x) & 0x7fffffffffffffffull, c = dbits(t.y) & 0x7fffffffffffffffull;
+  auto take = [&](double2 t) {
+    const u64 a = dbits(t.x) & 0x7fffffffffffffffull, c = dbits(t.y) & 0x7fffffffffffffffull;
     m = a > m ? a : m;
     m = c > m ? c : m;
+  };
+  i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+  // four independent 16-byte loads in flight per thread (one resident wave)
+  for (; i + 3 * stride < n2; i += 4 * stride) {
+    double2 t[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) t[q] = __ldg(u2 + i + q * stride);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) take(t[q]);
   }
+  for (; i < n2; i += stride) take(__ldg(u2 + i));
   if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
     u64 a = dbits(u[n - 1]) & 0x7fffffffffffffffull;
     m = a > m ? a : m;

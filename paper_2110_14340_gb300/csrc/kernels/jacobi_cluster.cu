@@ -30,6 +30,9 @@ namespace {
 
 constexpr int kThreads = 1024;
 constexpr int kResChunk = 512;  // sweeps whose residuals are held in shared memory before a flush
+// Column-pair items per thread held in registers.  A CTA's two fields fit in
+// at most 227 KB, 2 (rows + 2) pitch words, so rows * pitch / 2 / 1024 < 7.
+constexpr int kMaxItems = 8;
 
 JD u32 cluster_rank() {
   u32 r;
@@ -114,6 +117,31 @@ __global__ void __launch_bounds__(kThreads) jacc_k_jacobi_cluster(JClusterArgs a
   const bool push_dn = nr > 0 && r1 < ny;              // last own row -> next CTA's upper halo row
   __shared__ u64 wred[2][kThreads / 32];               // per-warp residual partials, by sweep parity
   __shared__ u64 rres[kResChunk];                      // this CTA's residual maxima of the current chunk
+  // The items of a thread are the same in every sweep: their shared-memory
+  // offsets and point kinds are worked out once (at most kMaxItems per thread,
+  // which the shared-memory budget guarantees for every grid that fits)
+  int ioff[kMaxItems];
+  u32 ikind = 0;  // per item i, bits 4i..4i+3: column 0 interior, column 1 interior, push up, push down
+  int nit = 0;
+  {
+    int lr = 1 + t / half, cp = t % half;
+    for (int it = t; it < nitems && nit < kMaxItems; it += kThreads, ++nit) {
+      const i64 x0 = 2 * (i64)cp;
+      const i64 g = r0 - 1 + lr;
+      const bool yin = g >= 1 && g <= ny - 2;
+      ioff[nit] = (int)(lr * pitch + x0);
+      ikind |= (u32)((yin && x0 >= 1 && x0 <= nx - 2) | ((yin && x0 + 1 <= nx - 2) << 1) |
+                     ((push_up && lr == 1) << 2) | ((push_dn && lr == nr) << 3))
+               << (4 * nit);
+      cp += step_cols;
+      lr += step_rows;
+      if (cp >= half) {
+        cp -= half;
+        ++lr;
+      }
+    }
+  }
+  const bool hoisted = nitems <= kMaxItems * kThreads;
   for (int k = 0; k < n; ++k) {
     const u64* src = (k & 1) ? bufB : bufA;
     u64* dst = (k & 1) ? bufA : bufB;
@@ -121,7 +149,42 @@ __global__ void __launch_bounds__(kThreads) jacc_k_jacobi_cluster(JClusterArgs a
     u64 rmax_fx = 0;
     double rmax_nat = 0.0;
     int lr = 1 + t / half, cp = t % half;
-    if (fixed && !last) {
+    if (fixed && !last && hoisted) {
+      // intermediate fixed-point sweeps: a column pair per item, 16-byte
+      // shared-memory accesses, no per-sweep index or predicate arithmetic
+#pragma unroll
+      for (int i = 0; i < kMaxItems; ++i) {
+        if (i < nit) {
+          const u32 kd = ikind >> (4 * i);
+          const u64* rc = src + ioff[i];
+          const longlong2 c = *reinterpret_cast<const longlong2*>(rc);
+          const longlong2 up = *reinterpret_cast<const longlong2*>(rc - pitch);
+          const longlong2 dn = *reinterpret_cast<const longlong2*>(rc + pitch);
+          const i64 xl = (i64)rc[-1], xr = (i64)rc[2];
+          const i64 s0 = (up.x + dn.x) + (xl + c.y);
+          const i64 s1 = (up.y + dn.y) + (c.x + xr);
+          const bool in0 = kd & 1u, in1 = kd & 2u;
+          longlong2 v;
+          v.x = in0 ? (s0 + 2) >> 2 : c.x;
+          v.y = in1 ? (s1 + 2) >> 2 : c.y;
+          const i64 d0 = s0 - c.x * 4, d1 = s1 - c.y * 4;
+          const u64 a0 = (u64)(d0 ^ (d0 >> 63)), a1 = (u64)(d1 ^ (d1 >> 63));  // |d| (one less if negative)
+          rmax_fx = (in0 && a0 > rmax_fx) ? a0 : rmax_fx;
+          rmax_fx = (in1 && a1 > rmax_fx) ? a1 : rmax_fx;
+          *reinterpret_cast<longlong2*>(dst + ioff[i]) = v;
+          if (kd & 4u) {  // first own row -> the previous CTA's lower halo row
+            const u32 ra = map_rank(dst + ioff[i] + rows * pitch, rank - 1);
+            st_cluster_u64(ra, (u64)v.x);
+            st_cluster_u64(ra + 8, (u64)v.y);
+          }
+          if (kd & 8u) {  // last own row -> the next CTA's upper halo row
+            const u32 ra = map_rank(dst + ioff[i] - nr * pitch, rank + 1);
+            st_cluster_u64(ra, (u64)v.x);
+            st_cluster_u64(ra + 8, (u64)v.y);
+          }
+        }
+      }
+    } else if (fixed && !last) {
       // intermediate fixed-point sweeps: a column pair per item, 16-byte
       // shared-memory accesses (pitch is even, so every pair is aligned; an
       // odd nx pads each row by one word, which is written but never used)
@@ -224,7 +287,9 @@ __global__ void __launch_bounds__(kThreads) jacc_k_jacobi_cluster(JClusterArgs a
         }
       }
     }
-    const u64 bits = warp_max_u64(fixed ? dbits(fx_to_u(rmax_fx, F + 2)) : dbits(rmax_nat));
+    // the maximum magnitude (fixed point) or the bits of the non-negative
+    // maximum (native) order alike; one conversion per CTA after the reduction
+    const u64 bits = warp_max_u64(fixed ? rmax_fx : dbits(rmax_nat));
     if ((t & 31) == 0) wred[k & 1][t >> 5] = bits;
     // orders this sweep's shared-memory writes (local and pushed) before any
     // CTA's next sweep, and keeps every CTA's shared memory alive
@@ -232,7 +297,7 @@ __global__ void __launch_bounds__(kThreads) jacc_k_jacobi_cluster(JClusterArgs a
     if (t < 32) {  // this CTA's residual of sweep k; wred[k & 1] is next written two sweeps later
       u64 w = t < kThreads / 32 ? wred[k & 1][t] : 0ull;
       w = warp_max_u64(w);
-      if (t == 0) rres[k % kResChunk] = w;
+      if (t == 0) rres[k % kResChunk] = fixed ? dbits(fx_to_u(w, F + 2)) : w;
     }
     // Residuals leave the cluster in chunks: a global write before a barrier
     // would make the barrier's release wait for it, so each sweep's CTA
