@@ -232,6 +232,7 @@ static std::string jit_source(const Kernel& k) {
   const char* T = k.desc.dtype == 64 ? "double" : "float";
   const char* entry = k.desc.stencil == 5 ? "jacobi2d_entry" : (k.desc.stencil == 7 ? "heat3d_entry" : "box27_entry");
   const int zc = k.desc.stencil == 5 ? c.zc / 4 : c.zc;
+  const char* edge = k.desc.dtype == 64 ? "true" : "false";  // the converting sweeps' instantiation
   std::snprintf(buf, sizeof(buf),
                 "\nstruct JFold {\n"
                 "  static constexpr i64 nx = %lldll, ny = %lldll, nz = %lldll;\n"
@@ -241,12 +242,14 @@ static std::string jit_source(const Kernel& k) {
                 "  static constexpr int fk = %d, fpath = %d;\n"
                 "};\n"
                 "template <> struct JacobiPrefetch<JFold> { static constexpr bool value = %s; };\n"
-                "extern \"C\" __global__ void __launch_bounds__(%d) jacc_jit(const %s* __restrict__ u, "
+                "extern \"C\" __global__ void __launch_bounds__(%d, (SweepMinBlocks<%d, %s, %d, %d, %d, false, true>::value))\n"
+                "jacc_jit(const %s* __restrict__ u, "
                 "%s* __restrict__ v, JParams rt, double* resid, const u64* maxword, int flags) {\n"
                 "  const JFold f{};\n"
                 "  %s<%s, %d, %d, %d, %d, false>(u, v, f, rt, resid, maxword, flags);\n"
                 "}\n"
-                "extern \"C\" __global__ void __launch_bounds__(%d) jacc_jit_out(const %s* __restrict__ u, "
+                "extern \"C\" __global__ void __launch_bounds__(%d, (SweepMinBlocks<%d, %s, %d, %d, %d, %s, true>::value))\n"
+                "jacc_jit_out(const %s* __restrict__ u, "
                 "%s* __restrict__ v, JParams rt, double* resid, const u64* maxword, int flags) {\n"
                 "  const JFold f{};\n"
                 "  %s<%s, %d, %d, %d, %d, %s>(u, v, f, rt, resid, maxword, flags);\n"
@@ -255,8 +258,8 @@ static std::string jit_source(const Kernel& k) {
                 (long long)p.fb, (long long)p.fw0, (long long)p.fw1, (long long)p.fw2, (long long)p.fw3, p.fk, p.fpath,
                 // small (L2-resident) 2D grids: the prefetching march
                 (k.desc.stencil == 5 && k.desc.nx * k.desc.ny <= (int64_t(1) << 17)) ? "true" : "false",
-                c.bx * c.by, T, T, entry, T, c.bx, c.by, k.vec, zc, c.bx * c.by, T, T, entry, T, c.bx, c.by, k.vec, zc,
-                k.desc.dtype == 64 ? "true" : "false");
+                c.bx * c.by, k.desc.stencil, T, c.bx, c.by, k.vec, T, T, entry, T, c.bx, c.by, k.vec, zc, c.bx * c.by,
+                k.desc.stencil, T, c.bx, c.by, k.vec, edge, T, T, entry, T, c.bx, c.by, k.vec, zc, edge);
   return std::string(device_source()) + buf;
 }
 

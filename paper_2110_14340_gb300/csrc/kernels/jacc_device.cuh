@@ -492,21 +492,16 @@ JD void heat3d_body(const T* __restrict__ u, T* __restrict__ v, const P& p, int 
 }
 
 // Residual of the heat sweep from max |L|: r max|L| scaled.
-// r = fb 2^-k with 1 <= k <= 4 and fb <= 2 (r = 1/8, 1/16, ...): the staged
-// fixed-point heat kernels form v 2^F directly as
+// r = fb 2^-k with 1 <= k <= 4 and fb <= 2 (r = 1/8, 1/16, ...): the
+// constant-folded staged heat kernels form v 2^F directly as
 // (fb S + (2^k - 6 fb) c + 2^(k-1)) >> k, which equals c + round(r L 2^F) bit
-// for bit (2^k c is a multiple of 2^k), and take the residual from v - c in
-// every sweep of a sequence (converting or not), so residuals do not depend on
-// which kernel ran a sweep.  Every term stays below 2^62 for |c| < 2^57 and
-// |S| < 6 * 2^57.
+// for bit (2^k c is a multiple of 2^k); every term stays below 2^62 for
+// |c| < 2^57 and |S| < 6 * 2^57.  (Every fixed-point heat kernel takes its
+// residual from the increment v - c, so this changes no result.)
 template <class P> JD bool heat_fold(const P& p) {
   return p.fpath == JACC_FP_SMALL && p.fk >= 1 && p.fk <= 4 && p.fb >= 1 && p.fb <= 2;
 }
 
-template <class P> JD double heat_resid_fixed(const P& p, u64 maxL, int F) {
-  const u64 m = (p.fpath == JACC_FP_SMALL) ? (u64)p.fb : (u64)p.fw0;
-  return fx128_to(mul_s64_u64((i64)maxL, m), F + p.fk);
-}
 
 // ---------------------------------------------------------------- 27-point periodic box
 //
@@ -1577,16 +1572,17 @@ JD void heat3d_fx_body(const double* __restrict__ u, double* __restrict__ v, con
       const i64 xr = (e == V - 1) ? r0[V] : cur[e + 1];
       const i64 sum = ((xl + xr) + (rm[e] + rp[e])) + (zp[e] + zn[e]);
       const i64 L = sum - 6 * cur[e];
+      // the increment v - c in fixed point: v = c + round(r L)
+      const i64 dv = small ? fx_round_shift(fb * L, k) : fx128_round_shift(mul_s64_u64(L, (u64)fw0), k);
       double o;
       if (outf) {
         if (small) o = fx_to(cur[e] * ((i64)1 << k) + fb * L, F + k);
         else o = fx128_to(add128(from_s64_shl(cur[e], k), mul_s64_u64(L, (u64)fw0)), F + k);
       } else {
-        if (small) o = i64_bits(cur[e] + fx_round_shift(fb * L, k));
-        else o = i64_bits(cur[e] + fx128_round_shift(mul_s64_u64(L, (u64)fw0), k));
+        o = i64_bits(cur[e] + dv);
       }
       out[e] = in ? o : bnd_out(rcur[e], cur[e]);
-      const u64 aL = (u64)(L ^ (L >> 63));  // |L| (one less for negative L: 2^-F, below the tolerance)
+      const u64 aL = (u64)(dv ^ (dv >> 63));  // |v - c| (one less for negative: 2^-F, below the tolerance)
       rmax = (in && aL > rmax) ? aL : rmax;
     }
     if (act) stv<double, V>(vrow + zoff, out);
@@ -1620,16 +1616,17 @@ JD void heat3d_fx_body(const double* __restrict__ u, double* __restrict__ v, con
 //
 // FX: FP64 storage in the resident 64-bit fixed point (EDGE: the first/last
 // sweep converts on load/store); otherwise native arithmetic on T.
-template <class T, int BX, int BY> struct Heat3S {
+template <class T, int BX, int BY, int SC> struct Heat3S {
   static constexpr int V = 16 / (int)sizeof(T);
   static constexpr int RY = 2;
   static constexpr int TW = BX * V, TH = BY * RY;
   static constexpr int W = TW + 2 * V, R = TH + 2;
   static constexpr int STAGE_BYTES = W * R * (int)sizeof(T);
   static constexpr int S0 = 45056 / STAGE_BYTES;
-  // stages: 2..6 for FP64 (heavier per-plane work, deeper prefetch pays),
-  // 2..4 for FP32 (measured: more stages cost occupancy)
-  static constexpr int SMAX = sizeof(T) == 8 ? 6 : 4;
+  // stages: at most ~44 KB and SC (512^3 with 32 x 4 threads, 5.4 KB
+  // stages: FP32 656 GLUP/s with 4 stages, 710 with 5, 713 with 6; FP64
+  // precompiled 327.5 with 6, 295.6 with 5); larger tiles' stages fit fewer
+  static constexpr int SMAX = SC;
   static constexpr int S = S0 < 2 ? 2 : (S0 > SMAX ? SMAX : S0);
   // A step needs planes z and z+1 staged.  With S >= 3 warp 0 refills the
   // stage released one step earlier (slack for lagging warps); with S = 2 it
@@ -1638,17 +1635,18 @@ template <class T, int BX, int BY> struct Heat3S {
   static constexpr int NW = BX * BY / 32;
 };
 
-template <class T, int BX, int BY> struct alignas(128) Heat3SSmem {
-  T st[Heat3S<T, BX, BY>::S][Heat3S<T, BX, BY>::R][Heat3S<T, BX, BY>::W];
-  u64 full[Heat3S<T, BX, BY>::S];
-  u64 empty[Heat3S<T, BX, BY>::S];
+template <class T, int BX, int BY, int SC> struct alignas(128) Heat3SSmem {
+  T st[Heat3S<T, BX, BY, SC>::S][Heat3S<T, BX, BY, SC>::R][Heat3S<T, BX, BY, SC>::W];
+  u64 full[Heat3S<T, BX, BY, SC>::S];
+  u64 empty[Heat3S<T, BX, BY, SC>::S];
 };
 
 // Warp 0 requests plane zg into stage s: one bulk copy per staged row inside
 // the grid; lane 0 first posts the byte count of the whole plane.
-template <class T, int BX, int BY, class P>
-JD void heat3s_issue(Heat3SSmem<T, BX, BY>& sm, int s, const T* __restrict__ u, const P& p, i64 zg, i64 bx0, i64 by0) {
-  typedef Heat3S<T, BX, BY> G;
+template <class T, int BX, int BY, int SC, class P>
+JD void heat3s_issue(Heat3SSmem<T, BX, BY, SC>& sm, int s, const T* __restrict__ u, const P& p, i64 zg, i64 bx0,
+                     i64 by0) {
+  typedef Heat3S<T, BX, BY, SC> G;
   const i64 nx = p.nx, ny = p.ny;
   const int lane = threadIdx.x & 31;
   const i64 c0 = bx0 - G::V < 0 ? 0 : bx0 - G::V;
@@ -1676,13 +1674,16 @@ JD void lds_vec(const void* p, i64 (&r)[2]) {
   r[0] = t.x; r[1] = t.y;
 }
 
+template <class A, class B> struct SameT { static constexpr bool value = false; };
+template <class A> struct SameT<A, A> { static constexpr bool value = true; };
+
 template <class T, bool FX> struct HeatAcc { typedef T type; };
 template <> struct HeatAcc<double, true> { typedef u64 type; };
 
-template <class T, int BX, int BY, int ZC, bool FX, bool EDGE, class P>
+template <class T, int BX, int BY, int ZC, bool FX, bool EDGE, int SC, class P>
 JD void heat3s_body(const T* __restrict__ u, T* __restrict__ v, const P& p, const JParams& rt, int F, int flags,
-                    typename HeatAcc<T, FX>::type& rmax, Heat3SSmem<T, BX, BY>& sm) {
-  typedef Heat3S<T, BX, BY> G;
+                    typename HeatAcc<T, FX>::type& rmax, Heat3SSmem<T, BX, BY, SC>& sm) {
+  typedef Heat3S<T, BX, BY, SC> G;
   constexpr int V = G::V;
   typedef typename WT<T, FX ? JM_FIXED : JM_NATIVE>::type Wt;  // working type: i64 (fixed) or T
   const i64 nx = p.nx, ny = p.ny, nz = p.nz, sz = nx * ny;
@@ -1751,7 +1752,7 @@ JD void heat3s_body(const T* __restrict__ u, T* __restrict__ v, const P& p, cons
   }
   __syncthreads();
   auto request = [&](int j, int s) {
-    if (!(stall_cta && j == rt.stall_plane)) heat3s_issue<T, BX, BY>(sm, s, u, p, z0 - 1 + j, bx0, by0);
+    if (!(stall_cta && j == rt.stall_plane)) heat3s_issue<T, BX, BY, SC>(sm, s, u, p, z0 - 1 + j, bx0, by0);
   };
   int issued = 0, consumed = 0;  // warp 0: planes requested, planes waited for
   if (warp0)
@@ -1831,6 +1832,7 @@ JD void heat3s_body(const T* __restrict__ u, T* __restrict__ v, const P& p, cons
   const int k = p.fk;
   const bool small = p.fpath == JACC_FP_SMALL;
   const bool fold = heat_fold(p);
+  constexpr bool folded = !SameT<P, JParams>::value;  // extents and coefficients are constants
   vo += z0 * sz;
   // one output plane (staged plane j, 1 <= j <= L-2) from the own values of
   // planes j-1 (zp) and j (cur); fills zn with those of plane j+1
@@ -1879,24 +1881,23 @@ JD void heat3s_body(const T* __restrict__ u, T* __restrict__ v, const P& p, cons
         const Wt ce = cur[yy][e];
         if constexpr (FX) {
           double o;
-          u64 aL;
-          if (fold) {
+          i64 dv;  // the increment v - c in fixed point: v = c + round(r L)
+          if (folded && fold) {
             const i64 vn = (fb * sum + ((((i64)1 << k) - 6 * fb) * ce + ((i64)1 << (k - 1)))) >> k;
-            const i64 dv = vn - ce;
-            aL = (u64)(dv ^ (dv >> 63));  // |v - c| (one less if negative)
-            if (outf) o = fx_to(ce * ((i64)1 << k) + fb * (sum - 6 * ce), F + k);
-            else o = i64_bits(vn);
+            dv = vn - ce;
+            o = outf ? fx_to(ce * ((i64)1 << k) + fb * (sum - 6 * ce), F + k) : i64_bits(vn);
           } else {
             const i64 Ld = sum - 6 * ce;
+            if (small) dv = fx_round_shift(fb * Ld, k);
+            else dv = fx128_round_shift(mul_s64_u64(Ld, (u64)fw0), k);
             if (outf) {
               if (small) o = fx_to(ce * ((i64)1 << k) + fb * Ld, F + k);
               else o = fx128_to(add128(from_s64_shl(ce, k), mul_s64_u64(Ld, (u64)fw0)), F + k);
             } else {
-              if (small) o = i64_bits(ce + fx_round_shift(fb * Ld, k));
-              else o = i64_bits(ce + fx128_round_shift(mul_s64_u64(Ld, (u64)fw0), k));
+              o = i64_bits(ce + dv);
             }
-            aL = (u64)(Ld ^ (Ld >> 63));
           }
+          const u64 aL = (u64)(dv ^ (dv >> 63));  // |v - c| (one less if negative)
           if constexpr (RAW) out[e] = in ? o : bnd_out(rcur[yy][e]);
           else out[e] = in ? o : as_out(ce);
           rmax = (in && aL > rmax) ? aL : rmax;
@@ -2124,18 +2125,20 @@ JD void heat3d_entry(const T* __restrict__ u, T* __restrict__ v, const P& p, con
     // 2 BY rows; the native fallback then runs two BY-row sub-tiles)
     constexpr bool STAGED = V == 2;
     constexpr size_t SM_PLANE = sizeof(Plane<i64, BX, BY, V>);
-    constexpr size_t SM_STAGED = STAGED ? sizeof(Heat3SSmem<double, BX, BY>) : 0;
+    // stage cap: 5 for the constant-folded intermediate sweeps (7 CTAs per SM,
+    // SweepMinBlocks), else 6
+    constexpr int SC = (!EDGE && !SameT<P, JParams>::value) ? 5 : 6;
+    constexpr size_t SM_STAGED = STAGED ? sizeof(Heat3SSmem<double, BX, BY, SC>) : 0;
     __shared__ __align__(128) unsigned char raw[SM_PLANE > SM_STAGED ? SM_PLANE : SM_STAGED];
     const int F = (maxword && p.fpath != JACC_FP_NONE) ? fx_frac_bits(*maxword) : -1;
     if (F >= 0) {
       u64 m = 0;
       if constexpr (STAGED)
-        heat3s_body<double, BX, BY, ZC, true, EDGE>(u, v, p, rt, F, flags, m,
-                                                    *reinterpret_cast<Heat3SSmem<double, BX, BY>*>(raw));
+        heat3s_body<double, BX, BY, ZC, true, EDGE, SC>(u, v, p, rt, F, flags, m,
+                                                        *reinterpret_cast<Heat3SSmem<double, BX, BY, SC>*>(raw));
       else
         heat3d_fx_body<EDGE, BX, BY, V, ZC>(u, v, p, F, flags, m, *reinterpret_cast<Plane<i64, BX, BY, V>*>(raw));
-      // the staged kernels with a folded r hold max |v - c|, the others max |L|
-      bits = dbits((STAGED && heat_fold(p)) ? fx_to_u(m, F) : heat_resid_fixed(p, m, F));
+      bits = dbits(fx_to_u(m, F));  // max |v - c| in fixed point
     } else {
       double m = 0.0;
 #pragma unroll 1
@@ -2145,9 +2148,9 @@ JD void heat3d_entry(const T* __restrict__ u, T* __restrict__ v, const P& p, con
       bits = dbits(m);
     }
   } else if constexpr (V == 4) {
-    __shared__ Heat3SSmem<float, BX, BY> sm;
+    __shared__ Heat3SSmem<float, BX, BY, 6> sm;
     float m = 0.0f;
-    heat3s_body<float, BX, BY, ZC, false, false>(u, v, p, rt, -1, 0, m, sm);
+    heat3s_body<float, BX, BY, ZC, false, false, 6>(u, v, p, rt, -1, 0, m, sm);
     bits = dbits((double)m);
   } else {
     __shared__ Plane<T, BX, BY, V> sm;
@@ -2235,6 +2238,22 @@ __global__ void jacc_k_fill_skipped(double* resid, int n, int T) {
 
 #endif  // JACC_AUX_KERNELS
 
+// Minimum resident CTAs per SM asked of the compiler (the second launch
+// bound) for a sweep kernel.  For the staged FP64 7-point kernel with 32 x 4
+// threads (512^3, 200 sweeps): the constant-folded intermediate sweeps at 7
+// CTAs (at most 72 registers, 5 stages of 5.4 KB) run 384.7 GLUP/s against
+// 378.8 at 6; the precompiled intermediate sweeps spill at that bound (298.9)
+// and, unbounded, take 124 registers (4 CTAs), so they ask for 6 (80
+// registers, 6 stages); the converting sweeps at 5 CTAs (at most 102
+// registers, from 157) take 2.40 ms for a 2-sweep sequence against 2.83.
+// Every other kernel: 0, no requirement (a bound of 1 is not neutral: it
+// lets the compiler take registers for one CTA per SM, e.g. 111 instead of
+// 80 for the staged FP32 7-point kernel).
+template <int STENCIL, class T, int BX, int BY, int V, bool EDGE, bool FOLDED> struct SweepMinBlocks {
+  static constexpr bool heat_staged_fp64 = STENCIL == 7 && sizeof(T) == 8 && BX == 32 && BY == 4 && V == 2;
+  static constexpr int value = heat_staged_fp64 ? (EDGE ? 5 : (FOLDED ? 7 : 6)) : 0;
+};
+
 // Kernel templates instantiated by the precompiled library (P = JParams).
 template <class T, int BX, int BY, int V, int ZC, bool EDGE>
 __global__ void __launch_bounds__(BX * BY) jacc_k_jacobi2d(const T* __restrict__ u, T* __restrict__ v, JParams p,
@@ -2242,7 +2261,8 @@ __global__ void __launch_bounds__(BX * BY) jacc_k_jacobi2d(const T* __restrict__
   jacobi2d_entry<T, BX, BY, V, ZC, EDGE>(u, v, p, p, resid, maxword, flags);
 }
 template <class T, int BX, int BY, int V, int ZC, bool EDGE>
-__global__ void __launch_bounds__(BX * BY) jacc_k_heat3d(const T* __restrict__ u, T* __restrict__ v, JParams p,
+__global__ void __launch_bounds__(BX * BY, (SweepMinBlocks<7, T, BX, BY, V, EDGE, false>::value))
+    jacc_k_heat3d(const T* __restrict__ u, T* __restrict__ v, JParams p,
                                                          double* resid, const u64* maxword, int flags) {
   heat3d_entry<T, BX, BY, V, ZC, EDGE>(u, v, p, p, resid, maxword, flags);
 }
