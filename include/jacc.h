@@ -295,7 +295,10 @@ jacc_status jacc_launch(jacc_kernel k, const void* u_in, void* u_out, double* re
  * between the sweeps of one call (same 8 bytes per value, in u0/u1): the
  * first sweep reads FP64, the last writes FP64, each intermediate sweep rounds
  * once to the fixed-point grid (2^-F with F >= 57 - e(max|u0|), finer than an
- * FP64 ulp of max|u0|).  Dirichlet boundary values pass through the same grid:
+ * FP64 ulp of max|u0|).  For fields of at least 2^22 points and nsweeps >= 2
+ * the conversion of u0 runs as its own kernel, in place, before the first
+ * sweep (u0 is overwritten by the second sweep in any case); the values are
+ * those the first sweep would convert on load.  Dirichlet boundary values pass through the same grid:
  * they come back unchanged when they are multiples of 2^-F (for instance any
  * value within 2^52 ulps of max|u0|) and otherwise within 2^-F.  After the
  * call the result buffer holds FP64; the other buffer holds the internal

@@ -92,6 +92,8 @@ constexpr int64_t kDefaultTimeoutNs = 2000000000;
 // Enqueue the max-abs pre-pass of `n` doubles into maxword (zeroing it first).
 cudaError_t launch_maxabs(const double* u, long long n, u64* maxword, cudaStream_t s);
 cudaError_t launch_fill_skipped(double* resid, int n, int T, cudaStream_t s);
+// u (n FP64 values) -> the resident fixed point in place, F from *maxword
+cudaError_t launch_to_fixed(double* u, long long n, const u64* maxword, cudaStream_t s);
 
 // NVRTC: compile `src` (plus jacc_params.h) for sm_103a, load it, return
 // kernel `name`.  Uses the on-disk cache under $JACC_CACHE_DIR if set.

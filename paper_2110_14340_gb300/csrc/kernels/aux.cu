@@ -24,6 +24,17 @@ cudaError_t launch_maxabs(const double* u, long long n, u64* maxword, cudaStream
   return cudaGetLastError();
 }
 
+cudaError_t launch_to_fixed(double* u, long long n, const u64* maxword, cudaStream_t s) {
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    nsm = 152;
+  long long blocks = (n / 2 + 255) / 256;
+  if (blocks < 1) blocks = 1;
+  if (blocks > 8ll * nsm) blocks = 8ll * nsm;
+  jacc_k_to_fixed<<<(unsigned)blocks, 256, 0, s>>>(u, n, maxword);
+  return cudaGetLastError();
+}
+
 // Temporally blocked 27-point FP32 kernels: region 128 x 16, depth 2 and 3, 64-plane chunks.
 extern "C" const void* const jacc_tab_tb[2] = {(const void*)jacc_k_box27_tb<16, 2, 64>,
                                                (const void*)jacc_k_box27_tb<16, 3, 64>};
