@@ -222,6 +222,15 @@ def run_gpu(args):
         k.release()
         return fb
 
+    def step_host(u_in, out, x, y, r, r_host, stream):
+        """The same step from and to host memory: one jacc_sweep_host call."""
+        st, _ = jacc.region_analyze(loops, refs, arrays)
+        assert st == 0
+        k = jacc.Kernel(jacc.STENCIL_7PT, jacc.F64, N, N, N, coeffs=(R,), tile_id=args.tile, jit=jit)
+        fb = jacc.sweep_host(k, u_in, out, x, y, SWEEPS, r, r_host, graph=True, stream=stream)
+        k.release()
+        return fb
+
     keep = jacc.Kernel(jacc.STENCIL_7PT, jacc.F64, N, N, N, coeffs=(R,), tile_id=args.tile,
                        jit=jit)  # holds the cache entry
     info = keep.info()
@@ -270,7 +279,7 @@ def run_gpu(args):
     # input field, the 200-sweep graph, D2H of the result field and residuals.
     e2e = None
     if not args.no_e2e:
-        e2e = measure_e2e(step, a, b, resid, u_host, args, ws)
+        e2e = measure_e2e(step_host, a, b, resid, u_host, args, ws)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GLUP/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -292,28 +301,38 @@ def run_gpu(args):
         torch.distributed.destroy_process_group()
 
 
-def measure_e2e(step, a, b, resid, u_host, args, ws):
+def measure_e2e(step_host, a, b, resid, u_host, args, ws):
+    """Whole-job rate from host memory: every step copies its input field (1 GiB,
+    page-locked) to the device, runs the 200-sweep sequence and copies the result
+    field and the residuals back, in one jacc_sweep_host call.  Consecutive steps
+    alternate between two streams and two sets of device buffers, so one step's
+    copies overlap the other's sweeps; the timed region is host wall time from the
+    first call to the completion of the last copy."""
     import numpy as np
     import torch
     pin_in = torch.from_numpy(u_host).pin_memory()
-    pin_out = torch.empty_like(pin_in).pin_memory()
-    pin_res = torch.empty(SWEEPS, dtype=torch.float64).pin_memory()
-    e_steps = max(1, min(args.steps, 3))
-    for it in range(e_steps + 1):
-        if it == 1:
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-        a.copy_(pin_in, non_blocking=True)
-        fb = step(a, b)
-        pin_out.copy_(a if fb == 0 else b, non_blocking=True)
-        pin_res.copy_(resid, non_blocking=True)
+    outs = [torch.empty_like(pin_in).pin_memory() for _ in range(2)]
+    res_host = [torch.empty(SWEEPS, dtype=torch.float64).pin_memory() for _ in range(2)]
+    sets = [(a, b, resid), (torch.empty_like(a), torch.empty_like(b), torch.zeros_like(resid))]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    e_steps = max(4, min(args.steps, 8))
+
+    def run(nsteps):
+        for i in range(nsteps):
+            x, y, r = sets[i % 2]
+            step_host(pin_in, outs[i % 2], x, y, r, res_host[i % 2], streams[i % 2])
         torch.cuda.synchronize()
+
+    run(2)  # captures the sequence graph of each buffer set
+    t0 = time.perf_counter()
+    run(e_steps)
     e2e_s = (time.perf_counter() - t0) / e_steps
     e2e = {"value": LUP_PER_SWEEP * SWEEPS * ws / e2e_s / 1e9, "unit": "GLUP/s",
-           "h2d_bytes_per_step": int(pin_in.numel() * 8), "d2h_bytes_per_step": int(pin_out.numel() * 8 + SWEEPS * 8),
-           "ms_per_step": 1e3 * e2e_s}
-
-    assert np.isfinite(pin_res.numpy()).all()
+           "h2d_bytes_per_step": int(pin_in.numel() * 8), "d2h_bytes_per_step": int(outs[0].numel() * 8 + SWEEPS * 8),
+           "ms_per_step": 1e3 * e2e_s, "steps": e_steps,
+           "overlap": "two streams, two device buffer sets; each step's copies overlap the other's sweeps"}
+    for rh in res_host:
+        assert np.isfinite(rh.numpy()).all()
     return e2e
 
 

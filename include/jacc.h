@@ -307,6 +307,28 @@ jacc_status jacc_launch(jacc_kernel k, const void* u_in, void* u_out, double* re
 jacc_status jacc_sweep(jacc_kernel k, void* u0, void* u1, int32_t nsweeps, double* resid_dev, uint32_t flags,
                        uintptr_t stream, int32_t* final_buf);
 
+/* jacc_sweep_host: jacc_sweep from and to host memory in one call (the
+ * whole-job path of a caller whose fields live on the host).  Enqueues on
+ * `stream`, in order: a copy of the input field u_host (host, nx*ny*nz values
+ * of the kernel's dtype) into u0, jacc_sweep(k, u0, u1, nsweeps, resid_dev,
+ * flags, stream), a copy of the result field into result_host (host, same
+ * size) and, if resid_host is non-NULL, of the nsweeps residuals from
+ * resid_dev (then required) into resid_host.  u0, u1 and resid_dev are the
+ * caller's device buffers with jacc_sweep's rules; the library allocates
+ * nothing here.  Host buffers are caller-owned and must stay valid until the
+ * stream reaches the copies; with page-locked host memory (cudaHostAlloc,
+ * cudaHostRegister) the copies are asynchronous, so calls on two streams with
+ * two sets of device buffers overlap each call's copies with the other's
+ * sweeps; pageable memory is correct but copies synchronously.  *final_buf
+ * (host, nullable) as jacc_sweep.  Errors: INVALID_ARG for NULL host buffers,
+ * resid_host without resid_dev and every jacc_sweep argument error; CUDA for
+ * a failed copy.  The paper's runtime copies data to and from the device
+ * around its kernels (§3.2.1, data-region tracking); this is that transfer
+ * for one sweep sequence. */
+jacc_status jacc_sweep_host(jacc_kernel k, const void* u_host, void* result_host, void* u0, void* u1,
+                            int32_t nsweeps, double* resid_dev, double* resid_host, uint32_t flags,
+                            uintptr_t stream, int32_t* final_buf);
+
 /* jacc_sweep_coeffs: nsweeps ping-pong sweeps of a JACC_STENCIL_19PT kernel,
  * as jacc_sweep (resid_dev, flags, stream and final_buf alike), with its
  * twelve coefficient fields: fields[0..11] = a0 a1 a2 a3 b0 b1 b2 c0 c1 c2

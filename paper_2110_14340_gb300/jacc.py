@@ -112,6 +112,7 @@ SIGNATURES = {
     "jacc_launch": ([P, P, P, P, C.c_size_t], C.c_int32),
     "jacc_launch_static": ([P, P, P, P, C.c_size_t], C.c_int32),
     "jacc_sweep": ([P, P, P, C.c_int32, P, C.c_uint32, C.c_size_t, P], C.c_int32),
+    "jacc_sweep_host": ([P, P, P, P, P, C.c_int32, P, P, C.c_uint32, C.c_size_t, P], C.c_int32),
     "jacc_sweep_until": ([P, P, P, C.c_int32, C.c_double, P, P, C.c_size_t], C.c_int32),
     "jacc_sweep_coeffs": ([P, P, P, C.c_int32, P, C.c_int32, P, C.c_uint32, C.c_size_t, P], C.c_int32),
     "jacc_sched_create": ([C.c_int32, C.c_uint32, C.c_size_t, P], C.c_int32),
@@ -370,6 +371,38 @@ def sweep(k, u0, u1, nsweeps, resid=None, graph=True, stream=None):
     fb = C.c_int32(-1)
     _check(lib().jacc_sweep(k.handle, _field(k, u0, "u0"), _field(k, u1, "u1"), nsweeps, _resid(resid),
                             SWEEP_GRAPH if graph else 0, _stream(stream), C.byref(fb)))
+    return fb.value
+
+
+def _host_field(k, t, name):
+    import torch
+    want = torch.float64 if k.desc.dtype == F64 else torch.float32
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise ValueError(f"{name} must be a CPU tensor")
+    if t.dtype != want or not t.is_contiguous() or tuple(t.shape) != k.shape:
+        raise ValueError(f"{name} must be a contiguous {want} tensor of shape {k.shape}")
+    return t.data_ptr()
+
+
+def sweep_host(k, u_host, result_host, u0, u1, nsweeps, resid=None, resid_host=None, graph=True, stream=None):
+    """jacc_sweep_host: copy u_host (CPU tensor; pinned for asynchronous copies) into
+    u0, run the sequence, copy the result field into result_host (and the residuals
+    into resid_host, a CPU float64 tensor, which needs resid).  Returns 0 if the
+    device result is in u0, 1 if in u1.  The host tensors must stay alive until the
+    stream has run the copies."""
+    import torch
+    if resid is not None and resid.numel() < nsweeps:
+        raise ValueError("resid needs nsweeps elements")
+    rh = None
+    if resid_host is not None:
+        if (not isinstance(resid_host, torch.Tensor) or resid_host.is_cuda or resid_host.dtype != torch.float64
+                or not resid_host.is_contiguous() or resid_host.numel() < nsweeps):
+            raise ValueError("resid_host must be a contiguous CPU float64 tensor of nsweeps elements")
+        rh = resid_host.data_ptr()
+    fb = C.c_int32(-1)
+    _check(lib().jacc_sweep_host(k.handle, _host_field(k, u_host, "u_host"), _host_field(k, result_host, "result_host"),
+                                 _field(k, u0, "u0"), _field(k, u1, "u1"), nsweeps, _resid(resid), rh,
+                                 SWEEP_GRAPH if graph else 0, _stream(stream), C.byref(fb)))
     return fb.value
 
 
