@@ -111,3 +111,19 @@ def test_until_rejects_27_point_and_bad_arguments():
         jacc.sweep_until(k5, a5, torch.zeros_like(a5), 4, -1.0, r, st)
     with pytest.raises(RuntimeError, match="INVALID_ARG"):
         jacc.sweep_until(k5, a5, a5, 4, 0.0, r, st)
+
+
+def test_large_field_sequence_with_input_conversion_matches_until():
+    # a field of at least 2^22 points: jacc_sweep converts u0 in place before
+    # its first sweep; jacc_sweep_until converts on load in its first sweep.
+    # Both must leave the same bits in both buffers and the same residuals.
+    side = 162  # 162^3 = 4.25 M points
+    u = inputs.heat3d_field(side, seed=33)
+    k = jacc.Kernel(jacc.STENCIL_7PT, jacc.F64, side, side, side, coeffs=(0.125,))
+    n = 6
+    fb, a, b, r = fixed_count(k, u, n)
+    n2, fb2, a2, b2, r2 = until(k, u, n, 0.0)
+    assert n2 == n and fb2 == fb
+    assert np.array_equal(a.view(np.int64), a2.view(np.int64))
+    assert np.array_equal(b.view(np.int64), b2.view(np.int64))
+    assert np.array_equal(r, r2[:n])
