@@ -16,6 +16,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -64,7 +65,9 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"bench_clocks_{os.getpid()}.csv")
+        # the raw samples go to BENCH_CLOCKS_DIR (default: the system's temporary directory)
+        d = os.environ.get("BENCH_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"bench_clocks_{os.getpid()}.csv")
 
     def start(self):
         try:
