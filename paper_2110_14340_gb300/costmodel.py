@@ -204,6 +204,19 @@ def evaluate(model, train_table, test_table, margin=None):
     # search cost the model saves: the exhaustive tuner times 24 tiles x 6 runs per query
     out["exhaustive_search_ms_per_query"] = float(np.mean([6 * sum(m for m in q["ms"] if math.isfinite(m))
                                                            for q in test_table]))
+    # the model as a filter: time only its k best predicted tiles and keep the
+    # fastest (the tables hold every tile's timing, so no new runs are needed)
+    P = pred.cpu().numpy()
+    for kk in (2, 3):
+        picks_k, cost = [], []
+        for i, q in enumerate(test_table):
+            valid = np.asarray(q["valid"], dtype=bool)
+            order = [t for t in np.argsort(P[i]) if valid[t]][:kk]
+            ms = np.asarray(q["ms"])
+            picks_k.append(int(order[int(np.argmin(ms[order]))]))
+            cost.append(6 * float(np.sum(ms[order])))
+        out[f"model_top{kk}_timed"] = dict(search_ms_per_query=float(np.mean(cost)),
+                                           **summary(regrets(test_table, picks_k)))
     if margin is not None:
         # model with its fallback: queries whose top-2 predicted gap is below the
         # margin go to the exhaustive autotuner (regret 0, search cost paid)
@@ -222,6 +235,8 @@ def main():
     ap.add_argument("--heldout", type=int, default=200)
     ap.add_argument("--epochs", type=int, default=8000)
     ap.add_argument("--max-side", type=int, default=1024)
+    ap.add_argument("--tables", default=None,
+                    help="reuse the timing tables of an earlier --out file instead of collecting them")
     args = ap.parse_args()
     import torch
 
@@ -233,11 +248,17 @@ def main():
     ho = heldout_sides(per, set(tr), 256, args.max_side)
     train_q = [(s, d, side) for s, d in PAIRS for side in tr]
     test_q = [(s, d, side) for s, d in PAIRS for side in ho][:args.heldout]
-    bufs = Buffers(args.max_side ** 3)
-    t0 = time.perf_counter()
-    train_table = collect(train_q, bufs, log=print)
-    test_table = collect(test_q, bufs, log=print)
-    t_collect = time.perf_counter() - t0
+    if args.tables:
+        with open(args.tables) as f:
+            old = json.load(f)
+        train_table, test_table = old["train_table"], old["test_table"]
+        t_collect = old["result"].get("collect_seconds")
+    else:
+        bufs = Buffers(args.max_side ** 3)
+        t0 = time.perf_counter()
+        train_table = collect(train_q, bufs, log=print)
+        test_table = collect(test_q, bufs, log=print)
+        t_collect = time.perf_counter() - t0
     X, Y = xy(train_table)
     model = jacc.CostModel(seed=5)
     loss, t_train = fit(model, X, Y, args.epochs)
