@@ -225,12 +225,13 @@ def run_gpu(args):
         k.release()
         return fb
 
-    def step_host(u_in, out, x, y, r, r_host, stream):
+    def step_host(u_in, out, x, y, r, r_host, stream, wait_event, done_event):
         """The same step from and to host memory: one jacc_sweep_host call."""
         st, _ = jacc.region_analyze(loops, refs, arrays)
         assert st == 0
         k = jacc.Kernel(jacc.STENCIL_7PT, jacc.F64, N, N, N, coeffs=(R,), tile_id=args.tile, jit=jit)
-        fb = jacc.sweep_host(k, u_in, out, x, y, SWEEPS, r, r_host, graph=True, stream=stream)
+        fb = jacc.sweep_host(k, u_in, out, x, y, SWEEPS, r, r_host, graph=True, stream=stream,
+                             wait_event=wait_event, done_event=done_event)
         k.release()
         return fb
 
@@ -308,9 +309,10 @@ def measure_e2e(step_host, a, b, resid, u_host, args, ws):
     """Whole-job rate from host memory: every step copies its input field (1 GiB,
     page-locked) to the device, runs the 200-sweep sequence and copies the result
     field and the residuals back, in one jacc_sweep_host call.  Consecutive steps
-    alternate between two streams and two sets of device buffers, so one step's
-    copies overlap the other's sweeps; the timed region is host wall time from the
-    first call to the completion of the last copy."""
+    alternate between two streams and two sets of device buffers, the sweeps kept
+    in order by events, so one step's copies overlap its neighbours' sweeps; the
+    timed region is host wall time from the first call to the completion of the
+    last copy."""
     import numpy as np
     import torch
     pin_in = torch.from_numpy(u_host).pin_memory()
@@ -318,12 +320,16 @@ def measure_e2e(step_host, a, b, resid, u_host, args, ws):
     res_host = [torch.empty(SWEEPS, dtype=torch.float64).pin_memory() for _ in range(2)]
     sets = [(a, b, resid), (torch.empty_like(a), torch.empty_like(b), torch.zeros_like(resid))]
     streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    done = [torch.cuda.Event(), torch.cuda.Event()]
     e_steps = max(4, min(args.steps, 8))
 
     def run(nsteps):
+        # step i: copy in on stream i % 2 at once, sweeps after step i-1's sweeps
+        # (events), copy out after its own sweeps
         for i in range(nsteps):
             x, y, r = sets[i % 2]
-            step_host(pin_in, outs[i % 2], x, y, r, res_host[i % 2], streams[i % 2])
+            step_host(pin_in, outs[i % 2], x, y, r, res_host[i % 2], streams[i % 2],
+                      done[(i + 1) % 2] if i else None, done[i % 2])
         torch.cuda.synchronize()
 
     run(2)  # captures the sequence graph of each buffer set
@@ -333,7 +339,8 @@ def measure_e2e(step_host, a, b, resid, u_host, args, ws):
     e2e = {"value": LUP_PER_SWEEP * SWEEPS * ws / e2e_s / 1e9, "unit": "GLUP/s",
            "h2d_bytes_per_step": int(pin_in.numel() * 8), "d2h_bytes_per_step": int(outs[0].numel() * 8 + SWEEPS * 8),
            "ms_per_step": 1e3 * e2e_s, "steps": e_steps,
-           "overlap": "two streams, two device buffer sets; each step's copies overlap the other's sweeps"}
+           "overlap": "two streams, two device buffer sets, sweeps kept in order by events; each step's copies "
+                      "overlap the neighbouring steps' sweeps"}
     for rh in res_host:
         assert np.isfinite(rh.numpy()).all()
     return e2e

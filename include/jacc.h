@@ -319,7 +319,12 @@ jacc_status jacc_sweep(jacc_kernel k, void* u0, void* u1, int32_t nsweeps, doubl
  * stream reaches the copies; with page-locked host memory (cudaHostAlloc,
  * cudaHostRegister) the copies are asynchronous, so calls on two streams with
  * two sets of device buffers overlap each call's copies with the other's
- * sweeps; pageable memory is correct but copies synchronously.  *final_buf
+ * sweeps; pageable memory is correct but copies synchronously.  wait_event
+ * and done_event (cudaEvent_t as an integer, each 0 for none): the sweeps
+ * wait for wait_event (after the input copy is enqueued), and done_event is
+ * recorded after the sweeps (before the copy back), so that consecutive
+ * calls on two streams can keep their sweeps in order while their copies
+ * overlap (pass the previous call's done_event as wait_event).  *final_buf
  * (host, nullable) as jacc_sweep.  Errors: INVALID_ARG for NULL host buffers,
  * resid_host without resid_dev and every jacc_sweep argument error; CUDA for
  * a failed copy.  The paper's runtime copies data to and from the device
@@ -327,7 +332,7 @@ jacc_status jacc_sweep(jacc_kernel k, void* u0, void* u1, int32_t nsweeps, doubl
  * for one sweep sequence. */
 jacc_status jacc_sweep_host(jacc_kernel k, const void* u_host, void* result_host, void* u0, void* u1,
                             int32_t nsweeps, double* resid_dev, double* resid_host, uint32_t flags,
-                            uintptr_t stream, int32_t* final_buf);
+                            uintptr_t stream, uintptr_t wait_event, uintptr_t done_event, int32_t* final_buf);
 
 /* jacc_sweep_coeffs: nsweeps ping-pong sweeps of a JACC_STENCIL_19PT kernel,
  * as jacc_sweep (resid_dev, flags, stream and final_buf alike), with its

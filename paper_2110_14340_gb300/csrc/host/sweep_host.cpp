@@ -6,7 +6,9 @@
 // Three cudaMemcpyAsync calls, one per buffer; the library allocates
 // nothing.  With page-locked host buffers the copies are asynchronous, so
 // calls on two streams with two sets of device buffers overlap one call's
-// copies with the other's sweeps.
+// copies with the other's sweeps; the optional events let the caller keep
+// the sweeps of consecutive calls in order (the sweeps wait for wait_event,
+// done_event is recorded after them, before the copy back).
 #include <cuda_runtime.h>
 
 #include "jacc_internal.h"
@@ -15,7 +17,8 @@ using namespace jacc;
 
 extern "C" jacc_status jacc_sweep_host(jacc_kernel h, const void* u_host, void* result_host, void* u0, void* u1,
                                        int32_t nsweeps, double* resid_dev, double* resid_host, uint32_t flags,
-                                       uintptr_t stream, int32_t* final_buf) {
+                                       uintptr_t stream, uintptr_t wait_event, uintptr_t done_event,
+                                       int32_t* final_buf) {
   if (!h) return fail(JACC_ERR_INVALID_ARG, "NULL handle");
   if (!u_host || !result_host) return fail(JACC_ERR_INVALID_ARG, "NULL host buffer");
   if (resid_host && !resid_dev) return fail(JACC_ERR_INVALID_ARG, "resid_host needs resid_dev");
@@ -28,9 +31,17 @@ extern "C" jacc_status jacc_sweep_host(jacc_kernel h, const void* u_host, void* 
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   st = cuda_check(cudaMemcpyAsync(u0, u_host, bytes, cudaMemcpyHostToDevice, s), "copy of the input field");
   if (st) return st;
+  if (wait_event) {
+    st = cuda_check(cudaStreamWaitEvent(s, reinterpret_cast<cudaEvent_t>(wait_event), 0), "wait before the sweeps");
+    if (st) return st;
+  }
   int32_t fb = 0;
   st = jacc_sweep(h, u0, u1, nsweeps, resid_dev, flags, stream, &fb);
   if (st) return st;
+  if (done_event) {
+    st = cuda_check(cudaEventRecord(reinterpret_cast<cudaEvent_t>(done_event), s), "record after the sweeps");
+    if (st) return st;
+  }
   st = cuda_check(cudaMemcpyAsync(result_host, fb ? u1 : u0, bytes, cudaMemcpyDeviceToHost, s), "copy of the result");
   if (st) return st;
   if (resid_host) {

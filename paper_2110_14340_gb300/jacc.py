@@ -112,7 +112,8 @@ SIGNATURES = {
     "jacc_launch": ([P, P, P, P, C.c_size_t], C.c_int32),
     "jacc_launch_static": ([P, P, P, P, C.c_size_t], C.c_int32),
     "jacc_sweep": ([P, P, P, C.c_int32, P, C.c_uint32, C.c_size_t, P], C.c_int32),
-    "jacc_sweep_host": ([P, P, P, P, P, C.c_int32, P, P, C.c_uint32, C.c_size_t, P], C.c_int32),
+    "jacc_sweep_host": ([P, P, P, P, P, C.c_int32, P, P, C.c_uint32, C.c_size_t, C.c_size_t, C.c_size_t, P],
+                        C.c_int32),
     "jacc_sweep_until": ([P, P, P, C.c_int32, C.c_double, P, P, C.c_size_t], C.c_int32),
     "jacc_sweep_coeffs": ([P, P, P, C.c_int32, P, C.c_int32, P, C.c_uint32, C.c_size_t, P], C.c_int32),
     "jacc_sched_create": ([C.c_int32, C.c_uint32, C.c_size_t, P], C.c_int32),
@@ -384,12 +385,14 @@ def _host_field(k, t, name):
     return t.data_ptr()
 
 
-def sweep_host(k, u_host, result_host, u0, u1, nsweeps, resid=None, resid_host=None, graph=True, stream=None):
+def sweep_host(k, u_host, result_host, u0, u1, nsweeps, resid=None, resid_host=None, graph=True, stream=None,
+               wait_event=None, done_event=None):
     """jacc_sweep_host: copy u_host (CPU tensor; pinned for asynchronous copies) into
     u0, run the sequence, copy the result field into result_host (and the residuals
-    into resid_host, a CPU float64 tensor, which needs resid).  Returns 0 if the
-    device result is in u0, 1 if in u1.  The host tensors must stay alive until the
-    stream has run the copies."""
+    into resid_host, a CPU float64 tensor, which needs resid).  The sweeps wait for
+    wait_event and done_event is recorded after them (torch.cuda.Event, optional).
+    Returns 0 if the device result is in u0, 1 if in u1.  The host tensors must stay
+    alive until the stream has run the copies."""
     import torch
     if resid is not None and resid.numel() < nsweeps:
         raise ValueError("resid needs nsweeps elements")
@@ -402,8 +405,22 @@ def sweep_host(k, u_host, result_host, u0, u1, nsweeps, resid=None, resid_host=N
     fb = C.c_int32(-1)
     _check(lib().jacc_sweep_host(k.handle, _host_field(k, u_host, "u_host"), _host_field(k, result_host, "result_host"),
                                  _field(k, u0, "u0"), _field(k, u1, "u1"), nsweeps, _resid(resid), rh,
-                                 SWEEP_GRAPH if graph else 0, _stream(stream), C.byref(fb)))
+                                 SWEEP_GRAPH if graph else 0, _stream(stream), _event(wait_event),
+                                 _event(done_event, create=True), C.byref(fb)))
     return fb.value
+
+
+def _event(e, create=False):
+    """A torch.cuda.Event as the cudaEvent_t integer (0 for None).  torch creates an
+    event on its first record: one never recorded is nothing to wait for, and one
+    the library is to record is created here first."""
+    if e is None:
+        return 0
+    if e.cuda_event == 0:
+        if not create:
+            return 0
+        e.record()
+    return e.cuda_event
 
 
 def sweep_coeffs(k, u0, u1, nsweeps, fields, resid=None, graph=True, stream=None):

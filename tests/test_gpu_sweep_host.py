@@ -76,6 +76,32 @@ def test_two_streams_two_buffer_sets_overlap_correctly():
         assert np.array_equal(outs[i].numpy().view(np.int64), want[i].view(np.int64)), i
 
 
+def test_events_keep_the_sweeps_of_consecutive_calls_in_order():
+    # the bench's whole-job loop: two streams, two buffer sets, each call's
+    # sweeps wait for the previous call's; results as if run one by one
+    side, n = 48, 10
+    k = jacc.Kernel(jacc.STENCIL_7PT, jacc.F64, side, side, side, coeffs=(0.125,))
+    hosts = [inputs.heat3d_field(side, seed=80 + i) for i in range(5)]
+    want = [device_reference(k, h, n) for h in hosts]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    done = [torch.cuda.Event(), torch.cuda.Event()]
+    sets = [(torch.empty((side,) * 3, dtype=torch.float64, device="cuda"),
+             torch.empty((side,) * 3, dtype=torch.float64, device="cuda"),
+             torch.zeros(n, dtype=torch.float64, device="cuda")) for _ in range(2)]
+    ins = [torch.from_numpy(h.copy()).pin_memory() for h in hosts]
+    outs = [torch.empty_like(t).pin_memory() for t in ins]
+    res = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in hosts]
+    torch.cuda.synchronize()
+    for i in range(5):
+        d0, d1, r = sets[i % 2]
+        jacc.sweep_host(k, ins[i], outs[i], d0, d1, n, r, res[i], stream=streams[i % 2],
+                        wait_event=done[(i + 1) % 2] if i else None, done_event=done[i % 2])
+    torch.cuda.synchronize()
+    for i in range(5):
+        assert np.array_equal(outs[i].numpy().view(np.int64), want[i][0].view(np.int64)), i
+        assert np.array_equal(res[i].numpy(), want[i][1]), i
+
+
 def test_sweep_host_argument_errors():
     side = 16
     k = jacc.Kernel(jacc.STENCIL_7PT, jacc.F64, side, side, side, coeffs=(0.125,))
