@@ -434,6 +434,14 @@ typedef struct {
 
 jacc_status jacc_autotune(const jacc_kernel_desc* desc, void* u0, void* u1, int32_t sweeps_per_rep, int32_t reps,
                           uintptr_t stream, jacc_tune_result* out);
+/* jacc_autotune restricted to the ntiles tile ids in `tiles` (host array,
+ * each in [0, JACC_NUM_TILES)): only those are timed (out->valid[t] = 1 for
+ * the timed tiles that fit the shape, 0 for all others), and the fastest of
+ * them is remembered for the shape.  INVALID_ARG for an empty list or an id
+ * out of range, UNSUPPORTED if none of them fits. */
+jacc_status jacc_autotune_tiles(const jacc_kernel_desc* desc, void* u0, void* u1, int32_t sweeps_per_rep,
+                                int32_t reps, uintptr_t stream, const int32_t* tiles, int32_t ntiles,
+                                jacc_tune_result* out);
 /* Forget every remembered autotuner pick. */
 jacc_status jacc_autotune_forget(void);
 
@@ -467,6 +475,11 @@ jacc_status jacc_autotune_forget(void);
  *               u0/u1 (needed then) when the side lies outside the range or
  *               the top-2 gap is below the margin.  *used_fallback tells
  *               which.  The chosen tile is remembered for the shape.
+ * choose_topk : the model as a filter: the k valid tiles with the lowest
+ *               predicted time for `desc` are timed on u0/u1 (required; their
+ *               contents change) by jacc_autotune_tiles and the fastest is
+ *               returned and remembered for the shape.  k >= the number of
+ *               valid tiles is the exhaustive search.
  * save / load : parameters and range in a small binary file ("JACCMLP1"). */
 typedef struct jacc_costmodel_s* jacc_costmodel;
 
@@ -484,6 +497,8 @@ jacc_status jacc_costmodel_pick(jacc_costmodel m, const float* feats_dev, const 
 jacc_status jacc_costmodel_set_range(jacc_costmodel m, double side_lo, double side_hi, double margin);
 jacc_status jacc_costmodel_choose(jacc_costmodel m, const jacc_kernel_desc* desc, void* u0, void* u1, uintptr_t stream,
                                   int32_t* tile, int32_t* used_fallback);
+jacc_status jacc_costmodel_choose_topk(jacc_costmodel m, const jacc_kernel_desc* desc, void* u0, void* u1,
+                                       uintptr_t stream, int32_t k, int32_t* tile);
 jacc_status jacc_costmodel_save(jacc_costmodel m, const char* path);
 jacc_status jacc_costmodel_load(jacc_costmodel m, const char* path);
 jacc_status jacc_costmodel_release(jacc_costmodel m);

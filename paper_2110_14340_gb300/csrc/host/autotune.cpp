@@ -48,8 +48,10 @@ void remember_tile(const jacc_kernel_desc& d, int tile) {
 
 using namespace jacc;
 
-extern "C" jacc_status jacc_autotune(const jacc_kernel_desc* desc, void* u0, void* u1, int32_t sweeps_per_rep,
-                                     int32_t reps, uintptr_t stream, jacc_tune_result* out) {
+// Times the tiles with want[t] set (each valid one), fills `out`, remembers
+// the fastest for the shape.
+static jacc_status autotune_subset(const jacc_kernel_desc* desc, void* u0, void* u1, int32_t sweeps_per_rep,
+                                   int32_t reps, uintptr_t stream, const bool* want, jacc_tune_result* out) {
   if (!desc || !out || sweeps_per_rep < 1 || reps < 1) return fail(JACC_ERR_INVALID_ARG, "bad autotune arguments");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   cudaEvent_t e0, e1;
@@ -68,7 +70,7 @@ extern "C" jacc_status jacc_autotune(const jacc_kernel_desc* desc, void* u0, voi
     jacc_kernel_desc d = *desc;
     d.tile_id = t;
     d.flags &= ~JACC_SPEC_JIT;
-    if (!tile_valid(d, t)) continue;
+    if (!want[t] || !tile_valid(d, t)) continue;
     jacc_kernel k = nullptr;
     st = jacc_specialize(&d, &k);
     if (st) break;
@@ -100,6 +102,26 @@ extern "C" jacc_status jacc_autotune(const jacc_kernel_desc* desc, void* u0, voi
   std::lock_guard<std::mutex> lock(global_mutex());
   tune_cache()[shape_key(*desc)] = out->best_tile;
   return ok();
+}
+
+extern "C" jacc_status jacc_autotune(const jacc_kernel_desc* desc, void* u0, void* u1, int32_t sweeps_per_rep,
+                                     int32_t reps, uintptr_t stream, jacc_tune_result* out) {
+  bool all[JACC_NUM_TILES];
+  std::fill(all, all + JACC_NUM_TILES, true);
+  return autotune_subset(desc, u0, u1, sweeps_per_rep, reps, stream, all, out);
+}
+
+extern "C" jacc_status jacc_autotune_tiles(const jacc_kernel_desc* desc, void* u0, void* u1, int32_t sweeps_per_rep,
+                                           int32_t reps, uintptr_t stream, const int32_t* tiles, int32_t ntiles,
+                                           jacc_tune_result* out) {
+  if (!tiles || ntiles < 1) return fail(JACC_ERR_INVALID_ARG, "no tiles to time");
+  bool want[JACC_NUM_TILES];
+  std::fill(want, want + JACC_NUM_TILES, false);
+  for (int32_t i = 0; i < ntiles; ++i) {
+    if (tiles[i] < 0 || tiles[i] >= JACC_NUM_TILES) return fail(JACC_ERR_INVALID_ARG, "tile id out of range");
+    want[tiles[i]] = true;
+  }
+  return autotune_subset(desc, u0, u1, sweeps_per_rep, reps, stream, want, out);
 }
 
 extern "C" jacc_status jacc_autotune_forget(void) {

@@ -10,6 +10,7 @@
 // predictions are closer than a margin.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -278,6 +279,44 @@ extern "C" jacc_status jacc_costmodel_choose(jacc_costmodel h, const jacc_kernel
   *tile = pick;
   *used_fallback = 0;
   remember_tile(*desc, pick);
+  return ok();
+}
+
+extern "C" jacc_status jacc_costmodel_choose_topk(jacc_costmodel h, const jacc_kernel_desc* desc, void* u0, void* u1,
+                                                  uintptr_t stream, int32_t k, int32_t* tile) {
+  if (!h || !desc || !tile || !u0 || !u1 || k < 1) return fail(JACC_ERR_INVALID_ARG, "bad choose_topk arguments");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const double vol = static_cast<double>(desc->nx) * desc->ny * desc->nz;
+  const double side = desc->stencil == JACC_STENCIL_5PT ? std::sqrt(vol) : std::cbrt(vol);
+  float feats[JACC_NUM_TILES * 4];
+  int valid[JACC_NUM_TILES];
+  for (int t = 0; t < JACC_NUM_TILES; ++t) {
+    jacc_costmodel_features(desc->stencil, side, desc->dtype, t, feats + 4 * t);
+    valid[t] = tile_valid(*desc, t) ? 1 : 0;
+  }
+  float pred[JACC_NUM_TILES];
+  jacc_status st = ok();
+  float* d_feat = nullptr;
+  st = cuda_check(cudaMalloc(reinterpret_cast<void**>(&d_feat), sizeof(feats) + sizeof(pred)), "cudaMalloc(topk)");
+  if (st) return st;
+  float* d_pred = d_feat + JACC_NUM_TILES * 4;
+  st = cuda_check(cudaMemcpyAsync(d_feat, feats, sizeof(feats), cudaMemcpyHostToDevice, s), "upload features");
+  if (!st) st = jacc_costmodel_predict(h, d_feat, JACC_NUM_TILES, d_pred, stream);
+  if (!st) st = cuda_check(cudaMemcpyAsync(pred, d_pred, sizeof(pred), cudaMemcpyDeviceToHost, s), "read predictions");
+  if (!st) st = cuda_check(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  cudaFree(d_feat);
+  if (st) return st;
+  // the k valid tiles with the lowest predicted time (ties to the lower id)
+  std::vector<int32_t> order;
+  for (int t = 0; t < JACC_NUM_TILES; ++t)
+    if (valid[t]) order.push_back(t);
+  if (order.empty()) return fail(JACC_ERR_UNSUPPORTED, "no tile configuration fits this shape");
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return pred[a] < pred[b]; });
+  if (static_cast<int32_t>(order.size()) > k) order.resize(static_cast<size_t>(k));
+  jacc_tune_result r;
+  st = jacc_autotune_tiles(desc, u0, u1, 2, 3, stream, order.data(), static_cast<int32_t>(order.size()), &r);
+  if (st) return st;
+  *tile = r.best_tile;
   return ok();
 }
 

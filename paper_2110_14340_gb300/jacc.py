@@ -133,6 +133,7 @@ SIGNATURES = {
     "jacc_batch_tune": ([P, C.c_int32, C.c_size_t, P, P], C.c_int32),
     "jacc_batch_release": ([P], C.c_int32),
     "jacc_autotune": ([P, P, P, C.c_int32, C.c_int32, C.c_size_t, P], C.c_int32),
+    "jacc_autotune_tiles": ([P, P, P, C.c_int32, C.c_int32, C.c_size_t, P, C.c_int32, P], C.c_int32),
     "jacc_autotune_forget": ([], C.c_int32),
     "jacc_costmodel_features": ([C.c_int32, C.c_double, C.c_int32, C.c_int32, P], C.c_int32),
     "jacc_costmodel_create": ([P, C.c_uint64, P], C.c_int32),
@@ -144,6 +145,7 @@ SIGNATURES = {
     "jacc_costmodel_pick": ([P, P, P, C.c_int32, P, P, P, C.c_size_t], C.c_int32),
     "jacc_costmodel_set_range": ([P, C.c_double, C.c_double, C.c_double], C.c_int32),
     "jacc_costmodel_choose": ([P, P, P, P, C.c_size_t, P, P], C.c_int32),
+    "jacc_costmodel_choose_topk": ([P, P, P, P, C.c_size_t, C.c_int32, P], C.c_int32),
     "jacc_costmodel_save": ([P, C.c_char_p], C.c_int32),
     "jacc_costmodel_load": ([P, C.c_char_p], C.c_int32),
     "jacc_costmodel_release": ([P], C.c_int32),
@@ -614,6 +616,16 @@ def autotune(k_args, u0, u1, sweeps_per_rep=2, reps=3, stream=None):
     return dict(ms=list(r.ms), valid=[bool(v) for v in r.valid], best_tile=r.best_tile, best_ms=r.best_ms)
 
 
+def autotune_tiles(k_args, u0, u1, tiles, sweeps_per_rep=2, reps=3, stream=None):
+    """autotune restricted to the tile ids in `tiles`; same result dict (untimed tiles invalid)."""
+    k = Desc(**dict(k_args, tile_id=-1))
+    r = TuneResult()
+    arr = (C.c_int32 * len(tiles))(*[int(t) for t in tiles])
+    _check(lib().jacc_autotune_tiles(C.byref(k.desc), _field(k, u0, "u0"), _field(k, u1, "u1"), sweeps_per_rep, reps,
+                                     _stream(stream), arr, len(tiles), C.byref(r)))
+    return dict(ms=list(r.ms), valid=[bool(v) for v in r.valid], best_tile=r.best_tile, best_ms=r.best_ms)
+
+
 def autotune_forget():
     _check(lib().jacc_autotune_forget())
 
@@ -713,6 +725,14 @@ class CostModel:
         _check(lib().jacc_costmodel_choose(self.handle, C.byref(k.desc), p0, p1, _stream(stream), C.byref(t),
                                            C.byref(fb)))
         return t.value, bool(fb.value)
+
+    def choose_topk(self, k_args, u0, u1, k, stream=None):
+        """The fastest of the model's k best-predicted tiles, timed on u0/u1."""
+        d = Desc(**dict(k_args, tile_id=-1))
+        t = C.c_int32(-1)
+        _check(lib().jacc_costmodel_choose_topk(self.handle, C.byref(d.desc), _field(d, u0, "u0"),
+                                                _field(d, u1, "u1"), _stream(stream), int(k), C.byref(t)))
+        return t.value
 
     def save(self, path):
         _check(lib().jacc_costmodel_save(self.handle, path.encode()))

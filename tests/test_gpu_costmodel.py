@@ -127,6 +127,40 @@ def test_autotuner_remembers_its_pick():
     jacc.autotune_forget()
 
 
+def test_autotune_tiles_times_only_the_listed_tiles():
+    nx = ny = nz = 64
+    a = torch.rand(nz, ny, nx, dtype=torch.float64, device="cuda")
+    b = torch.empty_like(a)
+    jacc.autotune_forget()
+    args = dict(stencil=7, dtype=64, nx=nx, ny=ny, nz=nz, coeffs=(0.125,))
+    r = jacc.autotune_tiles(args, a, b, [1, 3, 9], sweeps_per_rep=1, reps=3)
+    assert [t for t in range(24) if r["valid"][t]] == [1, 3, 9]
+    assert all(math.isinf(r["ms"][t]) for t in range(24) if t not in (1, 3, 9))
+    assert r["best_tile"] in (1, 3, 9) and r["best_ms"] == min(r["ms"][t] for t in (1, 3, 9))
+    assert jacc.Kernel(**args).info()["tile_id"] == r["best_tile"]
+    with pytest.raises(jacc.JaccError):
+        jacc.autotune_tiles(args, a, b, [24])
+    jacc.autotune_forget()
+
+
+def test_choose_topk_times_the_models_best_ranked_tiles():
+    m = jacc.CostModel(seed=5)
+    nx = ny = nz = 64
+    args = dict(stencil=7, dtype=64, nx=nx, ny=ny, nz=nz, coeffs=(0.125,))
+    a = torch.rand(nz, ny, nx, dtype=torch.float64, device="cuda")
+    b = torch.empty_like(a)
+    feats = torch.tensor([jacc.features(7, float(nx), 64, t) for t in range(24)], dtype=torch.float32,
+                         device="cuda").view(1, 24, 4)
+    valid = torch.ones(1, 24, dtype=torch.int32, device="cuda")
+    pred, _, _ = m.pick(feats, valid)
+    top3 = [int(t) for t in np.argsort(pred.cpu().numpy()[0], kind="stable")[:3]]
+    jacc.autotune_forget()
+    t = m.choose_topk(args, a, b, 3)
+    assert t in top3
+    assert jacc.Kernel(**args).info()["tile_id"] == t
+    jacc.autotune_forget()
+
+
 def test_choose_falls_back_outside_the_training_range():
     m = jacc.CostModel(seed=5)
     m.set_range(256.0, 512.0, 0.0)
