@@ -233,8 +233,10 @@ def main():
     ap.add_argument("--out", default=None)
     ap.add_argument("--train-per-pair", type=int, default=14)
     ap.add_argument("--heldout", type=int, default=200)
-    ap.add_argument("--epochs", type=int, default=8000)
+    ap.add_argument("--epochs", type=int, default=40000)
     ap.add_argument("--max-side", type=int, default=1024)
+    ap.add_argument("--lr", type=float, default=3e-4)
+    ap.add_argument("--seed", type=int, default=5)
     ap.add_argument("--tables", default=None,
                     help="reuse the timing tables of an earlier --out file instead of collecting them")
     args = ap.parse_args()
@@ -260,12 +262,12 @@ def main():
         test_table = collect(test_q, bufs, log=print)
         t_collect = time.perf_counter() - t0
     X, Y = xy(train_table)
-    model = jacc.CostModel(seed=5)
-    loss, t_train = fit(model, X, Y, args.epochs)
+    model = jacc.CostModel(seed=args.seed)
+    loss, t_train = fit(model, X, Y, args.epochs, args.lr)
     margin = margin_from_training(model, X, Y)
     res, _ = evaluate(model, train_table, test_table, margin)
     res.update(train_samples=int(len(Y)), final_train_mse=loss, train_seconds=t_train, collect_seconds=t_collect,
-               epochs=args.epochs, train_sides=tr, heldout_sides=ho)
+               epochs=args.epochs, lr=args.lr, seed=args.seed, train_sides=tr, heldout_sides=ho)
     print(json.dumps(res, indent=1))
     if args.out:
         with open(args.out, "w") as f:
