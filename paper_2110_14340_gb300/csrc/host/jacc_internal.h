@@ -56,6 +56,7 @@ struct Kernel {
   double compile_ms = 0.0;
   const void* func = nullptr;   // kernel entry (host stub or cudaKernel_t)
   const void* func_out = nullptr;  // entry for the first/last sweep of a fixed-point sequence (FP64 in or out)
+  const void* func_last = nullptr;  // constant-folded FP64 last sweep that converts only on store (or null)
   cudaLibrary_t lib = nullptr;  // NVRTC module, if jit
   dim3 grid, block;
   int tblock = 1;

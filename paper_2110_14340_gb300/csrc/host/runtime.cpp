@@ -253,13 +253,20 @@ static std::string jit_source(const Kernel& k) {
                 "%s* __restrict__ v, JParams rt, double* resid, const u64* maxword, int flags) {\n"
                 "  const JFold f{};\n"
                 "  %s<%s, %d, %d, %d, %d, %s>(u, v, f, rt, resid, maxword, flags);\n"
+                "}\n"
+                "extern \"C\" __global__ void __launch_bounds__(%d, (SweepMinBlocksLast<%d, %s, %d, %d, %d>::value))\n"
+                "jacc_jit_last(const %s* __restrict__ u, "
+                "%s* __restrict__ v, JParams rt, double* resid, const u64* maxword, int flags) {\n"
+                "  const JFold f{};\n"
+                "  %s<%s, %d, %d, %d, %d, %s>(u, v, f, rt, resid, maxword, JFX_OUT_F64);\n"
                 "}\n",
                 (long long)p.nx, (long long)p.ny, (long long)p.nz, p.c0, p.c1, p.c2, p.c3, (long long)p.fa,
                 (long long)p.fb, (long long)p.fw0, (long long)p.fw1, (long long)p.fw2, (long long)p.fw3, p.fk, p.fpath,
                 // small (L2-resident) 2D grids: the prefetching march
                 (k.desc.stencil == 5 && k.desc.nx * k.desc.ny <= (int64_t(1) << 17)) ? "true" : "false",
                 c.bx * c.by, k.desc.stencil, T, c.bx, c.by, k.vec, T, T, entry, T, c.bx, c.by, k.vec, zc, c.bx * c.by,
-                k.desc.stencil, T, c.bx, c.by, k.vec, edge, T, T, entry, T, c.bx, c.by, k.vec, zc, edge);
+                k.desc.stencil, T, c.bx, c.by, k.vec, edge, T, T, entry, T, c.bx, c.by, k.vec, zc, edge, c.bx * c.by,
+                k.desc.stencil, T, c.bx, c.by, k.vec, T, T, entry, T, c.bx, c.by, k.vec, zc, edge);
   return std::string(device_source()) + buf;
 }
 
@@ -359,12 +366,14 @@ extern "C" jacc_status jacc_specialize(const jacc_kernel_desc* desc, jacc_kernel
                    static_cast<unsigned>((desc->nz + 63) / 64));
     k->func_out = k->func;
   } else if (desc->flags & JACC_SPEC_JIT) {
-    static const char* const names[2] = {"jacc_jit", "jacc_jit_out"};
-    const void* f[2] = {nullptr, nullptr};
-    st = jit_compile(jit_source(*k), names, 2, &k->lib, f, &k->compile_ms);
+    static const char* const names[3] = {"jacc_jit", "jacc_jit_out", "jacc_jit_last"};
+    const void* f[3] = {nullptr, nullptr, nullptr};
+    st = jit_compile(jit_source(*k), names, 3, &k->lib, f, &k->compile_ms);
     if (st) return st;
     k->func = f[0];
     k->func_out = f[1];
+    // the store-only converting kernel: FP64 fixed-point sequences only
+    if (desc->dtype == 64) k->func_last = f[2];
     k->jit = true;
   } else {
     k->func = table_entry(desc->stencil, desc->dtype, tile, false);
@@ -486,7 +495,8 @@ cudaError_t launch_sweep_kernel(const Kernel& k, const void* u, void* v, double*
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelExC(&cfg, (flags & (kFxIn | kFxOut)) ? k.func_out : k.func, const_cast<void**>(args));
+  const void* f = flags == kFxOut && k.func_last ? k.func_last : ((flags & (kFxIn | kFxOut)) ? k.func_out : k.func);
+  return cudaLaunchKernelExC(&cfg, f, const_cast<void**>(args));
 }
 
 jacc_status check_buffers(const Kernel& k, const void* a, const void* b) {

@@ -2285,6 +2285,14 @@ template <int STENCIL, class T, int BX, int BY, int V, bool EDGE, bool FOLDED> s
   static constexpr int value = heat_staged_fp64 ? (EDGE ? 5 : (FOLDED ? 7 : 6)) : 0;
 };
 
+// The constant-folded last sweep of a sequence that does not convert on load
+// (the flags are the constant JFX_OUT_F64, so the load conversion is compiled
+// out): 80 registers at a bound of 6 CTAs per SM against 96 at 5 for the
+// kernel that converts both ways (staged FP64 7-point, 32 x 4 threads).
+template <int STENCIL, class T, int BX, int BY, int V> struct SweepMinBlocksLast {
+  static constexpr int value = (STENCIL == 7 && sizeof(T) == 8 && BX == 32 && BY == 4 && V == 2) ? 6 : 0;
+};
+
 // Kernel templates instantiated by the precompiled library (P = JParams).
 template <class T, int BX, int BY, int V, int ZC, bool EDGE>
 __global__ void __launch_bounds__(BX * BY) jacc_k_jacobi2d(const T* __restrict__ u, T* __restrict__ v, JParams p,
