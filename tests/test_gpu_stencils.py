@@ -269,6 +269,21 @@ def test_box27_f64(orc, tile):
     assert np.max(np.abs(gs - np.array(sums))) <= 1e-12 * float(np.sum(np.abs(o)))
 
 
+def test_box27_f64_large_field_with_input_conversion(orc):
+    # at least 2^22 points: the sequence converts u0 in place before its first
+    # sweep, which then runs the intermediate kernel (plain and folded)
+    nz, ny, nx = 64, 256, 258  # 4.23 M points
+    u = inputs.box27_field(nx, ny, nz, seed=19).astype(np.float64)
+    w64 = W.astype(np.float64)
+    o, sums = orc.box27_run_f64(u, w64, 3)
+    for jit in (False, True):
+        k = jacc.Kernel(jacc.STENCIL_27PT, jacc.F64, nx, ny, nz, coeffs=tuple(w64), jit=jit)
+        assert k.info()["fixed_point"]
+        g, gs = run(k, u, 3)
+        assert nerr(g, o) <= TOL64
+        assert np.max(np.abs(gs - np.array(sums))) <= 1e-12 * float(np.sum(np.abs(o)))
+
+
 def test_box27_impulse_response_exact():
     nz, ny, nx = 6, 7, 8
     u = np.zeros((nz, ny, nx), dtype=np.float32)
