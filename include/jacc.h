@@ -372,10 +372,13 @@ jacc_status jacc_sweep_until(jacc_kernel k, void* u0, void* u1, int32_t max_swee
  * The runtime's asynchronous execution (§3.2.1 tracks the data range each
  * kernel touches; §4 runs kernels without host synchronisation; §6.1 uses 16
  * queues): a scheduler owns a pool of nstreams CUDA streams (1..64) and runs
- * each submitted task on one of them after cudaStreamWaitEvent on every
- * earlier task whose memory ranges conflict with its own (read after write,
- * write after read, write after write on overlapping bytes); tasks without a
- * conflict run concurrently.  A task that depends on the last task of a
+ * each submitted task on one of them after cudaStreamWaitEvent on, for every
+ * byte the task touches, the last earlier task that wrote it and, for bytes
+ * it writes, the earlier tasks that read them since that write (read after
+ * write, write after read, write after write); every other earlier task with
+ * overlapping ranges is ordered before one of those, and tasks without a
+ * conflict run concurrently.  The ranges are kept in an interval map, so a
+ * submission costs O(log n) plus the segments it overlaps.  A task that depends on the last task of a
  * stream continues that stream; others take the next stream round-robin.
  * The pool starts after the work queued on `origin` when it is created;
  * jacc_sched_join makes a stream wait for every task.  Tasks completed on the
@@ -405,9 +408,9 @@ jacc_status jacc_sched_nest_begin(jacc_sched s, int32_t nloops, const jacc_loop*
                                   uintptr_t* stream_out);
 jacc_status jacc_sched_nest_end(jacc_sched s, int32_t task_id);
 /* The tasks task_id waited for (first max_deps of *ndeps, in id order) and
- * the index of its pool stream.  In live mode a conflicting task that had
- * already completed on the device when task_id was submitted is not listed
- * (it needed no wait); dry-run mode lists every conflicting earlier task. */
+ * the index of its pool stream.  In live mode such a task that had already
+ * completed on the device when task_id was submitted is not listed (it needed
+ * no wait); dry-run mode lists all of them. */
 jacc_status jacc_sched_task_info(jacc_sched s, int32_t task_id, int32_t* deps, int32_t max_deps, int32_t* ndeps,
                                  int32_t* stream_index);
 jacc_status jacc_sched_join(jacc_sched s, uintptr_t stream);

@@ -10,6 +10,13 @@
 // offset extremes of every array it touches), from a stencil sweep's two
 // fields, or from a copy's source and destination.
 //
+// Dependencies come from an interval map over the bytes tasks have touched:
+// disjoint segments, each holding its last writer and the tasks that read it
+// since.  A reading range depends on the last writers of the segments it
+// overlaps; a writing range also on their readers.  Those tasks are the only
+// ones a new task must wait for: every earlier conflicting task is ordered
+// before one of them already.  A query costs O(log n + segments overlapped).
+//
 // In dry-run mode no CUDA call is made: the scheduler only records each
 // task's dependencies and stream, so the dependency logic can be checked on
 // a host without a GPU.
@@ -17,6 +24,8 @@
 
 #include <algorithm>
 #include <cstring>
+#include <iterator>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -39,11 +48,76 @@ struct Task {
   bool retired = false;        // completed on the device: no later task needs to wait for it
 };
 
-bool conflict(const Task& a, const Task& b) {
-  for (const Range& x : a.ranges)
-    for (const Range& y : b.ranges)
-      if ((x.write || y.write) && x.lo < y.hi && y.lo < x.hi) return true;
-  return false;
+// A segment [key, hi) of touched bytes.
+struct Seg {
+  uint64_t hi;
+  int32_t writer;                // last task that wrote it (-1: none)
+  std::vector<int32_t> readers;  // tasks that read it since that write
+};
+typedef std::map<uint64_t, Seg> SegMap;
+
+// The first segment that overlaps [lo, ...).
+SegMap::iterator first_overlap(SegMap& m, uint64_t lo) {
+  auto it = m.upper_bound(lo);
+  if (it != m.begin()) {
+    auto p = std::prev(it);
+    if (p->second.hi > lo) return p;
+  }
+  return it;
+}
+
+// Splits the segment holding x, if any, so that a segment starts at x.
+void cut(SegMap& m, uint64_t x) {
+  auto it = m.upper_bound(x);
+  if (it == m.begin()) return;
+  --it;
+  if (it->first < x && x < it->second.hi) {
+    Seg right = it->second;
+    it->second.hi = x;
+    m.emplace(x, std::move(right));
+  }
+}
+
+// Records that task `id` reads (write = false) or writes [lo, hi).
+void record(SegMap& m, uint64_t lo, uint64_t hi, bool write, int32_t id) {
+  cut(m, lo);
+  cut(m, hi);
+  auto apply = [&](Seg& g) {
+    if (write) {
+      g.writer = id;
+      g.readers.clear();
+    } else if (std::find(g.readers.begin(), g.readers.end(), id) == g.readers.end()) {
+      g.readers.push_back(id);
+    }
+  };
+  uint64_t pos = lo;
+  auto it = m.lower_bound(lo);
+  while (pos < hi) {
+    if (it == m.end() || it->first > pos) {  // untouched bytes [pos, end)
+      const uint64_t end = (it == m.end() || it->first > hi) ? hi : it->first;
+      Seg g{end, -1, {}};
+      apply(g);
+      it = std::next(m.emplace_hint(it, pos, std::move(g)));
+      pos = end;
+      continue;
+    }
+    apply(it->second);
+    pos = it->second.hi;
+    ++it;
+  }
+  if (write) {  // the written segments now agree: merge them
+    auto a = m.find(lo);
+    while (a != m.end() && a->first < hi) {
+      auto b = std::next(a);
+      if (b != m.end() && b->first == a->second.hi && b->first < hi && b->second.writer == id &&
+          b->second.readers.empty()) {
+        a->second.hi = b->second.hi;
+        m.erase(b);
+      } else {
+        a = b;
+      }
+    }
+  }
 }
 
 }  // namespace
@@ -53,6 +127,7 @@ struct Sched {
   std::vector<cudaStream_t> streams;
   std::vector<int32_t> last_task;  // per stream: the last task placed on it (-1: none)
   std::vector<Task> tasks;
+  SegMap segs;            // the dependency index
   int32_t next_free = 0;  // round-robin cursor for tasks without dependencies
   std::mutex mu;
 };
@@ -63,7 +138,17 @@ static jacc_status place(Sched& s, std::vector<Range> ranges, int32_t* id_out, c
   Task t;
   t.ranges = std::move(ranges);
   const int32_t id = static_cast<int32_t>(s.tasks.size());
-  for (int32_t j = 0; j < id; ++j) {
+  std::vector<int32_t> cand;
+  for (const Range& r : t.ranges) {
+    if (r.lo >= r.hi) continue;
+    for (auto it = first_overlap(s.segs, r.lo); it != s.segs.end() && it->first < r.hi; ++it) {
+      if (it->second.writer >= 0) cand.push_back(it->second.writer);
+      if (r.write) cand.insert(cand.end(), it->second.readers.begin(), it->second.readers.end());
+    }
+  }
+  std::sort(cand.begin(), cand.end());
+  cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+  for (int32_t j : cand) {
     Task& o = s.tasks[j];
     if (o.retired) continue;
     if (!s.dry && !o.open && o.done && s.last_task[o.stream] != j && cudaEventQuery(o.done) == cudaSuccess) {
@@ -71,11 +156,10 @@ static jacc_status place(Sched& s, std::vector<Range> ranges, int32_t* id_out, c
       // the chain anchor)
       cudaEventDestroy(o.done);
       o.done = nullptr;
-      o.ranges.clear();
       o.retired = true;
       continue;
     }
-    if (conflict(t, o)) t.deps.push_back(j);
+    t.deps.push_back(j);
   }
   // stream: continue the chain of the latest dependency if it ends its
   // stream (no wait needed for it); otherwise the next stream round-robin
@@ -100,6 +184,12 @@ static jacc_status place(Sched& s, std::vector<Range> ranges, int32_t* id_out, c
     jacc_status e = cuda_check(cudaEventCreateWithFlags(&t.done, cudaEventDisableTiming), "cudaEventCreate");
     if (e) return e;
   }
+  // the task is placed: enter its ranges into the index (reads first, so a
+  // range both read and written ends as written)
+  for (const Range& r : t.ranges)
+    if (!r.write && r.lo < r.hi) record(s.segs, r.lo, r.hi, false, id);
+  for (const Range& r : t.ranges)
+    if (r.write && r.lo < r.hi) record(s.segs, r.lo, r.hi, true, id);
   s.last_task[st] = id;
   s.tasks.push_back(std::move(t));
   *id_out = id;
