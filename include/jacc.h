@@ -114,9 +114,12 @@ jacc_status jacc_region_analyze(int32_t nloops, const jacc_loop* loops, int32_t 
  * out: the extreme of c i_k over [lo_k, hi_k] is c hi_k or c lo_k, an affine
  * form in the outer indices (the paper's analysis covers rectangular ranges,
  * §4.1; this extends it to the nests its future work names).  An empty
- * outermost loop touches nothing.  JACC_ERR_UNSUPPORTED if some inner loop
- * is empty for some iteration of its outer loops (the elimination would then
- * need the loop's emptiness as a constraint); other errors as for
+ * outermost loop touches nothing.  An inner loop that is empty for some
+ * iterations of its outer loops, its extent following one outer index whose
+ * own bounds are constant (j = i .. 5 over i = 0 .. 9), first tightens that
+ * index's bounds to the iterations in which it runs (exact: the body runs
+ * nowhere else); JACC_ERR_UNSUPPORTED if the emptiness couples several
+ * indices or an index with affine bounds.  Other errors as for
  * jacc_region_analyze, plus JACC_ERR_OVERFLOW when an eliminated form leaves
  * int64. */
 typedef struct {

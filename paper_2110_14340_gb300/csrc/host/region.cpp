@@ -263,17 +263,65 @@ extern "C" jacc_status jacc_region_analyze_affine(int32_t nloops, const jacc_loo
   jacc_status st = check_refs(nrefs, refs, narrays, arrays);
   if (st) return st;
   std::memset(out, 0, sizeof(jacc_region) * static_cast<size_t>(narrays));
-  if (nloops > 0 && loops[0].hi < loops[0].lo) return jacc::ok();  // the nest never runs
-  // every inner loop must run for every iteration of its outer loops
-  for (int k = 1; k < nloops; ++k) {
+  // The body runs only where every loop is non-empty.  An inner loop k whose
+  // extent hi_k - lo_k = a i_m + b depends on one outer index i_m with
+  // constant bounds is non-empty exactly for i_m >= ceil(-b / a) (a > 0) or
+  // i_m <= floor(b / -a) (a < 0): tightening i_m's bounds to that range drops
+  // only outer iterations in which the body never runs, so the elimination
+  // below stays exact.  Repeated until no bound moves; emptiness that depends
+  // on several indices remains unsupported.
+  jacc_loop_affine L[JACC_MAX_LOOPS];
+  for (int k = 0; k < nloops; ++k) L[k] = loops[k];
+  auto floor_div = [](wide p, wide q) { return p >= 0 ? p / q : -((-p + q - 1) / q); };  // q > 0
+  for (int pass = 0; pass <= nloops; ++pass) {
+    if (nloops > 0 && L[0].hi < L[0].lo) return jacc::ok();  // the nest never runs
+    bool moved = false;
+    for (int k = 1; k < nloops; ++k) {
+      wide d[JACC_MAX_LOOPS];
+      for (int m = 0; m < k; ++m) d[m] = static_cast<wide>(L[k].hi_coef[m]) - L[k].lo_coef[m];
+      const wide b = static_cast<wide>(L[k].hi) - L[k].lo;
+      wide mn;
+      if (!affine_extreme(L, k, d, b, false, &mn)) return fail(JACC_ERR_OVERFLOW, "loop extent bound overflows int64");
+      if (mn >= 0) continue;
+      int var = -1, nvar = 0;
+      for (int m = 0; m < k; ++m)
+        if (d[m] != 0) {
+          var = m;
+          ++nvar;
+        }
+      if (nvar == 0) return jacc::ok();  // loop k never runs: the nest touches nothing
+      bool const_bounds = true;
+      for (int m = 0; m < JACC_MAX_LOOPS; ++m)
+        if (L[var].lo_coef[m] || L[var].hi_coef[m]) const_bounds = false;
+      if (nvar > 1 || !const_bounds)
+        return fail(JACC_ERR_UNSUPPORTED, "loop " + std::to_string(k) +
+                                              " is empty for some outer iterations in a way that couples several indices");
+      const wide a = d[var];
+      if (a > 0) {
+        const wide lo = -floor_div(b, a);  // ceil(-b / a)
+        if (lo > L[var].lo) {
+          L[var].lo = static_cast<int64_t>(lo);
+          moved = true;
+        }
+      } else {
+        const wide hi = floor_div(b, -a);
+        if (hi < L[var].hi) {
+          L[var].hi = static_cast<int64_t>(hi);
+          moved = true;
+        }
+      }
+      if (L[var].hi < L[var].lo) return jacc::ok();  // no outer iteration runs loop k
+    }
+    if (!moved) break;
+  }
+  for (int k = 1; k < nloops; ++k) {  // every loop now runs for every outer iteration left
     wide d[JACC_MAX_LOOPS];
-    for (int m = 0; m < k; ++m) d[m] = static_cast<wide>(loops[k].hi_coef[m]) - loops[k].lo_coef[m];
+    for (int m = 0; m < k; ++m) d[m] = static_cast<wide>(L[k].hi_coef[m]) - L[k].lo_coef[m];
     wide mn;
-    if (!affine_extreme(loops, k, d, static_cast<wide>(loops[k].hi) - loops[k].lo, false, &mn))
-      return fail(JACC_ERR_OVERFLOW, "loop extent bound overflows int64");
-    if (mn < 0)
+    if (!affine_extreme(L, k, d, static_cast<wide>(L[k].hi) - L[k].lo, false, &mn) || mn < 0)
       return fail(JACC_ERR_UNSUPPORTED, "loop " + std::to_string(k) + " is empty for some outer iterations");
   }
+  loops = L;
   for (int r = 0; r < nrefs; ++r) {
     const jacc_ref& R = refs[r];
     const jacc_array& A = arrays[R.array_id];

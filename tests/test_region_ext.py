@@ -84,7 +84,18 @@ def test_triangle_and_empty_cases(orc):
     st, got = jacc.region_analyze_affine([(3, 2, [], []), (0, 1, [0], [0])], refs, [[10, 10]])
     assert st == 0 and not got[0]["has_write"]
     # an inner loop empty for some outer iterations: j = i .. 5 with i up to 9
-    st, _ = jacc.region_analyze_affine([(0, 9, [], []), (0, 5, [1], [0])], refs, [[10, 10]])
+    # runs the body only for i <= 5; the outer bound is tightened to that
+    loops3 = [(0, 9, [], []), (0, 5, [1], [0])]
+    st, got = jacc.region_analyze_affine(loops3, refs, [[10, 10]])
+    ost, want = orc.region_enumerate_affine(loops3, refs, [[10, 10]])
+    assert st == 0 and ost == 0 and got == want and got[0]["whi"] == [5, 5]
+    # an inner loop that never runs: nothing is touched
+    st, got = jacc.region_analyze_affine([(2, 8, [], []), (9, 0, [0], [1])], refs, [[10, 10]])
+    assert st == 0 and not got[0]["has_write"]
+    # emptiness that couples two indices (k = i .. j - 1 over j = 0 .. 3):
+    # still unsupported
+    st, _ = jacc.region_analyze_affine([(0, 3, [], []), (0, 3, [0], [0]), (0, -1, [1, 0], [0, 1])],
+                                       [dict(array=0, coef=[[0, 0, 1]], off=[0])], [[10]])
     assert st == jacc.ERR_UNSUPPORTED
     # bounds may only depend on outer loops
     st, _ = jacc.region_analyze_affine([(0, 9, [0, 1], [0, 0])], [], [])
@@ -166,3 +177,41 @@ def test_widening_and_narrowing_triangles_match_enumeration(orc):
             st, got = jacc.region_analyze_affine(loops, refs, [[1000, 1000]])
             ost, want = orc.region_enumerate_affine(loops, refs, [[1000, 1000]])
             assert st == 0 and ost == 0 and got == want, (loops, refs)
+
+
+def test_inner_loops_empty_for_some_outer_iterations_match_enumeration(orc):
+    # inner bounds whose extent depends on one outer index with constant
+    # bounds (j = i .. c, j = c .. d - i, ...): the outer range is tightened to
+    # where the inner loop runs; the result must equal enumeration
+    rng = np.random.default_rng(4)
+    checked = 0
+    for trial in range(300):
+        n = int(rng.integers(2, 4))
+        loops = [(int(rng.integers(-3, 3)), int(rng.integers(3, 9)), [], [])]
+        for k in range(1, n):
+            m = int(rng.integers(0, k))  # the one outer index the extent follows
+            lc = [0] * k
+            hc = [0] * k
+            lc[m] = int(rng.integers(-2, 3))
+            hc[m] = int(rng.integers(-2, 3))
+            for q in range(k):  # other outer indices: same slope on both bounds
+                if q != m and rng.integers(0, 2):
+                    lc[q] = hc[q] = int(rng.integers(-1, 2))
+            lo = int(rng.integers(-4, 5))
+            loops.append((lo, lo + int(rng.integers(-3, 6)), lc, hc))
+        # the one-index rule needs that index's own bounds constant
+        if any(any(loops[m][2]) or any(loops[m][3]) for k in range(1, n) for m in range(k)
+               if (loops[k][3][m] - loops[k][2][m]) != 0):
+            continue
+        refs = random_refs(rng, n, 2, 1)
+        for r in refs:
+            r["off"] = [o + 200 for o in r["off"]]
+        st, got = jacc.region_analyze_affine(loops, refs, [[1000, 1000]])
+        ost, want = orc.region_enumerate_affine(loops, refs, [[1000, 1000]])
+        assert ost == 0
+        if st == jacc.ERR_UNSUPPORTED:
+            continue
+        assert st == 0, (trial, loops)
+        assert got == want, (trial, loops, refs)
+        checked += 1
+    assert checked >= 100
