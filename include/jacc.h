@@ -409,6 +409,13 @@ jacc_status jacc_sched_nest_begin(jacc_sched s, int32_t nloops, const jacc_loop*
                                   const jacc_ref* refs, int32_t narrays, const jacc_array* arrays,
                                   const uint64_t* base, const int32_t* elem_bytes, int32_t* task_id,
                                   uintptr_t* stream_out);
+/* The same for an affine (triangular) nest: its ranges come from
+ * jacc_region_analyze_affine, exact over the iterations that run, so a nest
+ * such as j = 0 .. i touches (and waits for) no more than its triangle. */
+jacc_status jacc_sched_nest_begin_affine(jacc_sched s, int32_t nloops, const jacc_loop_affine* loops, int32_t nrefs,
+                                         const jacc_ref* refs, int32_t narrays, const jacc_array* arrays,
+                                         const uint64_t* base, const int32_t* elem_bytes, int32_t* task_id,
+                                         uintptr_t* stream_out);
 jacc_status jacc_sched_nest_end(jacc_sched s, int32_t task_id);
 /* The tasks task_id waited for (first max_deps of *ndeps, in id order) and
  * the index of its pool stream.  In live mode such a task that had already

@@ -291,17 +291,11 @@ extern "C" jacc_status jacc_sched_copy(jacc_sched h, void* dst, const void* src,
   return finish(s, id);
 }
 
-extern "C" jacc_status jacc_sched_nest_begin(jacc_sched h, int32_t nloops, const jacc_loop* loops, int32_t nrefs,
-                                             const jacc_ref* refs, int32_t narrays, const jacc_array* arrays,
-                                             const uint64_t* base, const int32_t* elem_bytes, int32_t* task_id,
-                                             uintptr_t* stream_out) {
-  if (!h || !task_id || !stream_out || (narrays > 0 && (!base || !elem_bytes)))
-    return fail(JACC_ERR_INVALID_ARG, "NULL argument");
-  if (narrays < 0 || narrays > 64) return fail(JACC_ERR_INVALID_ARG, "narrays must be in [0, 64]");
+// A nest task from the regions its loop nest touches (analysed by the caller).
+static jacc_status nest_task(jacc_sched h, const std::vector<jacc_region>& reg, int32_t narrays, const uint64_t* base,
+                             const int32_t* elem_bytes, int32_t* task_id, uintptr_t* stream_out) {
   Sched& s = *reinterpret_cast<Sched*>(h);
-  std::vector<jacc_region> reg(static_cast<size_t>(narrays));
-  jacc_status st = jacc_region_analyze(nloops, loops, nrefs, refs, narrays, arrays, reg.data());
-  if (st) return st;
+  jacc_status st = ok();
   std::vector<Range> r;
   for (int32_t a = 0; a < narrays; ++a) {
     if (elem_bytes[a] < 1) return fail(JACC_ERR_INVALID_ARG, "elem_bytes must be >= 1");
@@ -322,6 +316,33 @@ extern "C" jacc_status jacc_sched_nest_begin(jacc_sched h, int32_t nloops, const
   *task_id = id;
   *stream_out = reinterpret_cast<uintptr_t>(cs);
   return ok();
+}
+
+extern "C" jacc_status jacc_sched_nest_begin(jacc_sched h, int32_t nloops, const jacc_loop* loops, int32_t nrefs,
+                                             const jacc_ref* refs, int32_t narrays, const jacc_array* arrays,
+                                             const uint64_t* base, const int32_t* elem_bytes, int32_t* task_id,
+                                             uintptr_t* stream_out) {
+  if (!h || !task_id || !stream_out || (narrays > 0 && (!base || !elem_bytes)))
+    return fail(JACC_ERR_INVALID_ARG, "NULL argument");
+  if (narrays < 0 || narrays > 64) return fail(JACC_ERR_INVALID_ARG, "narrays must be in [0, 64]");
+  std::vector<jacc_region> reg(static_cast<size_t>(narrays));
+  jacc_status st = jacc_region_analyze(nloops, loops, nrefs, refs, narrays, arrays, reg.data());
+  if (st) return st;
+  return nest_task(h, reg, narrays, base, elem_bytes, task_id, stream_out);
+}
+
+extern "C" jacc_status jacc_sched_nest_begin_affine(jacc_sched h, int32_t nloops, const jacc_loop_affine* loops,
+                                                    int32_t nrefs, const jacc_ref* refs, int32_t narrays,
+                                                    const jacc_array* arrays, const uint64_t* base,
+                                                    const int32_t* elem_bytes, int32_t* task_id,
+                                                    uintptr_t* stream_out) {
+  if (!h || !task_id || !stream_out || (narrays > 0 && (!base || !elem_bytes)))
+    return fail(JACC_ERR_INVALID_ARG, "NULL argument");
+  if (narrays < 0 || narrays > 64) return fail(JACC_ERR_INVALID_ARG, "narrays must be in [0, 64]");
+  std::vector<jacc_region> reg(static_cast<size_t>(narrays));
+  jacc_status st = jacc_region_analyze_affine(nloops, loops, nrefs, refs, narrays, arrays, reg.data());
+  if (st) return st;
+  return nest_task(h, reg, narrays, base, elem_bytes, task_id, stream_out);
 }
 
 extern "C" jacc_status jacc_sched_nest_end(jacc_sched h, int32_t task_id) {

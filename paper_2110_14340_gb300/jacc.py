@@ -120,6 +120,7 @@ SIGNATURES = {
     "jacc_sched_sweep": ([P, P, P, P, C.c_int32, P, P], C.c_int32),
     "jacc_sched_copy": ([P, P, P, C.c_uint64, P], C.c_int32),
     "jacc_sched_nest_begin": ([P, C.c_int32, P, C.c_int32, P, C.c_int32, P, P, P, P, P], C.c_int32),
+    "jacc_sched_nest_begin_affine": ([P, C.c_int32, P, C.c_int32, P, C.c_int32, P, P, P, P, P], C.c_int32),
     "jacc_sched_nest_end": ([P, C.c_int32], C.c_int32),
     "jacc_sched_task_info": ([P, C.c_int32, P, C.c_int32, P, P], C.c_int32),
     "jacc_sched_join": ([P, C.c_size_t], C.c_int32),
@@ -231,8 +232,7 @@ def _region_list(O, arrays):
     return out
 
 
-def region_analyze_affine(loops, refs, arrays):
-    """Triangular nests: loops [(lo, hi, lo_coef[], hi_coef[])], step 1; returns (status, [dict per array])."""
+def _affine_loops(loops):
     L = (LoopAffine * max(1, len(loops)))()
     for k, (lo, hi, lc, hc) in enumerate(loops):
         L[k].lo, L[k].hi = lo, hi
@@ -240,6 +240,12 @@ def region_analyze_affine(loops, refs, arrays):
             L[k].lo_coef[m] = c
         for m, c in enumerate(hc):
             L[k].hi_coef[m] = c
+    return L
+
+
+def region_analyze_affine(loops, refs, arrays):
+    """Triangular nests: loops [(lo, hi, lo_coef[], hi_coef[])], step 1; returns (status, [dict per array])."""
+    L = _affine_loops(loops)
     _, R, A = _nest([(0, 0, 1)] * len(loops), refs, arrays)
     O = (Region * max(1, len(arrays)))()
     st = lib().jacc_region_analyze_affine(len(loops), C.cast(L, P), len(refs), C.cast(R, P), len(arrays),
@@ -504,6 +510,19 @@ class Sched:
         _check(lib().jacc_sched_nest_begin(self.handle, len(loops), C.cast(L, P), len(refs), C.cast(R, P),
                                            len(arrays), C.cast(A, P), C.cast(B, P), C.cast(E, P), C.byref(t),
                                            C.byref(st)))
+        return t.value, st.value
+
+    def nest_begin_affine(self, loops, refs, arrays, bases, elem_bytes):
+        """nest_begin for an affine nest: loops [(lo, hi, lo_coef[], hi_coef[])], step 1."""
+        L = _affine_loops(loops)
+        _, R, A = _nest([(0, 0, 1)] * len(loops), refs, arrays)
+        B = (C.c_uint64 * max(1, len(arrays)))(*[int(b) for b in bases])
+        E = (C.c_int32 * max(1, len(arrays)))(*[int(e) for e in elem_bytes])
+        t = C.c_int32(-1)
+        st = C.c_size_t(0)
+        _check(lib().jacc_sched_nest_begin_affine(self.handle, len(loops), C.cast(L, P), len(refs), C.cast(R, P),
+                                                  len(arrays), C.cast(A, P), C.cast(B, P), C.cast(E, P), C.byref(t),
+                                                  C.byref(st)))
         return t.value, st.value
 
     def nest_end(self, task):

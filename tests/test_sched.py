@@ -163,3 +163,24 @@ def test_many_tasks_stay_cheap():
     print(f"20000 dry-run submissions: {dt:.2f} s")
     assert dt < 20.0
     s.release()
+
+
+def test_affine_nest_task_waits_only_for_its_triangle():
+    # A[10 + j - i] over the triangle j = 0 .. i, i = 0 .. 9 touches A[1..10];
+    # the rectangle i, j = 0 .. 9 would give A[1..19]
+    B = 0x5000000
+    ref = [dict(array=0, coef=[[-1, 1]], off=[10], write=True)]
+    s = jacc.Sched(nstreams=4, dry_run=True)
+    t0, _ = s.nest_begin_affine([(0, 9, [], []), (0, 0, [0], [1])], ref, [[32]], [B], [8])
+    s.nest_end(t0)
+    t1 = s.copy(B + 400, B + 120, 8 * 5)   # reads A[15..19], writes A[50..54]: disjoint from the triangle
+    assert s.info(t1)[0] == []
+    t2 = s.copy(B + 400, B + 8 * 8, 8 * 4)  # reads A[8..11]: after the triangle's writes of A[8..10]
+    assert s.info(t2)[0] == [t0, t1]        # (and after t1, which wrote the same destination)
+    s2 = jacc.Sched(nstreams=4, dry_run=True)
+    r0, _ = s2.nest_begin([(0, 9, 1), (0, 9, 1)], ref, [[32]], [B], [8])  # the rectangle's hull
+    s2.nest_end(r0)
+    r1 = s2.copy(B + 400, B + 120, 8 * 5)
+    assert s2.info(r1)[0] == [r0]
+    s.release()
+    s2.release()
