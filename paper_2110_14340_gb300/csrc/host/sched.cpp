@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <cstring>
 #include <iterator>
 #include <map>
@@ -128,13 +129,40 @@ struct Sched {
   std::vector<int32_t> last_task;  // per stream: the last task placed on it (-1: none)
   std::vector<Task> tasks;
   SegMap segs;            // the dependency index
+  std::vector<int32_t> pending;  // live mode: tasks not yet retired, in submission order
+  size_t pending_head = 0;       // first entry of `pending` still to check
   int32_t next_free = 0;  // round-robin cursor for tasks without dependencies
   std::mutex mu;
 };
 
 // Places a new task with the given ranges: finds its dependencies, picks a
 // stream and, in live mode, makes the stream wait for the dependencies.
+// Live mode: retires the oldest tasks that have completed on the device
+// (their events are destroyed; a later task that names them waits for
+// nothing).  Stops at the first task still running, so the cost stays
+// proportional to the tasks passed.  A stream's last task (the anchor of its
+// chain) and an open nest task are passed over here; they are retired later
+// when a new task names them, or freed with the scheduler.
+static void retire_completed(Sched& s) {
+  while (s.pending_head < s.pending.size()) {
+    const int32_t j = s.pending[s.pending_head];
+    Task& o = s.tasks[j];
+    if (!o.retired && !o.open && o.done && s.last_task[o.stream] != j) {
+      if (cudaEventQuery(o.done) != cudaSuccess) break;
+      cudaEventDestroy(o.done);
+      o.done = nullptr;
+      o.retired = true;
+    }
+    ++s.pending_head;
+  }
+  if (s.pending_head > 4096 && s.pending_head * 2 > s.pending.size()) {
+    s.pending.erase(s.pending.begin(), s.pending.begin() + static_cast<std::ptrdiff_t>(s.pending_head));
+    s.pending_head = 0;
+  }
+}
+
 static jacc_status place(Sched& s, std::vector<Range> ranges, int32_t* id_out, cudaStream_t* stream_out) {
+  if (!s.dry) retire_completed(s);
   Task t;
   t.ranges = std::move(ranges);
   const int32_t id = static_cast<int32_t>(s.tasks.size());
@@ -192,6 +220,7 @@ static jacc_status place(Sched& s, std::vector<Range> ranges, int32_t* id_out, c
     if (r.write && r.lo < r.hi) record(s.segs, r.lo, r.hi, true, id);
   s.last_task[st] = id;
   s.tasks.push_back(std::move(t));
+  if (!s.dry) s.pending.push_back(id);
   *id_out = id;
   if (stream_out) *stream_out = s.dry ? nullptr : s.streams[st];
   return ok();
