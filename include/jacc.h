@@ -152,6 +152,17 @@ typedef struct {
 jacc_status jacc_region_boxes(int32_t nloops, const jacc_loop* loops, int32_t nrefs, const jacc_ref* refs,
                               int32_t narrays, const jacc_array* arrays, jacc_box* boxes, int32_t max_boxes,
                               int32_t* nboxes);
+/* jacc_region_boxes for an affine nest (jacc_loop_affine, step 1; inner loops
+ * that run empty for some outer iterations first tighten their outer index
+ * as in jacc_region_analyze_affine).  Each reference contributes the box of
+ * its exact per-dimension extremes over the iterations that run; exact = 1
+ * when every subscript follows at most one loop with coefficient +-1, no two
+ * subscripts the same loop, and those loops have constant bounds (a
+ * reference A[i][j] over the triangle j = 0 .. i is not its box; A[i] is).
+ * Errors as for jacc_region_boxes and jacc_region_analyze_affine. */
+jacc_status jacc_region_boxes_affine(int32_t nloops, const jacc_loop_affine* loops, int32_t nrefs,
+                                     const jacc_ref* refs, int32_t narrays, const jacc_array* arrays, jacc_box* boxes,
+                                     int32_t max_boxes, int32_t* nboxes);
 
 /* ---------------------------------------------------------- specialisation
  * A kernel descriptor names one stencil sweep.  jacc_specialize returns a

@@ -234,6 +234,103 @@ bool affine_extreme(const jacc_loop_affine* L, int n, const wide* c_in, wide off
   return true;
 }
 
+// The body runs only where every loop is non-empty.  An inner loop k whose
+// extent hi_k - lo_k = a i_m + b depends on one outer index i_m with
+// constant bounds is non-empty exactly for i_m >= ceil(-b / a) (a > 0) or
+// i_m <= floor(b / -a) (a < 0): tightening i_m's bounds to that range drops
+// only outer iterations in which the body never runs, so the elimination
+// stays exact.  Repeated until no bound moves; emptiness that depends on
+// several indices is unsupported.  L receives the tightened nest; *runs =
+// false when no iteration runs at all.
+jacc_status tighten_affine(int32_t nloops, const jacc_loop_affine* loops, jacc_loop_affine* L, bool* runs) {
+  using jacc::fail;
+  *runs = true;
+  for (int k = 0; k < nloops; ++k) L[k] = loops[k];
+  auto floor_div = [](wide p, wide q) { return p >= 0 ? p / q : -((-p + q - 1) / q); };  // q > 0
+  for (int pass = 0; pass <= nloops; ++pass) {
+    if (nloops > 0 && L[0].hi < L[0].lo) {
+      *runs = false;
+      return jacc::ok();
+    }
+    bool moved = false;
+    for (int k = 1; k < nloops; ++k) {
+      wide d[JACC_MAX_LOOPS];
+      for (int m = 0; m < k; ++m) d[m] = static_cast<wide>(L[k].hi_coef[m]) - L[k].lo_coef[m];
+      const wide b = static_cast<wide>(L[k].hi) - L[k].lo;
+      wide mn;
+      if (!affine_extreme(L, k, d, b, false, &mn)) return fail(JACC_ERR_OVERFLOW, "loop extent bound overflows int64");
+      if (mn >= 0) continue;
+      int var = -1, nvar = 0;
+      for (int m = 0; m < k; ++m)
+        if (d[m] != 0) {
+          var = m;
+          ++nvar;
+        }
+      if (nvar == 0) {  // loop k never runs
+        *runs = false;
+        return jacc::ok();
+      }
+      bool const_bounds = true;
+      for (int m = 0; m < JACC_MAX_LOOPS; ++m)
+        if (L[var].lo_coef[m] || L[var].hi_coef[m]) const_bounds = false;
+      if (nvar > 1 || !const_bounds)
+        return fail(JACC_ERR_UNSUPPORTED, "loop " + std::to_string(k) +
+                                              " is empty for some outer iterations in a way that couples several indices");
+      const wide a = d[var];
+      if (a > 0) {
+        const wide lo = -floor_div(b, a);  // ceil(-b / a)
+        if (lo > L[var].lo) {
+          L[var].lo = static_cast<int64_t>(lo);
+          moved = true;
+        }
+      } else {
+        const wide hi = floor_div(b, -a);
+        if (hi < L[var].hi) {
+          L[var].hi = static_cast<int64_t>(hi);
+          moved = true;
+        }
+      }
+      if (L[var].hi < L[var].lo) {  // no outer iteration runs loop k
+        *runs = false;
+        return jacc::ok();
+      }
+    }
+    if (!moved) break;
+  }
+  for (int k = 1; k < nloops; ++k) {  // every loop now runs for every outer iteration left
+    wide d[JACC_MAX_LOOPS];
+    for (int m = 0; m < k; ++m) d[m] = static_cast<wide>(L[k].hi_coef[m]) - L[k].lo_coef[m];
+    wide mn;
+    if (!affine_extreme(L, k, d, static_cast<wide>(L[k].hi) - L[k].lo, false, &mn) || mn < 0)
+      return fail(JACC_ERR_UNSUPPORTED, "loop " + std::to_string(k) + " is empty for some outer iterations");
+  }
+  return jacc::ok();
+}
+
+// Drops boxes inside another box of the same array and kind (keeping the
+// first of equal ones) and writes the rest.
+jacc_status emit_boxes(const std::vector<jacc_box>& all, const jacc_array* arrays, jacc_box* boxes, int32_t max_boxes,
+                       int32_t* nboxes) {
+  auto inside = [&](const jacc_box& a, const jacc_box& b) {
+    for (int d = 0; d < arrays[a.array_id].ndim; ++d)
+      if (a.lo[d] < b.lo[d] || a.hi[d] > b.hi[d]) return false;
+    return true;
+  };
+  std::vector<jacc_box> keep;
+  for (size_t i = 0; i < all.size(); ++i) {
+    bool drop = false;
+    for (size_t j = 0; j < all.size() && !drop; ++j) {
+      if (i == j || all[i].array_id != all[j].array_id || all[i].is_write != all[j].is_write) continue;
+      if (inside(all[i], all[j]) && (!inside(all[j], all[i]) || j < i)) drop = true;
+    }
+    if (!drop) keep.push_back(all[i]);
+  }
+  *nboxes = static_cast<int32_t>(keep.size());
+  for (int32_t i = 0; i < *nboxes && i < max_boxes; ++i) boxes[i] = keep[static_cast<size_t>(i)];
+  if (*nboxes > max_boxes) return jacc::fail(JACC_ERR_INVALID_ARG, "more boxes than max_boxes");
+  return jacc::ok();
+}
+
 jacc_status bounds_check(const jacc_region* out, int32_t narrays, const jacc_array* arrays) {
   for (int a = 0; a < narrays; ++a) {
     const jacc_region& O = out[a];
@@ -263,64 +360,11 @@ extern "C" jacc_status jacc_region_analyze_affine(int32_t nloops, const jacc_loo
   jacc_status st = check_refs(nrefs, refs, narrays, arrays);
   if (st) return st;
   std::memset(out, 0, sizeof(jacc_region) * static_cast<size_t>(narrays));
-  // The body runs only where every loop is non-empty.  An inner loop k whose
-  // extent hi_k - lo_k = a i_m + b depends on one outer index i_m with
-  // constant bounds is non-empty exactly for i_m >= ceil(-b / a) (a > 0) or
-  // i_m <= floor(b / -a) (a < 0): tightening i_m's bounds to that range drops
-  // only outer iterations in which the body never runs, so the elimination
-  // below stays exact.  Repeated until no bound moves; emptiness that depends
-  // on several indices remains unsupported.
   jacc_loop_affine L[JACC_MAX_LOOPS];
-  for (int k = 0; k < nloops; ++k) L[k] = loops[k];
-  auto floor_div = [](wide p, wide q) { return p >= 0 ? p / q : -((-p + q - 1) / q); };  // q > 0
-  for (int pass = 0; pass <= nloops; ++pass) {
-    if (nloops > 0 && L[0].hi < L[0].lo) return jacc::ok();  // the nest never runs
-    bool moved = false;
-    for (int k = 1; k < nloops; ++k) {
-      wide d[JACC_MAX_LOOPS];
-      for (int m = 0; m < k; ++m) d[m] = static_cast<wide>(L[k].hi_coef[m]) - L[k].lo_coef[m];
-      const wide b = static_cast<wide>(L[k].hi) - L[k].lo;
-      wide mn;
-      if (!affine_extreme(L, k, d, b, false, &mn)) return fail(JACC_ERR_OVERFLOW, "loop extent bound overflows int64");
-      if (mn >= 0) continue;
-      int var = -1, nvar = 0;
-      for (int m = 0; m < k; ++m)
-        if (d[m] != 0) {
-          var = m;
-          ++nvar;
-        }
-      if (nvar == 0) return jacc::ok();  // loop k never runs: the nest touches nothing
-      bool const_bounds = true;
-      for (int m = 0; m < JACC_MAX_LOOPS; ++m)
-        if (L[var].lo_coef[m] || L[var].hi_coef[m]) const_bounds = false;
-      if (nvar > 1 || !const_bounds)
-        return fail(JACC_ERR_UNSUPPORTED, "loop " + std::to_string(k) +
-                                              " is empty for some outer iterations in a way that couples several indices");
-      const wide a = d[var];
-      if (a > 0) {
-        const wide lo = -floor_div(b, a);  // ceil(-b / a)
-        if (lo > L[var].lo) {
-          L[var].lo = static_cast<int64_t>(lo);
-          moved = true;
-        }
-      } else {
-        const wide hi = floor_div(b, -a);
-        if (hi < L[var].hi) {
-          L[var].hi = static_cast<int64_t>(hi);
-          moved = true;
-        }
-      }
-      if (L[var].hi < L[var].lo) return jacc::ok();  // no outer iteration runs loop k
-    }
-    if (!moved) break;
-  }
-  for (int k = 1; k < nloops; ++k) {  // every loop now runs for every outer iteration left
-    wide d[JACC_MAX_LOOPS];
-    for (int m = 0; m < k; ++m) d[m] = static_cast<wide>(L[k].hi_coef[m]) - L[k].lo_coef[m];
-    wide mn;
-    if (!affine_extreme(L, k, d, static_cast<wide>(L[k].hi) - L[k].lo, false, &mn) || mn < 0)
-      return fail(JACC_ERR_UNSUPPORTED, "loop " + std::to_string(k) + " is empty for some outer iterations");
-  }
+  bool runs = true;
+  st = tighten_affine(nloops, loops, L, &runs);
+  if (st) return st;
+  if (!runs) return jacc::ok();  // the nest never runs: nothing is touched
   loops = L;
   for (int r = 0; r < nrefs; ++r) {
     const jacc_ref& R = refs[r];
@@ -405,23 +449,71 @@ extern "C" jacc_status jacc_region_boxes(int32_t nloops, const jacc_loop* loops,
     b.exact = exact ? 1 : 0;
     all.push_back(b);
   }
-  // drop boxes inside another box of the same array and kind (keep the first of equals)
-  auto inside = [&](const jacc_box& a, const jacc_box& b) {
-    for (int d = 0; d < arrays[a.array_id].ndim; ++d)
-      if (a.lo[d] < b.lo[d] || a.hi[d] > b.hi[d]) return false;
-    return true;
-  };
-  std::vector<jacc_box> keep;
-  for (size_t i = 0; i < all.size(); ++i) {
-    bool drop = false;
-    for (size_t j = 0; j < all.size() && !drop; ++j) {
-      if (i == j || all[i].array_id != all[j].array_id || all[i].is_write != all[j].is_write) continue;
-      if (inside(all[i], all[j]) && (!inside(all[j], all[i]) || j < i)) drop = true;
+  return emit_boxes(all, arrays, boxes, max_boxes, nboxes);
+}
+
+extern "C" jacc_status jacc_region_boxes_affine(int32_t nloops, const jacc_loop_affine* loops, int32_t nrefs,
+                                                const jacc_ref* refs, int32_t narrays, const jacc_array* arrays,
+                                                jacc_box* boxes, int32_t max_boxes, int32_t* nboxes) {
+  using jacc::fail;
+  if (!nboxes || max_boxes < 0 || (max_boxes > 0 && !boxes)) return fail(JACC_ERR_INVALID_ARG, "NULL output");
+  if (nloops < 0 || nloops > JACC_MAX_LOOPS) return fail(JACC_ERR_INVALID_ARG, "nloops outside [0, JACC_MAX_LOOPS]");
+  if (nrefs < 0 || narrays < 0) return fail(JACC_ERR_INVALID_ARG, "negative reference or array count");
+  if ((nloops && !loops) || (nrefs && !refs) || (narrays && !arrays))
+    return fail(JACC_ERR_INVALID_ARG, "NULL array with a non-zero count");
+  for (int k = 0; k < nloops; ++k)
+    for (int m = k; m < JACC_MAX_LOOPS; ++m)
+      if (loops[k].lo_coef[m] || loops[k].hi_coef[m])
+        return fail(JACC_ERR_INVALID_ARG, "a loop bound may depend only on outer loops");
+  jacc_status st = check_refs(nrefs, refs, narrays, arrays);
+  if (st) return st;
+  *nboxes = 0;
+  jacc_loop_affine L[JACC_MAX_LOOPS];
+  bool runs = true;
+  st = tighten_affine(nloops, loops, L, &runs);
+  if (st) return st;
+  if (!runs) return jacc::ok();
+  std::vector<jacc_box> all;
+  for (int r = 0; r < nrefs; ++r) {
+    const jacc_ref& R = refs[r];
+    jacc_box b{};
+    b.array_id = R.array_id;
+    b.is_write = R.is_write ? 1 : 0;
+    // exact when every subscript follows at most one loop, with coefficient
+    // +-1, no two subscripts the same loop, and those loops have constant
+    // bounds: then every combination of their values occurs (the loops in
+    // between never run empty), and the touched set is the whole box
+    bool exact = true;
+    unsigned used = 0;
+    for (int d = 0; d < R.ndim; ++d) {
+      wide c[JACC_MAX_LOOPS];
+      for (int k = 0; k < nloops; ++k) c[k] = R.coef[d][k];
+      wide lo, hi;
+      if (!affine_extreme(L, nloops, c, R.off[d], false, &lo) || !affine_extreme(L, nloops, c, R.off[d], true, &hi))
+        return fail(JACC_ERR_OVERFLOW, "subscript bound overflows int64");
+      b.lo[d] = static_cast<int64_t>(lo);
+      b.hi[d] = static_cast<int64_t>(hi);
+      int nz = 0, kk = -1;
+      for (int k = 0; k < nloops; ++k)
+        if (R.coef[d][k]) {
+          ++nz;
+          kk = k;
+        }
+      if (nz > 1) exact = false;
+      if (nz == 1) {
+        const int64_t cc = R.coef[d][kk];
+        bool const_bounds = true;
+        for (int m = 0; m < JACC_MAX_LOOPS; ++m)
+          if (L[kk].lo_coef[m] || L[kk].hi_coef[m]) const_bounds = false;
+        if ((cc != 1 && cc != -1) || !const_bounds || (used >> kk & 1u)) exact = false;
+        used |= 1u << kk;
+      }
+      const int64_t last = arrays[R.array_id].extent[d] - 1;
+      if (b.lo[d] < 0 || b.hi[d] > last)
+        return fail(JACC_ERR_OUT_OF_BOUNDS, "touched region leaves array " + std::to_string(R.array_id));
     }
-    if (!drop) keep.push_back(all[i]);
+    b.exact = exact ? 1 : 0;
+    all.push_back(b);
   }
-  *nboxes = static_cast<int32_t>(keep.size());
-  for (int32_t i = 0; i < *nboxes && i < max_boxes; ++i) boxes[i] = keep[static_cast<size_t>(i)];
-  if (*nboxes > max_boxes) return fail(JACC_ERR_INVALID_ARG, "more boxes than max_boxes");
-  return jacc::ok();
+  return emit_boxes(all, arrays, boxes, max_boxes, nboxes);
 }

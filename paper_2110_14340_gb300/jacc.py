@@ -103,6 +103,7 @@ SIGNATURES = {
     "jacc_region_analyze": ([C.c_int32, P, C.c_int32, P, C.c_int32, P, P], C.c_int32),
     "jacc_region_analyze_affine": ([C.c_int32, P, C.c_int32, P, C.c_int32, P, P], C.c_int32),
     "jacc_region_boxes": ([C.c_int32, P, C.c_int32, P, C.c_int32, P, P, C.c_int32, P], C.c_int32),
+    "jacc_region_boxes_affine": ([C.c_int32, P, C.c_int32, P, C.c_int32, P, P, C.c_int32, P], C.c_int32),
     "jacc_specialize": ([P, P], C.c_int32),
     "jacc_kernel_info": ([P, P], C.c_int32),
     "jacc_release": ([P], C.c_int32),
@@ -253,6 +254,17 @@ def region_analyze_affine(loops, refs, arrays):
     return st, _region_list(O, arrays)
 
 
+def region_boxes_affine(loops, refs, arrays, max_boxes=256):
+    """region_boxes for an affine nest: loops [(lo, hi, lo_coef[], hi_coef[])], step 1."""
+    L = _affine_loops(loops)
+    _, R, A = _nest([(0, 0, 1)] * len(loops), refs, arrays)
+    B = (Box * max(1, max_boxes))()
+    n = C.c_int32(0)
+    st = lib().jacc_region_boxes_affine(len(loops), C.cast(L, P), len(refs), C.cast(R, P), len(arrays),
+                                        C.cast(A, P), C.cast(B, P), max_boxes, C.byref(n))
+    return st, _boxes_list(B, n, max_boxes, arrays)
+
+
 def region_boxes(loops, refs, arrays, max_boxes=256):
     """Touched sets as a union of boxes; returns (status, [dict(array, write, exact, lo, hi)])."""
     L, R, A = _nest(loops, refs, arrays)
@@ -260,13 +272,17 @@ def region_boxes(loops, refs, arrays, max_boxes=256):
     n = C.c_int32(0)
     st = lib().jacc_region_boxes(len(loops), C.cast(L, P), len(refs), C.cast(R, P), len(arrays), C.cast(A, P),
                                  C.cast(B, P), max_boxes, C.byref(n))
+    return st, _boxes_list(B, n, max_boxes, arrays)
+
+
+def _boxes_list(B, n, max_boxes, arrays):
     out = []
     for i in range(min(n.value, max_boxes)):
         b = B[i]
         nd = len(arrays[b.array_id])
         out.append(dict(array=b.array_id, write=bool(b.is_write), exact=bool(b.exact), lo=list(b.lo[:nd]),
                         hi=list(b.hi[:nd])))
-    return st, out
+    return out
 
 
 # ----------------------------------------------------------------------------- kernels

@@ -215,3 +215,61 @@ def test_inner_loops_empty_for_some_outer_iterations_match_enumeration(orc):
         assert got == want, (trial, loops, refs)
         checked += 1
     assert checked >= 100
+
+
+def touched_affine(loops, refs):
+    """Brute force over an affine nest (step 1): set of (array, write, index tuple)."""
+    out = set()
+
+    def walk(k, idx):
+        if k == len(loops):
+            for r in refs:
+                t = tuple(r["off"][d] + sum(c * i for c, i in zip(r["coef"][d], idx)) for d in range(len(r["off"])))
+                out.add((r["array"], bool(r.get("write")), t))
+            return
+        lo, hi, lc, hc = loops[k]
+        a = lo + sum(c * i for c, i in zip(lc, idx))
+        b = hi + sum(c * i for c, i in zip(hc, idx))
+        for v in range(a, b + 1):
+            walk(k + 1, idx + [v])
+
+    walk(0, [])
+    return out
+
+
+def test_affine_box_unions_cover_and_are_exact_when_flagged():
+    rng = np.random.default_rng(5)
+    exact_seen = inexact_seen = 0
+    for trial in range(200):
+        n = int(rng.integers(1, 4))
+        loops = random_affine_nest(rng, n)
+        nd = int(rng.integers(1, 3))
+        refs = []
+        for _ in range(int(rng.integers(1, 4))):
+            coef = [[int(rng.choice([0, 1, -1, 2])) if rng.integers(0, 2) else 0 for _ in range(n)] for _ in range(nd)]
+            refs.append(dict(array=0, write=bool(rng.integers(0, 2)), coef=coef, off=[int(rng.integers(20, 24)) for _ in range(nd)]))
+        arrays = [[64] * nd]
+        st, boxes = jacc.region_boxes_affine(loops, refs, arrays)
+        assert st == 0, trial
+        t = touched_affine(loops, refs)
+        union = set().union(*[box_points(b) for b in boxes]) if boxes else set()
+        assert t <= union, trial
+        for kind in (False, True):
+            bk = [b for b in boxes if b["write"] == kind]
+            if bk and all(b["exact"] for b in bk):
+                exact_seen += 1
+                assert {p for p in union if p[1] == kind} == {p for p in t if p[1] == kind}, (trial, loops, refs)
+            elif bk:
+                inexact_seen += 1
+    assert exact_seen > 20 and inexact_seen > 20
+
+
+def test_triangle_box_is_not_exact_but_constant_loops_are():
+    tri = [(0, 9, [], []), (0, 0, [0], [1])]            # j = 0 .. i
+    st, b = jacc.region_boxes_affine(tri, [dict(array=0, coef=[[1, 0], [0, 1]], off=[0, 0])], [[10, 10]])
+    assert st == 0 and len(b) == 1 and not b[0]["exact"] and b[0]["hi"] == [9, 9]
+    st, b = jacc.region_boxes_affine(tri, [dict(array=0, coef=[[1, 0]], off=[0])], [[10]])
+    assert st == 0 and b[0]["exact"]                     # A[i]: every i occurs
+    nest = [(0, 9, [], []), (0, 0, [0], [1]), (0, 3, [0, 0], [0, 0])]   # k = 0 .. 3 inside the triangle
+    st, b = jacc.region_boxes_affine(nest, [dict(array=0, coef=[[1, 0, 0], [0, 0, 1]], off=[0, 0])], [[10, 4]])
+    assert st == 0 and b[0]["exact"] and b[0]["lo"] == [0, 0] and b[0]["hi"] == [9, 3]
