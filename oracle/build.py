@@ -9,14 +9,14 @@ SOURCES = [os.path.join(HERE, "oracle.c")]
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c into _build/liboracle.so (plain gcc, -ffp-contract=off)."""
+    """Compile oracle.c into _build/liboracle.so (plain gcc, -ffp-contract=off, pthreads)."""
     os.makedirs(BUILD_DIR, exist_ok=True)
     newest_src = max(os.path.getmtime(s) for s in SOURCES + [os.path.join(HERE, "oracle.h")])
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest_src:
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           "-Wall", "-Wextra", "-o", tmp] + SOURCES + ["-lm"]
+           "-pthread", "-Wall", "-Wextra", "-o", tmp] + SOURCES + ["-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)
     return LIB

@@ -24,10 +24,14 @@
  *   MLP              - central finite differences of the loss; closed-form
  *                      first Adam step; exact fit of a representable target.
  *   regret           - hand-computed tables.
+ *   threads          - every sweep and sum on 2..n threads is bit-identical
+ *                      to the same call on one thread (the threads only split
+ *                      the outermost loop, or the top of the sum's recursion).
  */
 #include "oracle.h"
 
 #include <math.h>
+#include <pthread.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -255,12 +259,85 @@ int orc_region_analyze(int32_t nloops, const orc_loop* loops, int32_t nrefs, con
 /* the 5-, 7- and 27-point members of that family, written as plain loops.    */
 /* ------------------------------------------------------------------------- */
 
+/* ------------------------------------------------------------------------- */
+/* Threads.  A sweep may split its outermost loop (rows in 2D, planes in 3D)  */
+/* into contiguous slabs, one per thread.  Each thread runs the loop body of  */
+/* the single-thread sweep over its slab, so every output value comes from    */
+/* the same statements in the same order, and the residual (a maximum, which  */
+/* does not depend on the order it is taken in) is the same bits.  The count  */
+/* is a process-wide setting, 1 by default.                                   */
+/* ------------------------------------------------------------------------- */
+
+#define ORC_MAX_THREADS 256
+static int g_nthreads = 1;
+
+int32_t orc_set_threads(int32_t n) {
+  g_nthreads = n < 1 ? 1 : (n > ORC_MAX_THREADS ? ORC_MAX_THREADS : n);
+  return g_nthreads;
+}
+
+int32_t orc_get_threads(void) { return g_nthreads; }
+
+/* A slab body: the sweep's loop over outer indices [lo, hi); returns the
+ * largest |v - u| it saw (0 where the sweep has no residual). */
+typedef double (*slab_fn)(const void* args, int64_t lo, int64_t hi);
+
+typedef struct {
+  slab_fn fn;
+  const void* args;
+  int64_t lo, hi;
+  double res;
+} slab_job;
+
+static void* slab_main(void* p) {
+  slab_job* j = (slab_job*)p;
+  j->res = j->fn(j->args, j->lo, j->hi);
+  return NULL;
+}
+
+/* Runs fn over [0, n) in up to g_nthreads contiguous slabs; returns the
+ * largest residual.  A thread that cannot be started runs on the caller. */
+static double run_slabs(slab_fn fn, const void* args, int64_t n) {
+  int64_t T = g_nthreads < n ? g_nthreads : n;
+  if (T <= 1) return fn(args, 0, n);
+  slab_job job[ORC_MAX_THREADS];
+  pthread_t th[ORC_MAX_THREADS];
+  int started[ORC_MAX_THREADS];
+  for (int64_t t = 0; t < T; ++t) {
+    job[t].fn = fn;
+    job[t].args = args;
+    job[t].lo = n * t / T;
+    job[t].hi = n * (t + 1) / T;
+    job[t].res = 0.0;
+  }
+  for (int64_t t = 1; t < T; ++t) started[t] = pthread_create(&th[t], NULL, slab_main, &job[t]) == 0;
+  slab_main(&job[0]);
+  for (int64_t t = 1; t < T; ++t) {
+    if (started[t]) pthread_join(th[t], NULL);
+    else slab_main(&job[t]);
+  }
+  double res = 0.0;
+  for (int64_t t = 0; t < T; ++t)
+    if (job[t].res > res) res = job[t].res;
+  return res;
+}
+
 /* v[y][x] = 0.25 * ((u[y-1][x] + u[y+1][x]) + (u[y][x-1] + u[y][x+1])) on the
  * interior; boundary rows and columns are held (copied).  Residual: the
  * largest |v - u| over the interior, i.e. the change made by this sweep. */
-double orc_jacobi2d_sweep(int64_t nx, int64_t ny, const double* u, double* v) {
+typedef struct {
+  int64_t nx, ny;
+  const double* u;
+  double* v;
+} jacobi2d_args;
+
+static double jacobi2d_rows(const void* args, int64_t y0, int64_t y1) {
+  const jacobi2d_args* A = (const jacobi2d_args*)args;
+  const int64_t nx = A->nx, ny = A->ny;
+  const double* u = A->u;
+  double* v = A->v;
   double res = 0.0;
-  for (int64_t y = 0; y < ny; ++y) {
+  for (int64_t y = y0; y < y1; ++y) {
     for (int64_t x = 0; x < nx; ++x) {
       int64_t c = y * nx + x;
       if (y == 0 || y == ny - 1 || x == 0 || x == nx - 1) {
@@ -274,6 +351,11 @@ double orc_jacobi2d_sweep(int64_t nx, int64_t ny, const double* u, double* v) {
     }
   }
   return res;
+}
+
+double orc_jacobi2d_sweep(int64_t nx, int64_t ny, const double* u, double* v) {
+  jacobi2d_args A = {nx, ny, u, v};
+  return run_slabs(jacobi2d_rows, &A, ny);
 }
 
 int orc_jacobi2d_run(int64_t nx, int64_t ny, double* u0, double* u1, int32_t nsweeps, double* resid) {
@@ -292,10 +374,22 @@ int orc_jacobi2d_run(int64_t nx, int64_t ny, double* u0, double* u1, int32_t nsw
 /* Explicit heat step: v = u + r * ((((xm + xp) + (ym + yp)) + (zm + zp)) - 6 u)
  * on the interior; Dirichlet boundary values are held.  Residual: largest
  * |v - u| over the interior. */
-double orc_heat3d_sweep(int64_t nx, int64_t ny, int64_t nz, double r, const double* u, double* v) {
+typedef struct {
+  int64_t nx, ny, nz;
+  double r;
+  const double* u;
+  double* v;
+} heat3d_args;
+
+static double heat3d_planes(const void* args, int64_t z0, int64_t z1) {
+  const heat3d_args* A = (const heat3d_args*)args;
+  const int64_t nx = A->nx, ny = A->ny, nz = A->nz;
+  const double r = A->r;
+  const double* u = A->u;
+  double* v = A->v;
   const int64_t sy = nx, sz = nx * ny;
   double res = 0.0;
-  for (int64_t z = 0; z < nz; ++z)
+  for (int64_t z = z0; z < z1; ++z)
     for (int64_t y = 0; y < ny; ++y)
       for (int64_t x = 0; x < nx; ++x) {
         int64_t c = z * sz + y * sy + x;
@@ -309,6 +403,11 @@ double orc_heat3d_sweep(int64_t nx, int64_t ny, int64_t nz, double r, const doub
         if (d > res) res = d;
       }
   return res;
+}
+
+double orc_heat3d_sweep(int64_t nx, int64_t ny, int64_t nz, double r, const double* u, double* v) {
+  heat3d_args A = {nx, ny, nz, r, u, v};
+  return run_slabs(heat3d_planes, &A, nz);
 }
 
 int orc_heat3d_run(int64_t nx, int64_t ny, int64_t nz, double r, double* u0, double* u1, int32_t nsweeps,
@@ -369,20 +468,37 @@ int orc_var19_run(int64_t nx, int64_t ny, int64_t nz, float omega, const float* 
 /* 27-point periodic stencil in FP32.  Offsets (dx,dy,dz) in {-1,0,1}^3 are
  * classed by how many are non-zero: 0 centre, 1 face (6), 2 edge (12),
  * 3 corner (8).  v = w0*centre + wf*F + we*E + wc*C, where F, E, C are the
- * class sums taken in offset order dz, dy, dx = -1..1.  Indices wrap. */
-void orc_box27_sweep(int64_t nx, int64_t ny, int64_t nz, const float w[4], const float* u, float* v) {
-  for (int64_t z = 0; z < nz; ++z)
-    for (int64_t y = 0; y < ny; ++y)
+ * class sums taken in offset order dz, dy, dx = -1..1.  Indices wrap: the
+ * wrapped neighbour index of each axis, (i + d + n) % n, is formed once per
+ * index instead of once per neighbour. */
+typedef struct {
+  int64_t nx, ny, nz;
+  const float* w;
+  const float* u;
+  float* v;
+} box27_args;
+
+static double box27_planes(const void* args, int64_t z0, int64_t z1) {
+  const box27_args* A = (const box27_args*)args;
+  const int64_t nx = A->nx, ny = A->ny, nz = A->nz;
+  const float* w = A->w;
+  const float* u = A->u;
+  float* v = A->v;
+  for (int64_t z = z0; z < z1; ++z) {
+    int64_t zw[3];
+    for (int d = -1; d <= 1; ++d) zw[d + 1] = (z + d + nz) % nz;
+    for (int64_t y = 0; y < ny; ++y) {
+      int64_t yw[3];
+      for (int d = -1; d <= 1; ++d) yw[d + 1] = (y + d + ny) % ny;
       for (int64_t x = 0; x < nx; ++x) {
+        int64_t xw[3];
+        for (int d = -1; d <= 1; ++d) xw[d + 1] = (x + d + nx) % nx;
         float cls[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         for (int dz = -1; dz <= 1; ++dz)
           for (int dy = -1; dy <= 1; ++dy)
             for (int dx = -1; dx <= 1; ++dx) {
-              int64_t zz = (z + dz + nz) % nz;
-              int64_t yy = (y + dy + ny) % ny;
-              int64_t xx = (x + dx + nx) % nx;
               int k = (dz != 0) + (dy != 0) + (dx != 0);
-              cls[k] = cls[k] + u[(zz * ny + yy) * nx + xx];
+              cls[k] = cls[k] + u[(zw[dz + 1] * ny + yw[dy + 1]) * nx + xw[dx + 1]];
             }
         float acc = w[0] * cls[0];
         acc = acc + w[1] * cls[1];
@@ -390,6 +506,14 @@ void orc_box27_sweep(int64_t nx, int64_t ny, int64_t nz, const float w[4], const
         acc = acc + w[3] * cls[3];
         v[(z * ny + y) * nx + x] = acc;
       }
+    }
+  }
+  return 0.0;
+}
+
+void orc_box27_sweep(int64_t nx, int64_t ny, int64_t nz, const float w[4], const float* u, float* v) {
+  box27_args A = {nx, ny, nz, w, u, v};
+  run_slabs(box27_planes, &A, nz);
 }
 
 int orc_box27_run(int64_t nx, int64_t ny, int64_t nz, const float w[4], float* u0, float* u1, int32_t nsweeps,
@@ -407,19 +531,34 @@ int orc_box27_run(int64_t nx, int64_t ny, int64_t nz, const float w[4], float* u
 }
 
 /* The same definition with FP64 storage and arithmetic. */
-void orc_box27_sweep_f64(int64_t nx, int64_t ny, int64_t nz, const double w[4], const double* u, double* v) {
-  for (int64_t z = 0; z < nz; ++z)
-    for (int64_t y = 0; y < ny; ++y)
+typedef struct {
+  int64_t nx, ny, nz;
+  const double* w;
+  const double* u;
+  double* v;
+} box27_f64_args;
+
+static double box27_f64_planes(const void* args, int64_t z0, int64_t z1) {
+  const box27_f64_args* A = (const box27_f64_args*)args;
+  const int64_t nx = A->nx, ny = A->ny, nz = A->nz;
+  const double* w = A->w;
+  const double* u = A->u;
+  double* v = A->v;
+  for (int64_t z = z0; z < z1; ++z) {
+    int64_t zw[3];
+    for (int d = -1; d <= 1; ++d) zw[d + 1] = (z + d + nz) % nz;
+    for (int64_t y = 0; y < ny; ++y) {
+      int64_t yw[3];
+      for (int d = -1; d <= 1; ++d) yw[d + 1] = (y + d + ny) % ny;
       for (int64_t x = 0; x < nx; ++x) {
+        int64_t xw[3];
+        for (int d = -1; d <= 1; ++d) xw[d + 1] = (x + d + nx) % nx;
         double cls[4] = {0.0, 0.0, 0.0, 0.0};
         for (int dz = -1; dz <= 1; ++dz)
           for (int dy = -1; dy <= 1; ++dy)
             for (int dx = -1; dx <= 1; ++dx) {
-              int64_t zz = (z + dz + nz) % nz;
-              int64_t yy = (y + dy + ny) % ny;
-              int64_t xx = (x + dx + nx) % nx;
               int k = (dz != 0) + (dy != 0) + (dx != 0);
-              cls[k] = cls[k] + u[(zz * ny + yy) * nx + xx];
+              cls[k] = cls[k] + u[(zw[dz + 1] * ny + yw[dy + 1]) * nx + xw[dx + 1]];
             }
         double acc = w[0] * cls[0];
         acc = acc + w[1] * cls[1];
@@ -427,6 +566,14 @@ void orc_box27_sweep_f64(int64_t nx, int64_t ny, int64_t nz, const double w[4], 
         acc = acc + w[3] * cls[3];
         v[(z * ny + y) * nx + x] = acc;
       }
+    }
+  }
+  return 0.0;
+}
+
+void orc_box27_sweep_f64(int64_t nx, int64_t ny, int64_t nz, const double w[4], const double* u, double* v) {
+  box27_f64_args A = {nx, ny, nz, w, u, v};
+  run_slabs(box27_f64_planes, &A, nz);
 }
 
 int orc_box27_run_f64(int64_t nx, int64_t ny, int64_t nz, const double w[4], double* u0, double* u1, int32_t nsweeps,
@@ -457,25 +604,94 @@ double orc_maxabs_diff(const double* a, const double* b, int64_t n) {
   return m;
 }
 
-/* Pairwise (cascade) summation: error O(log n * eps * sum|a|). */
-double orc_sum_f64(const double* a, int64_t n) {
+/* Pairwise (cascade) summation: error O(log n * eps * sum|a|).  The
+ * recursion halves the range (first half n/2 elements) down to runs of at
+ * most 8, summed left to right. */
+static double sum_f64_seq(const double* a, int64_t n) {
   if (n <= 8) {
     double s = 0.0;
     for (int64_t i = 0; i < n; ++i) s += a[i];
     return s;
   }
   int64_t h = n / 2;
-  return orc_sum_f64(a, h) + orc_sum_f64(a + h, n - h);
+  return sum_f64_seq(a, h) + sum_f64_seq(a + h, n - h);
 }
 
-double orc_sum_f32(const float* a, int64_t n) {
+static double sum_f32_seq(const float* a, int64_t n) {
   if (n <= 8) {
     double s = 0.0;
     for (int64_t i = 0; i < n; ++i) s += (double)a[i];
     return s;
   }
   int64_t h = n / 2;
-  return orc_sum_f32(a, h) + orc_sum_f32(a + h, n - h);
+  return sum_f32_seq(a, h) + sum_f32_seq(a + h, n - h);
+}
+
+/* With threads, the top `depth` levels of the same recursion are unrolled:
+ * its subranges at that depth are summed in parallel (each by the recursion
+ * above) and their sums combined in the recursion's own pairing, so the
+ * result is bit-identical to the single-thread sum. */
+typedef struct {
+  const void* a;
+  int64_t n;
+  int f32;
+  double s;
+} sum_job;
+
+static void* sum_main(void* p) {
+  sum_job* j = (sum_job*)p;
+  j->s = j->f32 ? sum_f32_seq((const float*)j->a, j->n) : sum_f64_seq((const double*)j->a, j->n);
+  return NULL;
+}
+
+static void sum_leaves(const char* a, int64_t n, int64_t esz, int f32, int depth, sum_job* leaf, int* nl) {
+  if (depth == 0 || n <= 8) {
+    leaf[*nl].a = a;
+    leaf[*nl].n = n;
+    leaf[*nl].f32 = f32;
+    leaf[*nl].s = 0.0;
+    ++*nl;
+    return;
+  }
+  int64_t h = n / 2;
+  sum_leaves(a, h, esz, f32, depth - 1, leaf, nl);
+  sum_leaves(a + h * esz, n - h, esz, f32, depth - 1, leaf, nl);
+}
+
+static double sum_combine(int64_t n, int depth, const sum_job* leaf, int* i) {
+  if (depth == 0 || n <= 8) return leaf[(*i)++].s;
+  int64_t h = n / 2;
+  double l = sum_combine(h, depth - 1, leaf, i);
+  double r = sum_combine(n - h, depth - 1, leaf, i);
+  return l + r;
+}
+
+static double sum_threaded(const void* a, int64_t n, int64_t esz, int f32) {
+  int depth = 0;
+  while ((1 << depth) < g_nthreads && depth < 8) ++depth;
+  sum_job leaf[ORC_MAX_THREADS];
+  pthread_t th[ORC_MAX_THREADS];
+  int started[ORC_MAX_THREADS];
+  int nl = 0;
+  sum_leaves((const char*)a, n, esz, f32, depth, leaf, &nl);
+  for (int t = 1; t < nl; ++t) started[t] = pthread_create(&th[t], NULL, sum_main, &leaf[t]) == 0;
+  sum_main(&leaf[0]);
+  for (int t = 1; t < nl; ++t) {
+    if (started[t]) pthread_join(th[t], NULL);
+    else sum_main(&leaf[t]);
+  }
+  int i = 0;
+  return sum_combine(n, depth, leaf, &i);
+}
+
+double orc_sum_f64(const double* a, int64_t n) {
+  if (g_nthreads > 1 && n >= (1 << 16)) return sum_threaded(a, n, sizeof(double), 0);
+  return sum_f64_seq(a, n);
+}
+
+double orc_sum_f32(const float* a, int64_t n) {
+  if (g_nthreads > 1 && n >= (1 << 16)) return sum_threaded(a, n, sizeof(float), 1);
+  return sum_f32_seq(a, n);
 }
 
 /* ------------------------------------------------------------------------- */

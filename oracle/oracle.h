@@ -62,6 +62,16 @@ typedef struct {
   int64_t hi_coef[ORC_MAX_LOOPS];
 } orc_loop_affine;
 
+/* Threads for the stencil sweeps and the large sums (default 1).  A sweep
+ * splits its outermost loop into contiguous slabs, one per thread, each
+ * running the single-thread loop body; a sum unrolls the top levels of its
+ * pairwise recursion across threads.  Results are bit-identical to one
+ * thread for every count.  The variable-coefficient 19-point sweep, whose
+ * residual is a sum taken in loop order, always runs on one thread.
+ * Returns the count in effect (clamped to [1, 256]). */
+int32_t orc_set_threads(int32_t n);
+int32_t orc_get_threads(void);
+
 /* Region of an affine-bounded nest by enumerating every iteration (small
  * nests only: at most 2^22 iterations, else ORC_ERR_INVALID_ARG).  Same
  * output as orc_region_analyze; no bounds check. */

@@ -88,6 +88,10 @@ def lib():
         L.orc_adam_step.restype = None
         L.orc_adam_step.argtypes = [P, P, P, P, C.c_int64, C.c_int64, C.c_double, C.c_double, C.c_double,
                                     C.c_double]
+        L.orc_set_threads.restype = C.c_int32
+        L.orc_set_threads.argtypes = [C.c_int32]
+        L.orc_get_threads.restype = C.c_int32
+        L.orc_get_threads.argtypes = []
         L.orc_regret.restype = None
         L.orc_regret.argtypes = [P, C.c_int32, C.c_int32, P, P]
         _lib = L
@@ -174,6 +178,33 @@ def region_enumerate_affine(loops, refs, arrays):
     st = lib().orc_region_enumerate_affine(len(loops), C.cast(L, C.c_void_p), len(refs), C.cast(R, C.c_void_p),
                                            len(arrays), C.cast(A, C.c_void_p), C.cast(O, C.c_void_p))
     return st, _regions(O, arrays)
+
+
+# ----------------------------------------------------------------------------- threads
+
+def set_threads(n):
+    """Threads for the sweeps and large sums (bit-identical results for any count); returns the count set."""
+    return int(lib().orc_set_threads(int(n)))
+
+
+def get_threads():
+    return int(lib().orc_get_threads())
+
+
+class threads:
+    """Context manager: run the oracle on n threads (default: every host core), then restore."""
+
+    def __init__(self, n=None):
+        self.n = n if n is not None else (os.cpu_count() or 1)
+
+    def __enter__(self):
+        self.old = get_threads()
+        set_threads(self.n)
+        return self
+
+    def __exit__(self, *exc):
+        set_threads(self.old)
+        return False
 
 
 # ----------------------------------------------------------------------------- stencils
