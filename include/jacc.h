@@ -435,6 +435,13 @@ jacc_status jacc_sched_nest_end(jacc_sched s, int32_t task_id);
 jacc_status jacc_sched_task_info(jacc_sched s, int32_t task_id, int32_t* deps, int32_t max_deps, int32_t* ndeps,
                                  int32_t* stream_index);
 jacc_status jacc_sched_join(jacc_sched s, uintptr_t stream);
+/* Resource count for long runs: first retires every task that has completed
+ * on the device and is neither its stream's last task nor an open nest, then
+ * reports in *live_events how many tasks still hold a completion event (at
+ * most the stream count plus the open nests plus the tasks still running)
+ * and, if ntasks is not NULL, how many tasks were submitted.  Dry-run
+ * schedulers hold no events (0). */
+jacc_status jacc_sched_live_events(jacc_sched s, int64_t* live_events, int64_t* ntasks);
 /* Waits for the pool's streams, then frees the scheduler. */
 jacc_status jacc_sched_release(jacc_sched s);
 
@@ -594,15 +601,18 @@ jacc_status jacc_batch_release(jacc_batch b);
  * grid size), which every GPU that loads the library holds until exit.  The
  * first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call shares the array and the call
+ * before any stream capture.  The address is kept per device for the
+ * device's primary context; jacc_shutdown forgets it (call jacc_shutdown
+ * after a cudaDeviceReset).  Every call shares the array and the call
  * clears the word it uses; calls that overlap on the GPU (other streams, or
  * other threads) race on it.  No cudaMalloc, cudaFree or allocating library
  * routine is called.  The handle itself comes from jacc_specialize, which
  * may allocate: create it during set-up. */
 jacc_status jacc_launch_static(jacc_kernel k, const void* u_in, void* u_out, double* resid_dev, uintptr_t stream);
 
-/* Release every cached kernel, graph and library allocation.  Handles become
- * invalid.  Safe to call more than once. */
+/* Release every cached kernel, graph and library allocation, and forget the
+ * per-device address of jacc_launch_static's array.  Handles become invalid.
+ * Safe to call more than once. */
 jacc_status jacc_shutdown(void);
 
 #ifdef __cplusplus

@@ -95,6 +95,8 @@ cudaError_t launch_maxabs(const double* u, long long n, u64* maxword, cudaStream
 cudaError_t launch_fill_skipped(double* resid, int n, int T, cudaStream_t s);
 // u (n FP64 values) -> the resident fixed point in place, F from *maxword
 cudaError_t launch_to_fixed(double* u, long long n, const u64* maxword, cudaStream_t s);
+// Drops the cached per-device address of jacc_launch_static's scratch array.
+void static_scratch_forget();
 
 // NVRTC: compile `src` (plus jacc_params.h) for sm_103a, load it, return
 // kernel `name`.  Uses the on-disk cache under $JACC_CACHE_DIR if set.

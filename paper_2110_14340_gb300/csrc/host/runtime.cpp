@@ -471,6 +471,7 @@ extern "C" jacc_status jacc_shutdown(void) {
   std::lock_guard<std::mutex> lock(global_mutex());
   for (auto& e : cache()) free_kernel(e.second);
   cache().clear();
+  static_scratch_forget();
   return ok();
 }
 

@@ -129,20 +129,23 @@ struct Sched {
   std::vector<int32_t> last_task;  // per stream: the last task placed on it (-1: none)
   std::vector<Task> tasks;
   SegMap segs;            // the dependency index
-  std::vector<int32_t> pending;  // live mode: tasks not yet retired, in submission order
+  std::vector<int32_t> pending;  // live mode: tasks to retire once completed (submission order, plus
+                                 // former stream anchors and closed nests queued again)
   size_t pending_head = 0;       // first entry of `pending` still to check
+  int64_t live_events = 0;       // tasks whose completion event still exists
   int32_t next_free = 0;  // round-robin cursor for tasks without dependencies
   std::mutex mu;
 };
 
-// Places a new task with the given ranges: finds its dependencies, picks a
-// stream and, in live mode, makes the stream wait for the dependencies.
 // Live mode: retires the oldest tasks that have completed on the device
 // (their events are destroyed; a later task that names them waits for
 // nothing).  Stops at the first task still running, so the cost stays
 // proportional to the tasks passed.  A stream's last task (the anchor of its
-// chain) and an open nest task are passed over here; they are retired later
-// when a new task names them, or freed with the scheduler.
+// chain, whose event jacc_sched_join waits on) and an open nest task cannot
+// be retired yet: they leave the queue here and are queued again when they
+// stop being one (place() when the stream gets a new last task,
+// jacc_sched_nest_end when the nest closes), so every task is retired once
+// it has completed and is neither.
 static void retire_completed(Sched& s) {
   while (s.pending_head < s.pending.size()) {
     const int32_t j = s.pending[s.pending_head];
@@ -152,6 +155,7 @@ static void retire_completed(Sched& s) {
       cudaEventDestroy(o.done);
       o.done = nullptr;
       o.retired = true;
+      --s.live_events;
     }
     ++s.pending_head;
   }
@@ -185,6 +189,7 @@ static jacc_status place(Sched& s, std::vector<Range> ranges, int32_t* id_out, c
       cudaEventDestroy(o.done);
       o.done = nullptr;
       o.retired = true;
+      --s.live_events;
       continue;
     }
     t.deps.push_back(j);
@@ -211,6 +216,7 @@ static jacc_status place(Sched& s, std::vector<Range> ranges, int32_t* id_out, c
     }
     jacc_status e = cuda_check(cudaEventCreateWithFlags(&t.done, cudaEventDisableTiming), "cudaEventCreate");
     if (e) return e;
+    ++s.live_events;
   }
   // the task is placed: enter its ranges into the index (reads first, so a
   // range both read and written ends as written)
@@ -218,6 +224,10 @@ static jacc_status place(Sched& s, std::vector<Range> ranges, int32_t* id_out, c
     if (!r.write && r.lo < r.hi) record(s.segs, r.lo, r.hi, false, id);
   for (const Range& r : t.ranges)
     if (r.write && r.lo < r.hi) record(s.segs, r.lo, r.hi, true, id);
+  // the stream's previous last task stops being its anchor: queue it again
+  // (it completes before the new task, which follows it on the stream)
+  const int32_t old_anchor = s.last_task[st];
+  if (!s.dry && old_anchor >= 0 && !s.tasks[old_anchor].retired) s.pending.push_back(old_anchor);
   s.last_task[st] = id;
   s.tasks.push_back(std::move(t));
   if (!s.dry) s.pending.push_back(id);
@@ -381,6 +391,7 @@ extern "C" jacc_status jacc_sched_nest_end(jacc_sched h, int32_t task_id) {
   if (task_id < 0 || task_id >= static_cast<int32_t>(s.tasks.size()) || !s.tasks[task_id].open)
     return fail(JACC_ERR_INVALID_ARG, "not an open nest task");
   s.tasks[task_id].open = false;
+  if (!s.dry) s.pending.push_back(task_id);  // retirable once completed
   return finish(s, task_id);
 }
 
@@ -394,6 +405,16 @@ extern "C" jacc_status jacc_sched_task_info(jacc_sched h, int32_t task_id, int32
   *ndeps = static_cast<int32_t>(t.deps.size());
   *stream_index = t.stream;
   for (int32_t i = 0; i < max_deps && i < *ndeps; ++i) deps[i] = t.deps[i];
+  return ok();
+}
+
+extern "C" jacc_status jacc_sched_live_events(jacc_sched h, int64_t* live_events, int64_t* ntasks) {
+  if (!h || !live_events) return fail(JACC_ERR_INVALID_ARG, "NULL argument");
+  Sched& s = *reinterpret_cast<Sched*>(h);
+  std::lock_guard<std::mutex> lock(s.mu);
+  if (!s.dry) retire_completed(s);
+  *live_events = s.live_events;
+  if (ntasks) *ntasks = static_cast<int64_t>(s.tasks.size());
   return ok();
 }
 

@@ -9,13 +9,10 @@ namespace jacc {
 cudaError_t launch_maxabs(const double* u, long long n, u64* maxword, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(maxword, 0, sizeof(u64), s);
   if (e != cudaSuccess) return e;
-  // one resident wave of 256-thread blocks (8 per SM)
-  static int nsm = 0;
-  if (nsm == 0) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      nsm = 152;
-  }
+  // one resident wave of 256-thread blocks (8 per SM) of the current device
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    nsm = 152;
   long long pairs = n / 2;
   long long blocks = (pairs + 255) / 256;
   if (blocks < 1) blocks = 1;

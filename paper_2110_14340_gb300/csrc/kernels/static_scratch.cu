@@ -30,7 +30,9 @@ u64* g_addr[kMaxDevices] = {nullptr};
 
 // The host-side name g_static_scratch is not a device address; the address
 // valid on the current device comes from cudaGetSymbolAddress, taken once per
-// device with that device current.
+// device with that device current.  The cached address belongs to the
+// device's primary context: jacc_shutdown forgets it (a context reset makes
+// it stale, and jacc_shutdown is required after one anyway).
 jacc_status static_scratch_address(u64** out) {
   int dev = 0;
   jacc_status st = jacc::cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
@@ -48,6 +50,13 @@ jacc_status static_scratch_address(u64** out) {
 }
 
 }  // namespace
+
+namespace jacc {
+void static_scratch_forget() {
+  std::lock_guard<std::mutex> lock(g_mu);
+  for (auto& a : g_addr) a = nullptr;
+}
+}  // namespace jacc
 
 extern "C" jacc_status jacc_launch_static(jacc_kernel h, const void* u_in, void* u_out, double* resid_dev,
                                           uintptr_t stream) {

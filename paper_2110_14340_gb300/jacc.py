@@ -125,6 +125,7 @@ SIGNATURES = {
     "jacc_sched_nest_end": ([P, C.c_int32], C.c_int32),
     "jacc_sched_task_info": ([P, C.c_int32, P, C.c_int32, P, P], C.c_int32),
     "jacc_sched_join": ([P, C.c_size_t], C.c_int32),
+    "jacc_sched_live_events": ([P, P, P], C.c_int32),
     "jacc_sched_release": ([P], C.c_int32),
     "jacc_shutdown": ([], C.c_int32),
     "jacc_batch_create": ([C.c_int32, P, P, P], C.c_int32),
@@ -550,6 +551,13 @@ class Sched:
         s = C.c_int32(-1)
         _check(lib().jacc_sched_task_info(self.handle, int(task), d, max_deps, C.byref(n), C.byref(s)))
         return list(d[:min(n.value, max_deps)]), s.value
+
+    def live_events(self):
+        """(tasks still holding a completion event, tasks submitted), after retiring completed ones."""
+        e = C.c_int64(0)
+        n = C.c_int64(0)
+        _check(lib().jacc_sched_live_events(self.handle, C.byref(e), C.byref(n)))
+        return e.value, n.value
 
     def join(self, stream=None):
         _check(lib().jacc_sched_join(self.handle, _stream(stream)))

@@ -10,6 +10,7 @@ import pytest
 import torch
 
 from paper_2110_14340_gb300 import inputs, jacc
+from tolerances import TOL64, assert_resid, nerr
 
 pytestmark = pytest.mark.gpu
 
@@ -51,8 +52,8 @@ def test_sweep_host_matches_device_sweep(orc, pinned, n):
     assert np.array_equal(out.numpy().view(np.int64), want.view(np.int64))
     assert np.array_equal(res_host.numpy(), wres)
     o, orr = orc.heat3d_run(u, 0.125, n)
-    assert np.max(np.abs(out.numpy() - o)) <= 1e-12 * np.max(np.abs(o))
-    assert np.max(np.abs(res_host.numpy() - orr)) <= 1e-12 * np.max(np.abs(o))
+    assert nerr(out.numpy(), o) <= TOL64
+    assert_resid(res_host.numpy(), orr, np.max(np.abs(u)))
 
 
 def test_two_streams_two_buffer_sets_overlap_correctly():

@@ -4,7 +4,7 @@ Some callers cannot allocate device memory when they launch (a memory pool
 that must own every device byte, a path that must not synchronise on
 cudaMalloc).  jacc_launch_static keeps its scratch in a static device array
 instead; its output must equal jacc_launch's, call after call, since the
-array keeps the previous call's contents.  This file sorts last so that a run
+array keeps the previous call's contents, and match the oracle's sweep.  This file sorts last so that a run
 stopping at the first failure has run every other test first.
 """
 import ctypes as C
@@ -14,13 +14,12 @@ import pytest
 import torch
 
 from paper_2110_14340_gb300 import inputs, jacc
+from tolerances import TOL64, assert_resid, nerr
 
 pytestmark = pytest.mark.gpu
 
-TOL64 = 1e-12
 
-
-def test_static_scratch_launch_matches_jacc_launch():
+def test_static_scratch_launch_matches_jacc_launch(orc):
     from paper_2110_14340_gb300 import build
     build.build()
     L = jacc.lib()
@@ -44,6 +43,9 @@ def test_static_scratch_launch_matches_jacc_launch():
         g, w = got.cpu().numpy(), want.cpu().numpy()
         assert np.max(np.abs(g - w)) <= TOL64 * np.max(np.abs(w))
         assert abs(r_got.item() - r_want.item()) <= TOL64 * np.max(np.abs(w))
+        o, orr = orc.heat3d_sweep(u, 0.125)
+        assert nerr(g, o) <= TOL64
+        assert_resid([r_got.item()], [orr], np.max(np.abs(u)))
     # errors are those of jacc_launch
     assert L.jacc_launch_static(k.handle, C.c_void_p(a.data_ptr()), C.c_void_p(a.data_ptr()), None, s) == \
         jacc.ERR_INVALID_ARG
