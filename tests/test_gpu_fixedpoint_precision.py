@@ -93,7 +93,7 @@ def check(g, exact, o, M, k):
 
 @pytest.mark.parametrize("tile", [0, 17])
 def test_jacobi_fixed_point_pointwise_bound_on_1e12_range(orc, tile):
-    ny, nx, k = 70, 97, 10
+    ny, nx, k = 70, 98, 10
     x = np.arange(nx) / (nx - 1)
     u = np.repeat((10.0 ** (-12.0 * x))[None, :], ny, axis=0)  # smooth: 1 at x = 0 down to 1e-12
     u *= 1.0 + 0.25 * inputs.uniform64(51, nx * ny).reshape(ny, nx)
