@@ -538,22 +538,37 @@ jacc_status jacc_costmodel_release(jacc_costmodel m);
  * Many independent 2D 5-point Jacobi grids (FP64, Dirichlet boundary held)
  * swept together in one persistent, cooperative launch.  No counterpart in
  * the paper, which overlaps independent kernels on OpenACC queues (§6.1).
- * Every sweep of every grid runs inside that launch: work is a sequence of
- * tickets (sweep, band of rows of one grid) in sweep-major order; a band
- * waits, bounded by a time limit, until the previous sweep of its own grid
- * has finished, so grids advance independently.  Arithmetic is the 5-point
- * stencil's (exact fixed point for finite inputs, see jacc_specialize).
+ * Every sweep of every grid runs inside that launch.  Each grid is cut into
+ * items (tiles of rows x cols points, cols = 64 x the tile's warps across);
+ * grids are packed into groups whose two fields fit an L2 budget together;
+ * work is a sequence of tickets (sweep, item), group after group and
+ * sweep-major within a group, so a group's fields stay in L2 across its
+ * sweeps.  An item waits, bounded by a time limit, only until the items
+ * whose rows or columns it reads (the tiles above, below, left and right,
+ * and itself) have finished the previous sweep.  Arithmetic is the 5-point
+ * stencil's (exact fixed point for finite inputs, see jacc_specialize);
+ * every schedule gives the same bits.
  *
- * Schedule (jacc_batch_config): target points per band (band height =
- * max(1, item_points / nx) rows), persistent CTAs per SM (0 = as many as
- * fit), and band order (0: grids largest first, bands grid by grid;
- * 1: round-robin over grids).  timeout_ms bounds every device wait (0 =
- * 2000 ms).  test_stall_ticket is a fault-injection hook for tests: that
- * ticket never reports completion, so the waits behind it time out; -1 = off.
- * jacc_batch_tune times every schedule candidate (band size in {4K, 8K, 16K,
- * 32K, 64K} points x CTAs per SM in {1, 2, max} x both orders) for
- * probe_sweeps sweeps on the batch's own buffers (their contents change),
- * keeps the fastest, and returns it and its time.  */
+ * Schedule (jacc_batch_config): target points per item (tile columns: the
+ * fewest 64-column strips, at most 8, that cover a row; rows = max(warps per
+ * strip, item_points / columns)), persistent CTAs per SM (0 = as many as
+ * fit), item order within a group (0: grid by grid, largest grid first;
+ * 1: round-robin over the group's grids), the L2 budget per group in bytes
+ * of both fields (0 = 40 % of the device's L2; -1 = one group), and the
+ * load path (march 0: each warp stages its rows in shared memory with
+ * cp.async, 8 rows deep; 1: rows marched through registers).  timeout_ms
+ * bounds every device wait (0 = 2000 ms).  test_stall_ticket is a
+ * fault-injection hook for tests: that ticket never reports completion, so
+ * the waits behind it time out; -1 = off.  jacc_batch_set_tiles overrides
+ * the tile of each grid (rows, cols; 0 = from item_points) and
+ * jacc_batch_get_tiles reports every grid's tile, item count and group.
+ * jacc_batch_tune times, for probe_sweeps sweeps on the batch's own buffers
+ * (their contents change), every combination of load path x CTAs per SM in
+ * {2, max} x L2 budget in {20 %, 40 %, 60 % of L2, one group} x item size in
+ * {4K, 8K, 16K} points, keeps the fastest, then times each group alone at
+ * item sizes {2K .. 32K} and gives that group's grids their best tile (kept
+ * only if the whole batch then runs faster); returns the schedule and its
+ * time.  */
 typedef struct {
   int64_t nx, ny; /* extents, each in [3, 2^31]                                   */
   void* u0;       /* device FP64 field [ny][nx], 16-byte aligned: sweep 0 input    */
@@ -561,12 +576,22 @@ typedef struct {
 } jacc_grid;
 
 typedef struct {
-  int32_t item_points;       /* target points per band; 0 = 16384                */
+  int32_t item_points;       /* target points per item; 0 = 8192                  */
   int32_t ctas_per_sm;       /* persistent CTAs per SM; 0 = as many as fit        */
-  int32_t order;             /* 0 largest grid first, 1 round-robin               */
+  int32_t order;             /* 0 grid by grid, 1 round-robin (within a group)    */
   int32_t timeout_ms;        /* bound on each device wait; 0 = 2000               */
   int64_t test_stall_ticket; /* fault injection for tests; -1 = off               */
+  int64_t group_bytes;       /* L2 budget per group; 0 = 40 % of L2, -1 = one     */
+  int32_t march;             /* 0 staged in shared memory, 1 registers            */
+  int32_t reserved;          /* 0                                                 */
 } jacc_batch_config;
+
+typedef struct {
+  int32_t rows;   /* rows per item (set: 0 = from item_points)                     */
+  int32_t cols;   /* columns per item: 64, 128, 256 or 512 (set: 0 = from nx)      */
+  int32_t nitems; /* items of the grid (get only)                                  */
+  int32_t group;  /* the grid's group (get only)                                   */
+} jacc_batch_tile;
 
 typedef struct jacc_batch_s* jacc_batch;
 
@@ -576,6 +601,10 @@ jacc_status jacc_batch_create(int32_t ngrids, const jacc_grid* grids, const jacc
 /* Replace the schedule (synchronous; drops cached graphs). */
 jacc_status jacc_batch_configure(jacc_batch b, const jacc_batch_config* cfg);
 jacc_status jacc_batch_get_config(jacc_batch b, jacc_batch_config* out);
+/* Per-grid tiles (arrays of ngrids entries, host memory); set replans
+ * synchronously and drops cached graphs. */
+jacc_status jacc_batch_set_tiles(jacc_batch b, int32_t ngrids, const jacc_batch_tile* tiles);
+jacc_status jacc_batch_get_tiles(jacc_batch b, int32_t ngrids, jacc_batch_tile* out);
 /* nsweeps ping-pong sweeps of every grid.  resid_dev (nullable, device,
  * ngrids * nsweeps doubles, row g = grid g) receives each grid's per-sweep
  * max |v - u| over its interior.  flags: JACC_SWEEP_GRAPH captures the

@@ -1,16 +1,36 @@
 // batched.cu - many uneven 5-point Jacobi grids in one persistent launch.
 //
 // No counterpart in the paper (which overlaps independent kernels on 16
-// OpenACC queues, §6.1).  All sweeps of all grids run inside one
-// cooperative launch whose CTAs are co-resident.  Work is a sequence of
-// tickets in sweep-major order: ticket t names sweep s = t / I and item
-// j = t % I of the schedule's item table (item = one band of rows of one
-// grid).  A CTA takes the next ticket, waits until every item of sweep s-1 of
-// that grid has finished (a per-grid completion counter), runs its band and
-// bumps the counter.  Every wait targets strictly smaller tickets, which were
-// handed to running CTAs earlier, so the smallest unfinished ticket always
-// progresses: no deadlock.  Waits are bounded by %globaltimer; a wait that
-// gives up writes JACC_ERR_TIMEOUT to the status word and every CTA leaves.
+// OpenACC queues, §6.1).  All sweeps of all grids run inside one cooperative
+// launch whose CTAs are co-resident.
+//
+// Work.  Each grid is cut into items: tiles of `rows` rows x `cols` columns
+// (cols = 64 x the warps across a tile).  Grids are packed into groups whose
+// two fields fit a budget of L2 bytes together.  Tickets run group by group,
+// sweep-major inside a group: ticket t of a group names sweep t / I and item
+// t % I of the group's I items.  A group's fields are read from HBM in its
+// first sweep and stay in L2 for the rest; the next group's tickets follow,
+// so CTAs that find no ready work in a group's last sweeps start the next one.
+//
+// Dependencies.  The 5-point item (b, c) of sweep s reads the rows above and
+// below it and the columns left and right of it, written in sweep s-1 by
+// items (b-1, c), (b+1, c), (b, c-1), (b, c+1) and itself, and overwrites
+// what those items read in sweep s-1.  So it waits until each of these five
+// items has finished s sweeps (a per-item counter), and then sets its own
+// counter to s + 1.  Every wait targets strictly smaller tickets.  Tickets
+// are handed out in order (one atomic counter; each CTA holds its current
+// ticket and a prefetched next one), so the smallest unfinished ticket is
+// always some CTA's current ticket, whose dependencies are finished: no
+// deadlock.  Waits are bounded by %globaltimer; a wait that gives up writes
+// JACC_ERR_TIMEOUT to the status word and every CTA leaves.
+//
+// Loads.  In the staged variant each warp streams its 64-column strip of an
+// item's rows through a ring of 8 rows in shared memory with 16-byte
+// cp.async.cg copies (L2 only: the same launch writes the fields, and L1 is
+// not coherent), so up to 7 rows per warp are in flight without registers.
+// A row whose start is not 16-byte aligned (odd nx, odd row) is staged one
+// element to the right.  The register variant marches rows through
+// registers with ld.global.cg, as the single-grid kernels do.
 #include <cuda_runtime.h>
 
 #include "../host/jacc_internal.h"
@@ -23,6 +43,9 @@ JD unsigned ld_acquire_u32(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
+}
+JD void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 JD int ld_relaxed_i32(const int* p) {
   int v;
@@ -47,78 +70,252 @@ JD int wait_done(const unsigned* done, unsigned target, int* status, u64 timeout
       atomicCAS(status, 0, JACC_ERR_TIMEOUT);
       return 1;
     }
-    __nanosleep(256);
+    __nanosleep(128);
   }
 }
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
+constexpr int kRing = 8;   // staged rows per warp (a power of two)
+constexpr int kSlot = 68;  // doubles per staged row: columns x0-2 .. x0+65 (one more when shifted)
+constexpr int kStagedSmem = kWarps * kRing * kSlot * 8;
 
-// One band: warps take 32*V-column chunks; the fixed-point path keeps the
-// field resident in fixed point between sweeps (flags: first sweep reads
-// FP64, last sweep writes FP64).
-template <int V, int MODE>
-JD void run_band(const JBGrid& G, const double* src, double* dst, i64 r0, i64 r1, int F, int flags,
-                 typename RT<double, MODE>::type& m) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const i64 chunk = 32 * V;
-  const i64 nchunks = (G.nx + chunk - 1) / chunk;
-  for (i64 c = warp; c < nchunks; c += kWarps) {
-    const i64 x0 = c * chunk + lane * V;
-    if constexpr (MODE == JM_FIXED) {
-      if (flags) jacobi_fx_march<V, true, true>(src, dst, G.nx, G.ny, x0, r0, r1, F, flags, m);
-      else jacobi_fx_march<V, true, false>(src, dst, G.nx, G.ny, x0, r0, r1, F, flags, m);
+// ---------------------------------------------------------------- staged march
+
+JD void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+JD void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> JD void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Stages the columns [x0-1, x0+64] of row r that lie in the grid.  Element x
+// goes to slot[x - x0 + 2 + sh], sh = (r * nx) & 1: 16-byte chunks start at
+// even element indices, chunk l (columns x0 - sh + 2l, +1) lands at
+// slot[2l + 2].  Lane l copies chunk l, lane 0 also chunk -1 (aligned rows),
+// lane 31 also chunk 32.  The array's last element, whose pair would run past
+// the end of the field, is loaded through a register instead.
+JD void stage_row(double* slot, const double* __restrict__ u, i64 nx, i64 ny, i64 r, i64 x0, int lane) {
+  if (r < 0 || r >= ny) return;
+  const i64 row0 = r * nx;
+  const int sh = (int)(row0 & 1);
+  const i64 clo = x0 >= 1 ? x0 - 1 : 0;
+  const i64 chi = x0 + 64 <= nx - 1 ? x0 + 64 : nx - 1;
+  const i64 n_all = nx * ny;
+  auto chunk = [&](int l) {
+    const i64 cf = x0 - sh + 2 * l;
+    if (cf > chi || cf + 1 < clo) return;
+    const i64 e = row0 + cf;
+    double* d = slot + 2 * l + 2;
+    if (e + 1 < n_all) cp_async16(d, u + e);
+    else d[0] = __ldcg(u + e);
+  };
+  if (lane == 0 && sh == 0) chunk(-1);
+  chunk(lane);
+  if (lane == 31) chunk(32);
+}
+
+// One warp: output rows [ya, yb) of columns [x0, x0 + 64) (lane: x0 + 2 lane
+// and the next column).  Arithmetic and outputs are those of jacobi_fx_march
+// (FX: resident 64-bit fixed point, EDGE: first or last sweep) or of the
+// native jacobi_march, value for value.
+template <bool FX, bool EDGE>
+JD void staged_march(double* ring, const double* __restrict__ u, double* __restrict__ v, i64 nx, i64 ny, i64 x0,
+                     i64 ya, i64 yb, int F, int flags, u64& rfx, double& rnat) {
+  const int lane = threadIdx.x & 31;
+  const i64 xa = x0 + 2 * lane;
+  const bool inf = EDGE && (flags & JFX_IN_F64);
+  const bool outf = EDGE && (flags & JFX_OUT_F64);
+  const bool c0 = xa < nx, c1 = xa + 1 < nx;
+  const bool in0 = xa >= 1 && xa <= nx - 2, in1 = xa + 1 >= 1 && xa + 1 <= nx - 2;
+  auto slot = [&](i64 r) -> double* { return ring + (int)((r + 1) & (kRing - 1)) * kSlot; };
+  auto shift = [&](i64 r) -> int { return (int)((r * nx) & 1); };
+  auto stage = [&](i64 r) {
+    if (r <= yb) stage_row(slot(r), u, nx, ny, r, x0, lane);
+    cp_async_commit();
+  };
+  auto own = [&](i64 r, double (&o)[2]) {
+    o[0] = o[1] = 0.0;
+    if (r < 0 || r >= ny || !c0) return;
+    const double* p = slot(r) + 2 * lane + 2 + shift(r);
+    if (shift(r) == 0 && c1) {
+      const double2 t = *reinterpret_cast<const double2*>(p);
+      o[0] = t.x;
+      o[1] = t.y;
     } else {
-      jacobi_march<double, V, MODE, true>(src, dst, G.nx, G.ny, x0, r0, r1, F, m);
+      o[0] = p[0];
+      if (c1) o[1] = p[1];
+    }
+  };
+  auto cvt = [&](double raw) -> i64 { return inf ? fx_from(raw, F) : bits_i64(raw); };
+
+  for (int j = 0; j < kRing; ++j) stage(ya - 1 + j);
+  cp_async_wait<kRing - 2>();  // rows ya-1 and ya
+  __syncwarp();
+  double rup[2], rcur[2];
+  own(ya - 1, rup);
+  own(ya, rcur);
+  __syncwarp();
+  stage(ya + kRing - 1);  // into the slot of row ya-1
+  for (i64 y = ya; y < yb; ++y) {
+    cp_async_wait<kRing - 2>();  // row y+1
+    __syncwarp();
+    double rdn[2];
+    own(y + 1, rdn);
+    const double* cs = slot(y) + 2 * lane + 2 + shift(y);
+    const double rl = in0 ? cs[-1] : 0.0;
+    const double rr = in1 ? cs[2] : 0.0;
+    const bool yint = y >= 1 && y <= ny - 2;
+    double out[2];
+    if constexpr (FX) {
+      const i64 up0 = cvt(rup[0]), up1 = cvt(rup[1]);
+      const i64 cu0 = cvt(rcur[0]), cu1 = cvt(rcur[1]);
+      const i64 dn0 = cvt(rdn[0]), dn1 = cvt(rdn[1]);
+      const i64 xl = cvt(rl), xr = cvt(rr);
+      const i64 s0 = (up0 + dn0) + (xl + cu1);
+      const i64 s1 = (up1 + dn1) + (cu0 + xr);
+      auto bnd = [&](double raw, i64 w) -> double {
+        if constexpr (!EDGE) return i64_bits(w);
+        if (inf && outf) return raw;
+        if (outf) return fx_to(w, F);
+        return i64_bits(w);
+      };
+      const bool a0 = yint && in0, a1 = yint && in1;
+      out[0] = a0 ? (outf ? fx_to(s0, F + 2) : i64_bits((s0 + 2) >> 2)) : bnd(rcur[0], cu0);
+      out[1] = a1 ? (outf ? fx_to(s1, F + 2) : i64_bits((s1 + 2) >> 2)) : bnd(rcur[1], cu1);
+      const i64 d0 = s0 - cu0 * 4, d1 = s1 - cu1 * 4;
+      const u64 ad0 = (u64)(d0 ^ (d0 >> 63)), ad1 = (u64)(d1 ^ (d1 >> 63));
+      if (a0 && ad0 > rfx) rfx = ad0;
+      if (a1 && ad1 > rfx) rfx = ad1;
+    } else {
+      const double s0 = (rup[0] + rdn[0]) + (rl + rcur[1]);
+      const double s1 = (rup[1] + rdn[1]) + (rcur[0] + rr);
+      const double q0 = 0.25 * s0, q1 = 0.25 * s1;
+      const bool a0 = yint && in0, a1 = yint && in1;
+      out[0] = a0 ? q0 : rcur[0];
+      out[1] = a1 ? q1 : rcur[1];
+      double e0 = q0 - rcur[0], e1 = q1 - rcur[1];
+      e0 = e0 < 0.0 ? -e0 : e0;
+      e1 = e1 < 0.0 ? -e1 : e1;
+      if (a0 && e0 > rnat) rnat = e0;
+      if (a1 && e1 > rnat) rnat = e1;
+    }
+    double* o = v + y * nx + xa;
+    if (c1 && shift(y) == 0) {
+      double2 t;
+      t.x = out[0];
+      t.y = out[1];
+      *reinterpret_cast<double2*>(o) = t;
+    } else if (c0) {
+      o[0] = out[0];
+      if (c1) o[1] = out[1];
+    }
+    rup[0] = rcur[0];
+    rup[1] = rcur[1];
+    rcur[0] = rdn[0];
+    rcur[1] = rdn[1];
+    __syncwarp();
+    stage(y + kRing);  // into the slot of row y
+  }
+  cp_async_wait<0>();  // no copy may land in the ring after the next unit starts with it
+  __syncwarp();
+}
+
+// ---------------------------------------------------------------- register march
+
+template <bool EDGE>
+JD void register_units(const JBGrid& G, const double* src, double* dst, i64 x0, i64 ya, i64 yb, int F, int flags,
+                       u64& rfx, double& rnat) {
+  if (G.nx % 2 == 0) {
+    if (F >= 0) jacobi_fx_march<2, true, EDGE>(src, dst, G.nx, G.ny, x0 + 2 * (threadIdx.x & 31), ya, yb, F, flags, rfx);
+    else jacobi_march<double, 2, JM_NATIVE, true>(src, dst, G.nx, G.ny, x0 + 2 * (threadIdx.x & 31), ya, yb, F, rnat);
+  } else {
+    for (int half = 0; half < 2; ++half) {
+      const i64 xl = x0 + 32 * half + (threadIdx.x & 31);
+      if (F >= 0) jacobi_fx_march<1, true, EDGE>(src, dst, G.nx, G.ny, xl, ya, yb, F, flags, rfx);
+      else jacobi_march<double, 1, JM_NATIVE, true>(src, dst, G.nx, G.ny, xl, ya, yb, F, rnat);
     }
   }
 }
 
+// ---------------------------------------------------------------- the persistent kernel
+
+template <int STAGED>
 __global__ void __launch_bounds__(kThreads, 3) jacc_k_batched(JBatchParams bp) {
+  extern __shared__ __align__(16) double s_ring[];
+  __shared__ int s_stop, s_sweep, s_item;
   __shared__ long long s_ticket;
-  __shared__ int s_stop;
-  const long long total = (long long)bp.total_items * bp.nsweeps;
+  long long next = -1;  // thread 0: prefetched ticket
+  int grp = 0;          // thread 0: group cursor (tickets only grow)
+  const int base_item = bp.groups[0].item_begin;
   for (;;) {
     if (threadIdx.x == 0) {
-      const long long t = (long long)atomicAdd(bp.ticket, 1ull);
-      int stop = t >= total;
+      const long long t = next >= 0 ? next : (long long)atomicAdd(bp.ticket, 1ull);
+      int stop = t >= bp.total_tickets;
       if (!stop) {
-        const int s = (int)(t / bp.total_items);
-        const JBItem it = bp.items[t % bp.total_items];
-        stop = wait_done(bp.done + it.g, (unsigned)s * (unsigned)bp.grids[it.g].nitems, bp.status, bp.timeout_ns);
+        next = (long long)atomicAdd(bp.ticket, 1ull);
+        while (grp + 1 < bp.ngroups &&
+               t >= (long long)(bp.groups[grp + 1].item_begin - base_item) * bp.nsweeps)
+          ++grp;
+        const JBGroup Q = bp.groups[grp];
+        const long long lt = t - (long long)(Q.item_begin - base_item) * bp.nsweeps;
+        const int s = (int)(lt / Q.nitems);
+        const int i = Q.item_begin + (int)(lt % Q.nitems);
+        const JBItem it = bp.items[i];
+        const JBGrid G = bp.grids[it.g];
+        const int self = G.item_base + it.b * G.nc + it.c;
+        const unsigned want = (unsigned)s;
+        stop = wait_done(bp.done + self, want, bp.status, bp.timeout_ns);
+        if (!stop && it.b > 0) stop = wait_done(bp.done + self - G.nc, want, bp.status, bp.timeout_ns);
+        if (!stop && it.b + 1 < G.nb) stop = wait_done(bp.done + self + G.nc, want, bp.status, bp.timeout_ns);
+        if (!stop && it.c > 0) stop = wait_done(bp.done + self - 1, want, bp.status, bp.timeout_ns);
+        if (!stop && it.c + 1 < G.nc) stop = wait_done(bp.done + self + 1, want, bp.status, bp.timeout_ns);
+        s_sweep = s;
+        s_item = i;
       }
       s_ticket = t;
       s_stop = stop;
     }
     __syncthreads();
     if (s_stop) break;
-    const long long t = s_ticket;
-    const int s = (int)(t / bp.total_items);
-    const JBItem it = bp.items[t % bp.total_items];
+    const int s = s_sweep;
+    const JBItem it = bp.items[s_item];
     const JBGrid G = bp.grids[it.g];
-    const i64 r0 = (i64)it.item * G.rows;
-    const i64 r1 = (r0 + G.rows < G.ny) ? r0 + G.rows : G.ny;
     const double* src = G.u[s & 1];
     double* dst = G.u[(s + 1) & 1];
     const int F = bp.maxwords ? fx_frac_bits(bp.maxwords[it.g]) : -1;
     const int flags = (s == 0 ? JFX_IN_F64 : 0) | (s == bp.nsweeps - 1 ? JFX_OUT_F64 : 0);
-    u64 bits;
-    if (F >= 0) {
-      u64 m = 0;
-      if (G.vec == 2) run_band<2, JM_FIXED>(G, src, dst, r0, r1, F, flags, m);
-      else run_band<1, JM_FIXED>(G, src, dst, r0, r1, F, flags, m);
-      bits = dbits(fx_to_u(m, F + 2));
-    } else {
-      double m = 0.0;
-      if (G.vec == 2) run_band<2, JM_NATIVE>(G, src, dst, r0, r1, F, flags, m);
-      else run_band<1, JM_NATIVE>(G, src, dst, r0, r1, F, flags, m);
-      bits = dbits(m);
+    // this warp's unit of the item: a 64-column strip of a slice of its rows
+    const int warp = threadIdx.x >> 5;
+    const int across = G.cols / 64;
+    const int slices = kWarps / across;
+    const i64 x0 = (i64)it.c * G.cols + 64 * (warp % across);
+    const i64 r0 = (i64)it.b * G.rows;
+    const i64 r1 = r0 + G.rows < G.ny ? r0 + G.rows : G.ny;
+    const i64 h = (r1 - r0 + slices - 1) / slices;
+    const i64 ya = r0 + (warp / across) * h;
+    const i64 yb = ya + h < r1 ? ya + h : r1;
+    u64 rfx = 0;
+    double rnat = 0.0;
+    if (x0 < G.nx && ya < yb) {
+      if constexpr (STAGED) {
+        double* ring = s_ring + warp * kRing * kSlot;
+        if (F >= 0) {
+          if (flags) staged_march<true, true>(ring, src, dst, G.nx, G.ny, x0, ya, yb, F, flags, rfx, rnat);
+          else staged_march<true, false>(ring, src, dst, G.nx, G.ny, x0, ya, yb, F, flags, rfx, rnat);
+        } else {
+          staged_march<false, false>(ring, src, dst, G.nx, G.ny, x0, ya, yb, F, flags, rfx, rnat);
+        }
+      } else {
+        if (flags) register_units<true>(G, src, dst, x0, ya, yb, F, flags, rfx, rnat);
+        else register_units<false>(G, src, dst, x0, ya, yb, F, flags, rfx, rnat);
+      }
     }
+    const u64 bits = F >= 0 ? dbits(fx_to_u(rfx, F + 2)) : dbits(rnat);
     block_max_to<kThreads>(bits, bp.resid ? bp.resid + (i64)it.g * bp.nsweeps + s : nullptr);
-    __syncthreads();  // every thread's stores of this band precede the signal
-    if (threadIdx.x == 0 && t != bp.stall_ticket) {
+    __syncthreads();  // every thread's stores of this item precede the signal
+    if (threadIdx.x == 0 && s_ticket != bp.stall_ticket) {
       __threadfence();
-      atomicAdd(bp.done + it.g, 1u);
+      st_release_u32(bp.done + G.item_base + it.b * G.nc + it.c, (unsigned)(s + 1));
     }
   }
 }
@@ -148,22 +345,28 @@ __global__ void __launch_bounds__(256) jacc_k_maxabs_batched(const JBGrid* grids
 
 namespace jacc {
 
-cudaError_t batched_occupancy(int* blocks_per_sm) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, jacc_k_batched, kThreads, 0);
+cudaError_t batched_occupancy(int staged, int* blocks_per_sm) {
+  if (staged) {
+    cudaError_t e = cudaFuncSetAttribute(jacc_k_batched<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStagedSmem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, jacc_k_batched<1>, kThreads, kStagedSmem);
+  }
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, jacc_k_batched<0>, kThreads, 0);
 }
 
 cudaError_t launch_batched(const JBatchParams& bp, int nctas, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)nctas);
   cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = bp.staged ? kStagedSmem : 0;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, jacc_k_batched, bp);
+  if (bp.staged) return cudaLaunchKernelEx(&cfg, jacc_k_batched<1>, bp);
+  return cudaLaunchKernelEx(&cfg, jacc_k_batched<0>, bp);
 }
 
 cudaError_t launch_maxabs_batched(const JBGrid* d_grids, int ngrids, i64 max_n, u64* maxwords, cudaStream_t s) {

@@ -73,7 +73,12 @@ class Grid(C.Structure):
 
 class BatchConfig(C.Structure):
     _fields_ = [("item_points", C.c_int32), ("ctas_per_sm", C.c_int32), ("order", C.c_int32),
-                ("timeout_ms", C.c_int32), ("test_stall_ticket", C.c_int64)]
+                ("timeout_ms", C.c_int32), ("test_stall_ticket", C.c_int64), ("group_bytes", C.c_int64),
+                ("march", C.c_int32), ("reserved", C.c_int32)]
+
+
+class BatchTile(C.Structure):
+    _fields_ = [("rows", C.c_int32), ("cols", C.c_int32), ("nitems", C.c_int32), ("group", C.c_int32)]
 
 
 class TuneResult(C.Structure):
@@ -131,6 +136,8 @@ SIGNATURES = {
     "jacc_batch_create": ([C.c_int32, P, P, P], C.c_int32),
     "jacc_batch_configure": ([P, P], C.c_int32),
     "jacc_batch_get_config": ([P, P], C.c_int32),
+    "jacc_batch_set_tiles": ([P, C.c_int32, P], C.c_int32),
+    "jacc_batch_get_tiles": ([P, C.c_int32, P], C.c_int32),
     "jacc_batch_sweep": ([P, C.c_int32, P, C.c_uint32, C.c_size_t, P], C.c_int32),
     "jacc_batch_status": ([P, C.c_size_t], C.c_int32),
     "jacc_batch_tune": ([P, C.c_int32, C.c_size_t, P, P], C.c_int32),
@@ -572,13 +579,14 @@ class Sched:
 
 def _cfg_dict(c):
     return dict(item_points=c.item_points, ctas_per_sm=c.ctas_per_sm, order=c.order, timeout_ms=c.timeout_ms,
-                test_stall_ticket=c.test_stall_ticket)
+                test_stall_ticket=c.test_stall_ticket, group_bytes=c.group_bytes, march=c.march)
 
 
-def _cfg_struct(item_points=0, ctas_per_sm=0, order=0, timeout_ms=0, test_stall_ticket=-1):
+def _cfg_struct(item_points=0, ctas_per_sm=0, order=0, timeout_ms=0, test_stall_ticket=-1, group_bytes=0, march=0):
     c = BatchConfig()
     c.item_points, c.ctas_per_sm, c.order = item_points, ctas_per_sm, order
     c.timeout_ms, c.test_stall_ticket = timeout_ms, test_stall_ticket
+    c.group_bytes, c.march, c.reserved = group_bytes, march, 0
     return c
 
 
@@ -626,6 +634,21 @@ class Batch:
     def status(self, stream=None):
         """JACC_OK or the status of the last run (raises JaccError on a timeout)."""
         _check(lib().jacc_batch_status(self.handle, _stream(stream)))
+
+    def tiles(self):
+        """Per grid: dict(rows, cols, nitems, group)."""
+        T = (BatchTile * self.n)()
+        _check(lib().jacc_batch_get_tiles(self.handle, self.n, C.cast(T, P)))
+        return [dict(rows=t.rows, cols=t.cols, nitems=t.nitems, group=t.group) for t in T]
+
+    def set_tiles(self, tiles):
+        """tiles: per grid (rows, cols); 0 = the default for item_points."""
+        if len(tiles) != self.n:
+            raise ValueError("one tile per grid")
+        T = (BatchTile * self.n)()
+        for g, (r, c) in enumerate(tiles):
+            T[g].rows, T[g].cols = int(r), int(c)
+        _check(lib().jacc_batch_set_tiles(self.handle, self.n, C.cast(T, P)))
 
     def tune(self, probe_sweeps=20, stream=None):
         c = BatchConfig()
