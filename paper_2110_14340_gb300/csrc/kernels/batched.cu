@@ -39,11 +39,6 @@
 
 namespace {
 
-JD unsigned ld_acquire_u32(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
 JD void st_release_u32(unsigned* p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -56,22 +51,6 @@ JD u64 globaltimer_ns() {
   u64 t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
-}
-
-// Bounded wait for *done >= target.  Returns 0 on success, 1 if the batch is
-// being abandoned (this wait timed out, or another CTA's did).
-JD int wait_done(const unsigned* done, unsigned target, int* status, u64 timeout_ns) {
-  if (ld_acquire_u32(done) >= target) return 0;
-  const u64 t0 = globaltimer_ns();
-  for (;;) {
-    if (ld_acquire_u32(done) >= target) return 0;
-    if (ld_relaxed_i32(status) != 0) return 1;
-    if (globaltimer_ns() - t0 > timeout_ns) {
-      atomicCAS(status, 0, JACC_ERR_TIMEOUT);
-      return 1;
-    }
-    __nanosleep(128);
-  }
 }
 
 constexpr int kThreads = 256;
@@ -238,54 +217,152 @@ JD void register_units(const JBGrid& G, const double* src, double* dst, i64 x0, 
 }
 
 // ---------------------------------------------------------------- the persistent kernel
+//
+// A CTA is 8 compute warps and one scheduler warp.  The scheduler takes the
+// next ticket, loads its item and grid and polls its five dependency
+// counters (one lane each, relaxed loads in parallel) while the compute
+// warps work on the current item; when they are done (named barrier 2) it
+// publishes the next item at once if it is ready (named barrier 1), and only
+// then makes the finished item visible (fence, release store of its
+// counter).  It signals the finished item before it blocks on anything, so
+// the smallest unfinished ticket is always some CTA's current item.
+
+constexpr int kCTA = kThreads + 32;  // compute warps + the scheduler warp
+
+JD void bar_sync(int id) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kCTA) : "memory"); }
+JD void bar_arrive(int id) { asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(kCTA) : "memory"); }
+JD unsigned ld_relaxed_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+struct Mailbox {
+  int stop;
+  int s;     // sweep
+  int item;  // entry of the item table
+};
+
+// Scheduler-side view of one ticket.
+struct Tk {
+  long long t;
+  int s, item, self;
+  int dep;  // this lane's counter (lanes 0..4: self, up, down, left, right), -1 if none
+};
+
+// Decodes ticket t (all lanes of the scheduler warp; grp is the group cursor).
+JD bool decode(const JBatchParams& bp, long long t, int& grp, int base_item, Tk& k) {
+  k.t = t;
+  if (t >= bp.total_tickets) return false;
+  while (grp + 1 < bp.ngroups && t >= (long long)(bp.groups[grp + 1].item_begin - base_item) * bp.nsweeps) ++grp;
+  const JBGroup Q = bp.groups[grp];
+  const long long lt = t - (long long)(Q.item_begin - base_item) * bp.nsweeps;
+  k.s = (int)(lt / Q.nitems);
+  k.item = Q.item_begin + (int)(lt % Q.nitems);
+  const JBItem it = bp.items[k.item];
+  const JBGrid G = bp.grids[it.g];
+  k.self = G.item_base + it.b * G.nc + it.c;
+  const int lane = threadIdx.x & 31;
+  k.dep = -1;
+  if (lane == 0) k.dep = k.self;
+  if (lane == 1 && it.b > 0) k.dep = k.self - G.nc;
+  if (lane == 2 && it.b + 1 < G.nb) k.dep = k.self + G.nc;
+  if (lane == 3 && it.c > 0) k.dep = k.self - 1;
+  if (lane == 4 && it.c + 1 < G.nc) k.dep = k.self + 1;
+  return true;
+}
+
+// One round of dependency loads: true when all five counters reach k.s.
+JD bool deps_ready(const JBatchParams& bp, const Tk& k) {
+  const bool ok = k.dep < 0 || ld_relaxed_u32(bp.done + k.dep) >= (unsigned)k.s;
+  return __all_sync(0xffffffffu, ok);
+}
+
+// Polls until ready; false if the batch is abandoned (timeout here or elsewhere).
+JD bool deps_wait(const JBatchParams& bp, const Tk& k) {
+  if (deps_ready(bp, k)) return true;
+  const u64 t0 = globaltimer_ns();
+  for (;;) {
+    __nanosleep(64);
+    if (deps_ready(bp, k)) return true;
+    int bad = 0;
+    if ((threadIdx.x & 31) == 0) {
+      bad = ld_relaxed_i32(bp.status) != 0;
+      if (!bad && globaltimer_ns() - t0 > bp.timeout_ns) {
+        atomicCAS(bp.status, 0, JACC_ERR_TIMEOUT);
+        bad = 1;
+      }
+    }
+    if (__shfl_sync(0xffffffffu, bad, 0)) return false;
+  }
+}
+
+JD void publish(Mailbox& mb, int stop, const Tk& k) {
+  if ((threadIdx.x & 31) == 0) {
+    mb.stop = stop;
+    mb.s = k.s;
+    mb.item = k.item;
+  }
+  __threadfence();  // acquire side of the relaxed dependency loads (every lane)
+  __syncwarp();
+  bar_sync(1);
+}
+
+JD void signal_done(const JBatchParams& bp, const Tk& k) {
+  if ((threadIdx.x & 31) == 0 && k.t != bp.stall_ticket) {
+    __threadfence();
+    st_release_u32(bp.done + k.self, (unsigned)(k.s + 1));
+  }
+}
 
 template <int STAGED>
-__global__ void __launch_bounds__(kThreads, 3) jacc_k_batched(JBatchParams bp) {
+__global__ void __launch_bounds__(kCTA, 3) jacc_k_batched(JBatchParams bp) {
   extern __shared__ __align__(16) double s_ring[];
-  __shared__ int s_stop, s_sweep, s_item;
-  __shared__ long long s_ticket;
-  long long next = -1;  // thread 0: prefetched ticket
-  int grp = 0;          // thread 0: group cursor (tickets only grow)
+  __shared__ Mailbox mb;
+  const int warp = threadIdx.x >> 5;
   const int base_item = bp.groups[0].item_begin;
-  for (;;) {
-    if (threadIdx.x == 0) {
-      const long long t = next >= 0 ? next : (long long)atomicAdd(bp.ticket, 1ull);
-      int stop = t >= bp.total_tickets;
-      if (!stop) {
-        next = (long long)atomicAdd(bp.ticket, 1ull);
-        while (grp + 1 < bp.ngroups &&
-               t >= (long long)(bp.groups[grp + 1].item_begin - base_item) * bp.nsweeps)
-          ++grp;
-        const JBGroup Q = bp.groups[grp];
-        const long long lt = t - (long long)(Q.item_begin - base_item) * bp.nsweeps;
-        const int s = (int)(lt / Q.nitems);
-        const int i = Q.item_begin + (int)(lt % Q.nitems);
-        const JBItem it = bp.items[i];
-        const JBGrid G = bp.grids[it.g];
-        const int self = G.item_base + it.b * G.nc + it.c;
-        const unsigned want = (unsigned)s;
-        stop = wait_done(bp.done + self, want, bp.status, bp.timeout_ns);
-        if (!stop && it.b > 0) stop = wait_done(bp.done + self - G.nc, want, bp.status, bp.timeout_ns);
-        if (!stop && it.b + 1 < G.nb) stop = wait_done(bp.done + self + G.nc, want, bp.status, bp.timeout_ns);
-        if (!stop && it.c > 0) stop = wait_done(bp.done + self - 1, want, bp.status, bp.timeout_ns);
-        if (!stop && it.c + 1 < G.nc) stop = wait_done(bp.done + self + 1, want, bp.status, bp.timeout_ns);
-        s_sweep = s;
-        s_item = i;
+  if (warp == kWarps) {
+    // ------------------------------------------------------------ scheduler warp
+    int grp = 0;
+    Tk cur;
+    long long t = 0;
+    if ((threadIdx.x & 31) == 0) t = (long long)atomicAdd(bp.ticket, 1ull);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    bool live = decode(bp, t, grp, base_item, cur) && deps_wait(bp, cur);
+    publish(mb, live ? 0 : 1, cur);
+    while (live) {
+      Tk nxt;
+      long long tn = 0;
+      if ((threadIdx.x & 31) == 0) tn = (long long)atomicAdd(bp.ticket, 1ull);
+      tn = __shfl_sync(0xffffffffu, tn, 0);
+      const bool has = decode(bp, tn, grp, base_item, nxt);
+      const bool ready = has && deps_ready(bp, nxt);
+      bar_sync(2);  // the compute warps are done with cur
+      if (ready) {
+        publish(mb, 0, nxt);
+        signal_done(bp, cur);
+      } else {
+        signal_done(bp, cur);
+        live = has && deps_wait(bp, nxt);
+        publish(mb, live ? 0 : 1, nxt);
       }
-      s_ticket = t;
-      s_stop = stop;
+      cur = nxt;
     }
-    __syncthreads();
-    if (s_stop) break;
-    const int s = s_sweep;
-    const JBItem it = bp.items[s_item];
+    return;
+  }
+  // -------------------------------------------------------------- compute warps
+  double* ring = s_ring + warp * kRing * kSlot;
+  for (;;) {
+    bar_sync(1);
+    if (mb.stop) break;
+    const int s = mb.s;
+    const JBItem it = bp.items[mb.item];
     const JBGrid G = bp.grids[it.g];
     const double* src = G.u[s & 1];
     double* dst = G.u[(s + 1) & 1];
     const int F = bp.maxwords ? fx_frac_bits(bp.maxwords[it.g]) : -1;
     const int flags = (s == 0 ? JFX_IN_F64 : 0) | (s == bp.nsweeps - 1 ? JFX_OUT_F64 : 0);
     // this warp's unit of the item: a 64-column strip of a slice of its rows
-    const int warp = threadIdx.x >> 5;
     const int across = G.cols / 64;
     const int slices = kWarps / across;
     const i64 x0 = (i64)it.c * G.cols + 64 * (warp % across);
@@ -298,7 +375,6 @@ __global__ void __launch_bounds__(kThreads, 3) jacc_k_batched(JBatchParams bp) {
     double rnat = 0.0;
     if (x0 < G.nx && ya < yb) {
       if constexpr (STAGED) {
-        double* ring = s_ring + warp * kRing * kSlot;
         if (F >= 0) {
           if (flags) staged_march<true, true>(ring, src, dst, G.nx, G.ny, x0, ya, yb, F, flags, rfx, rnat);
           else staged_march<true, false>(ring, src, dst, G.nx, G.ny, x0, ya, yb, F, flags, rfx, rnat);
@@ -310,13 +386,12 @@ __global__ void __launch_bounds__(kThreads, 3) jacc_k_batched(JBatchParams bp) {
         else register_units<false>(G, src, dst, x0, ya, yb, F, flags, rfx, rnat);
       }
     }
-    const u64 bits = F >= 0 ? dbits(fx_to_u(rfx, F + 2)) : dbits(rnat);
-    block_max_to<kThreads>(bits, bp.resid ? bp.resid + (i64)it.g * bp.nsweeps + s : nullptr);
-    __syncthreads();  // every thread's stores of this item precede the signal
-    if (threadIdx.x == 0 && s_ticket != bp.stall_ticket) {
-      __threadfence();
-      st_release_u32(bp.done + G.item_base + it.b * G.nc + it.c, (unsigned)(s + 1));
-    }
+    // the warp's residual maximum: one atomic per warp (non-negative doubles
+    // order like their bit patterns)
+    const u64 bits = warp_max_u64(F >= 0 ? dbits(fx_to_u(rfx, F + 2)) : dbits(rnat));
+    if ((threadIdx.x & 31) == 0 && bp.resid)
+      atomicMax(reinterpret_cast<unsigned long long*>(bp.resid + (i64)it.g * bp.nsweeps + s), (unsigned long long)bits);
+    bar_arrive(2);
   }
 }
 
@@ -349,15 +424,15 @@ cudaError_t batched_occupancy(int staged, int* blocks_per_sm) {
   if (staged) {
     cudaError_t e = cudaFuncSetAttribute(jacc_k_batched<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStagedSmem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, jacc_k_batched<1>, kThreads, kStagedSmem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, jacc_k_batched<1>, kCTA, kStagedSmem);
   }
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, jacc_k_batched<0>, kThreads, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, jacc_k_batched<0>, kCTA, 0);
 }
 
 cudaError_t launch_batched(const JBatchParams& bp, int nctas, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)nctas);
-  cfg.blockDim = dim3(kThreads);
+  cfg.blockDim = dim3(kCTA);
   cfg.dynamicSmemBytes = bp.staged ? kStagedSmem : 0;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
