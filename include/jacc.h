@@ -530,6 +530,59 @@ jacc_status jacc_costmodel_choose(jacc_costmodel m, const jacc_kernel_desc* desc
                                   int32_t* tile, int32_t* used_fallback);
 jacc_status jacc_costmodel_choose_topk(jacc_costmodel m, const jacc_kernel_desc* desc, void* u0, void* u1,
                                        uintptr_t stream, int32_t k, int32_t* tile);
+/* ---- the model's data pipeline, from raw autotuner tables (host memory).
+ * One jacc_tune_table row is one query (stencil, dtype, side) with the
+ * per-tile times jacc_autotune reported for it (ms, valid as in
+ * jacc_tune_result).
+ * fit_tables  : training set = every valid (query, tile): features as
+ *               jacc_costmodel_features, target = ln(1000 ms) minus the mean
+ *               of that over the query's valid tiles (the argmin over tiles
+ *               does not depend on a per-query constant, and centring keeps
+ *               the loss on the differences between tiles); then `epochs`
+ *               full-batch Adam steps at lr (jacc_costmodel_train).
+ *               *final_mse (nullable) = the loss before the last step.
+ *               Synchronous; allocates the training arrays on the device.
+ * evaluate    : per query: the model's pick (valid argmin of its
+ *               predictions, ties to the lowest tile; -1 if no tile is
+ *               valid), the top-2 predicted gap, regret = ms[pick] / min
+ *               over valid tiles of ms - 1, fallback = (gap < margin), and
+ *               for the model used as a filter (k = topk best-ranked valid
+ *               tiles timed, the fastest kept) its regret and the summed ms
+ *               of those k tiles.  Synchronous.
+ * fixed_tile  : the method without the model: the one tile valid for every
+ *               query with the lowest mean ln(ms) over the tables (host
+ *               only; UNSUPPORTED if no tile is valid everywhere).
+ * margin      : the decision margin at which the model falls back on at
+ *               most `fraction` of these queries: the largest gap g such
+ *               that fewer than fraction x nq queries have gap < g (0 for
+ *               fraction 0). */
+typedef struct {
+  int32_t stencil;               /* 5, 7 or 27                                */
+  int32_t dtype;                 /* 32 or 64                                  */
+  double side;                   /* grid side (> 0)                           */
+  double ms[JACC_NUM_TILES];     /* time per sweep of each tile               */
+  int32_t valid[JACC_NUM_TILES]; /* 1 where the tile fits and was timed       */
+} jacc_tune_table;
+
+typedef struct {
+  int32_t pick;          /* the model's tile, or -1                          */
+  int32_t fallback;      /* 1 if gap < margin                                */
+  double gap;            /* second-best minus best prediction (ln us)        */
+  double regret;         /* ms[pick] / best ms - 1                           */
+  double regret_topk;    /* regret of the fastest of the top-k ranked tiles  */
+  double search_ms_topk; /* sum of ms over those k tiles                      */
+} jacc_costmodel_eval;
+
+jacc_status jacc_costmodel_fit_tables(jacc_costmodel m, int32_t nq, const jacc_tune_table* tables, int32_t epochs,
+                                      float lr, uintptr_t stream, double* final_mse);
+jacc_status jacc_costmodel_evaluate(jacc_costmodel m, int32_t nq, const jacc_tune_table* tables, double margin,
+                                    int32_t topk, uintptr_t stream, jacc_costmodel_eval* out);
+jacc_status jacc_costmodel_fixed_tile(int32_t nq, const jacc_tune_table* tables, int32_t* tile);
+/* regret[q] = ms[picks[q]] / min over valid tiles of ms - 1 (host only);
+ * INVALID_ARG if a pick is out of range or not valid for its query. */
+jacc_status jacc_costmodel_regret(int32_t nq, const jacc_tune_table* tables, const int32_t* picks, double* regret);
+jacc_status jacc_costmodel_margin(jacc_costmodel m, int32_t nq, const jacc_tune_table* tables, double fraction,
+                                  uintptr_t stream, double* margin);
 jacc_status jacc_costmodel_save(jacc_costmodel m, const char* path);
 jacc_status jacc_costmodel_load(jacc_costmodel m, const char* path);
 jacc_status jacc_costmodel_release(jacc_costmodel m);

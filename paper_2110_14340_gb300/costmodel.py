@@ -1,21 +1,26 @@
-"""Learned launch-configuration cost model: data, training and regret.
+"""Learned launch-configuration cost model: timing runs and the evaluation report.
 
-No counterpart in the paper (auto-tuning is named as future work, §8).  The
-workflow, all on the GPU through libjacc.so:
+No counterpart in the paper (auto-tuning is named as future work, §8).  This
+module only orchestrates; every step of the method runs in libjacc.so:
 
 1. timing tables: for (stencil, dtype, side) the exhaustive autotuner
    (`jacc.autotune`) times all 24 tile configurations (median of 5 runs);
-2. training: the MLP (`jacc.CostModel`, FP32, 4 -> 3x64 -> 1) is fitted by
-   the library's own forward/backward/Adam kernels to ln(time in us) of
-   every valid (shape, tile) pair, centred per shape (see `xy`);
-3. evaluation on held-out sides: the model picks argmin over the 24 tiles;
-   regret = t(pick) / t(best) - 1 against the exhaustive search, compared
-   with the method without the model: one fixed default tile (the tile with
-   the lowest mean log-time over the training tables) and the library's
-   built-in default.
+2. training: `CostModel.fit_tables` (jacc_costmodel_fit_tables) builds the
+   features and the per-query centred ln(time in us) targets of every valid
+   (query, tile) and fits the MLP (FP32, 4 -> 3x64 -> 1) with the library's
+   own forward/backward/Adam kernels;
+3. evaluation on held-out sides (jacc_costmodel_evaluate): the model's pick,
+   its regret t(pick) / t(best) - 1 against the exhaustive search, the model
+   as a filter over its k best-ranked tiles, and the fallback to the
+   exhaustive search below a decision margin calibrated on the training
+   tables (jacc_costmodel_margin) so that it fires on a stated fraction of
+   queries.  The methods without the model: the best single tile over the
+   training tables (jacc_costmodel_fixed_tile) and the library's built-in
+   size-aware default; their regret also comes from the library
+   (jacc_costmodel_regret).
 
 Run the full configuration (about 2000 training timings over 5/7/27-point,
-FP32/FP64, sides 256-1024, and 200 held-out shapes):
+FP32/FP64, sides 256-1024, and 200 held-out shapes), three training seeds:
     python -m paper_2110_14340_gb300.costmodel --out results.json
 """
 import argparse
@@ -88,87 +93,18 @@ def collect(queries, bufs, reps=5, log=None):
         u0, u1 = bufs.fields(dt, (nx, ny, nz))
         # 4-sweep sequences: for FP64 fixed point two of them are the
         # intermediate sweeps that dominate long runs
-        spr = 4
         r = jacc.autotune(dict(stencil=st, dtype=dt, nx=nx, ny=ny, nz=nz, coeffs=coeffs_for(st)), u0, u1,
-                          sweeps_per_rep=spr, reps=reps)
+                          sweeps_per_rep=4, reps=reps)
         table.append(dict(stencil=st, dtype=dt, side=side, ms=r["ms"], valid=r["valid"]))
         if log:
             log(f"[{i + 1}/{len(queries)}] {st}pt f{dt} side {side}: best tile {r['best_tile']} {r['best_ms']:.4f} ms")
     return table
 
 
-def xy(table, centred=True):
-    """Feature rows and ln(time in microseconds) targets of every valid (shape, tile).
-
-    centred: subtract each shape's mean log-time over its valid tiles.  The
-    argmin over tiles is invariant to a per-shape constant, and without it
-    the squared error is dominated by the shape's overall scale (which grows
-    with side^3 and dtype) instead of the differences between tiles."""
-    X, Y = [], []
-    for q in table:
-        v = [t for t in range(NUM_TILES) if q["valid"][t]]
-        lt = [math.log(q["ms"][t] * 1e3) for t in v]
-        c = float(np.mean(lt)) if centred else 0.0
-        for t, y in zip(v, lt):
-            X.append(jacc.features(q["stencil"], q["side"], q["dtype"], t))
-            Y.append(y - c)
-    return np.asarray(X, dtype=np.float32), np.asarray(Y, dtype=np.float32)
-
-
-def query_features(table):
-    F = np.zeros((len(table), NUM_TILES, 4), dtype=np.float32)
-    V = np.zeros((len(table), NUM_TILES), dtype=np.int32)
-    for i, q in enumerate(table):
-        for t in range(NUM_TILES):
-            F[i, t] = jacc.features(q["stencil"], q["side"], q["dtype"], t)
-            V[i, t] = 1 if q["valid"][t] else 0
-    return F, V
-
-
-def fit(model, X, Y, epochs=3000, lr=1e-3):
-    import torch
-    x = torch.from_numpy(X).cuda()
-    y = torch.from_numpy(Y).cuda()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    loss = model.train(x, y, epochs, lr)
-    torch.cuda.synchronize()
-    return float(loss.item()), time.perf_counter() - t0
-
-
-def default_tile(train_table):
-    """The method without the model: one fixed tile, the lowest mean ln(time) over the training tables."""
-    s = np.zeros(NUM_TILES)
-    c = np.zeros(NUM_TILES)
-    for q in train_table:
-        for t in range(NUM_TILES):
-            if q["valid"][t]:
-                s[t] += math.log(q["ms"][t])
-                c[t] += 1
-    m = np.where(c == len(train_table), s / np.maximum(c, 1), np.inf)
-    return int(np.argmin(m))
-
-
-def regrets(table, picks):
-    out = []
-    for q, p in zip(table, picks):
-        ms = np.asarray(q["ms"])
-        best = np.min(ms[np.asarray(q["valid"], dtype=bool)])
-        out.append(ms[p] / best - 1.0 if p >= 0 and q["valid"][p] else np.inf)
-    return np.asarray(out)
-
-
 def summary(r):
-    r = np.asarray(r)
+    r = np.asarray(r, dtype=np.float64)
     return dict(mean=float(np.mean(r)), median=float(np.median(r)), p90=float(np.percentile(r, 90)),
                 max=float(np.max(r)), exact_best=float(np.mean(r == 0.0)))
-
-
-def margin_from_training(model, X, Y):
-    """Decision margin: half the model's RMS error on its own training targets."""
-    import torch
-    pred = model.predict(torch.from_numpy(X).cuda()).cpu().numpy()
-    return 0.5 * float(np.sqrt(np.mean((pred - Y) ** 2)))
 
 
 def library_default_tile(q):
@@ -181,51 +117,38 @@ def library_default_tile(q):
     return t
 
 
-def evaluate(model, train_table, test_table, margin=None):
-    import torch
-    F, V = query_features(test_table)
-    f = torch.from_numpy(F).cuda()
-    v = torch.from_numpy(V).cuda()
-    model.pick(f, v)  # warm
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    pred, pick, gap = model.pick(f, v)
-    e1.record()
-    torch.cuda.synchronize()
-    picks = pick.cpu().numpy()
-    dt = default_tile(train_table)
-    lib_default = [library_default_tile(q) for q in test_table]
-    out = dict(model=summary(regrets(test_table, picks)),
-               fixed_default_tile=dict(tile=dt, **summary(regrets(test_table, [dt] * len(test_table)))),
-               library_default_tile=summary(regrets(test_table, lib_default)),
-               inference_ms_all_queries=e0.elapsed_time(e1), queries=len(test_table))
-    # search cost the model saves: the exhaustive tuner times 24 tiles x 6 runs per query
-    out["exhaustive_search_ms_per_query"] = float(np.mean([6 * sum(m for m in q["ms"] if math.isfinite(m))
-                                                           for q in test_table]))
-    # the model as a filter: time only its k best predicted tiles and keep the
-    # fastest (the tables hold every tile's timing, so no new runs are needed)
-    P = pred.cpu().numpy()
-    for kk in (2, 3):
-        picks_k, cost = [], []
-        for i, q in enumerate(test_table):
-            valid = np.asarray(q["valid"], dtype=bool)
-            order = [t for t in np.argsort(P[i]) if valid[t]][:kk]
-            ms = np.asarray(q["ms"])
-            picks_k.append(int(order[int(np.argmin(ms[order]))]))
-            cost.append(6 * float(np.sum(ms[order])))
-        out[f"model_top{kk}_timed"] = dict(search_ms_per_query=float(np.mean(cost)),
-                                           **summary(regrets(test_table, picks_k)))
-    if margin is not None:
-        # model with its fallback: queries whose top-2 predicted gap is below the
-        # margin go to the exhaustive autotuner (regret 0, search cost paid)
-        g = gap.cpu().numpy()
-        fb = g < margin
-        r = regrets(test_table, picks)
-        r = np.where(fb, 0.0, r)
-        out["model_with_fallback"] = dict(margin=margin, fallback_fraction=float(np.mean(fb)), **summary(r))
-    return out, picks
+def search_ms(q):
+    """Timing cost of the exhaustive search for one query: 24 tiles x (1 warm-up + 5 timed) runs."""
+    return 6.0 * sum(m for m, v in zip(q["ms"], q["valid"]) if v)
+
+
+def baselines(train_table, test_table):
+    """Regret of the methods without the model on the held-out tables."""
+    ft = jacc.fixed_tile(train_table)
+    lib = [library_default_tile(q) for q in test_table]
+    return dict(fixed_tile=dict(tile=ft, **summary(jacc.regret(test_table, [ft] * len(test_table)))),
+                library_default_tile=summary(jacc.regret(test_table, lib)))
+
+
+def evaluate(model, train_table, test_table, fallback_fraction=0.25):
+    """The model's regret on the held-out tables: argmin pick, filter over its 2 or 3 best-ranked tiles,
+    and with a fallback to the exhaustive search calibrated on the training tables."""
+    exhaustive = float(np.mean([search_ms(q) for q in test_table]))
+    out = dict(queries=len(test_table), exhaustive_search_ms_per_query=exhaustive)
+    ev = model.evaluate(test_table, margin=0.0, topk=1)
+    out["model"] = summary([e["regret"] for e in ev])
+    for k in (2, 3):
+        evk = model.evaluate(test_table, margin=0.0, topk=k)
+        out[f"model_top{k}_timed"] = dict(search_ms_per_query=6.0 * float(np.mean([e["search_ms_topk"] for e in evk])),
+                                          **summary([e["regret_topk"] for e in evk]))
+    margin = model.margin(train_table, fallback_fraction)
+    evm = model.evaluate(test_table, margin=margin, topk=1)
+    fb = np.array([e["fallback"] for e in evm])
+    r = np.where(fb, 0.0, [e["regret"] for e in evm])
+    out["model_with_fallback"] = dict(margin=margin, calibrated_fraction=fallback_fraction,
+                                      fallback_fraction=float(np.mean(fb)),
+                                      search_ms_per_query=float(np.mean(fb)) * exhaustive, **summary(r))
+    return out, [e["pick"] for e in ev]
 
 
 def main():
@@ -236,7 +159,8 @@ def main():
     ap.add_argument("--epochs", type=int, default=40000)
     ap.add_argument("--max-side", type=int, default=1024)
     ap.add_argument("--lr", type=float, default=3e-4)
-    ap.add_argument("--seed", type=int, default=5)
+    ap.add_argument("--seeds", default="5,6,7", help="training seeds (comma-separated)")
+    ap.add_argument("--fallback-fraction", type=float, default=0.25)
     ap.add_argument("--tables", default=None,
                     help="reuse the timing tables of an earlier --out file instead of collecting them")
     args = ap.parse_args()
@@ -261,13 +185,18 @@ def main():
         train_table = collect(train_q, bufs, log=print)
         test_table = collect(test_q, bufs, log=print)
         t_collect = time.perf_counter() - t0
-    X, Y = xy(train_table)
-    model = jacc.CostModel(seed=args.seed)
-    loss, t_train = fit(model, X, Y, args.epochs, args.lr)
-    margin = margin_from_training(model, X, Y)
-    res, _ = evaluate(model, train_table, test_table, margin)
-    res.update(train_samples=int(len(Y)), final_train_mse=loss, train_seconds=t_train, collect_seconds=t_collect,
-               epochs=args.epochs, lr=args.lr, seed=args.seed, train_sides=tr, heldout_sides=ho)
+    res = dict(baselines=baselines(train_table, test_table), seeds={}, collect_seconds=t_collect,
+               epochs=args.epochs, lr=args.lr, train_sides=tr, heldout_sides=ho,
+               train_samples=int(sum(sum(1 for v in q["valid"] if v) for q in train_table)))
+    for seed in [int(x) for x in args.seeds.split(",")]:
+        model = jacc.CostModel(seed=seed)
+        t0 = time.perf_counter()
+        mse = model.fit_tables(train_table, args.epochs, args.lr)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        ev, _ = evaluate(model, train_table, test_table, args.fallback_fraction)
+        res["seeds"][str(seed)] = dict(final_train_mse=mse, train_seconds=t_train, **ev)
+        model.release()
     print(json.dumps(res, indent=1))
     if args.out:
         with open(args.out, "w") as f:

@@ -320,6 +320,181 @@ extern "C" jacc_status jacc_costmodel_choose_topk(jacc_costmodel h, const jacc_k
   return ok();
 }
 
+// ---------------------------------------------------------------- pipeline from autotuner tables
+
+namespace jacc {
+
+static bool table_ok(const jacc_tune_table& q) {
+  return (q.stencil == 5 || q.stencil == 7 || q.stencil == 27) && (q.dtype == 32 || q.dtype == 64) && q.side > 0.0;
+}
+
+// Predictions for every (query, tile) of the tables: pred[q * 24 + t].
+static jacc_status predict_tables(jacc_costmodel h, int32_t nq, const jacc_tune_table* tables, cudaStream_t s,
+                                  std::vector<float>& pred) {
+  const size_t rows = static_cast<size_t>(nq) * JACC_NUM_TILES;
+  std::vector<float> feats(rows * 4);
+  for (int32_t q = 0; q < nq; ++q)
+    for (int t = 0; t < JACC_NUM_TILES; ++t)
+      jacc_costmodel_features(tables[q].stencil, tables[q].side, tables[q].dtype, t, &feats[(q * JACC_NUM_TILES + t) * 4]);
+  float* d = nullptr;
+  jacc_status st = cuda_check(cudaMalloc(reinterpret_cast<void**>(&d), sizeof(float) * rows * 5), "cudaMalloc(eval)");
+  if (st) return st;
+  pred.resize(rows);
+  st = cuda_check(cudaMemcpyAsync(d, feats.data(), sizeof(float) * rows * 4, cudaMemcpyHostToDevice, s), "upload");
+  if (!st) st = jacc_costmodel_predict(h, d, static_cast<int32_t>(rows), d + rows * 4, reinterpret_cast<uintptr_t>(s));
+  if (!st)
+    st = cuda_check(cudaMemcpyAsync(pred.data(), d + rows * 4, sizeof(float) * rows, cudaMemcpyDeviceToHost, s), "read");
+  if (!st) st = cuda_check(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  cudaFree(d);
+  return st;
+}
+
+// Valid tiles of one query ordered by prediction (ties to the lower tile).
+static std::vector<int> ranked(const jacc_tune_table& q, const float* pred) {
+  std::vector<int> order;
+  for (int t = 0; t < JACC_NUM_TILES; ++t)
+    if (q.valid[t]) order.push_back(t);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return pred[a] < pred[b]; });
+  return order;
+}
+
+static double best_ms(const jacc_tune_table& q) {
+  double b = 1e300;
+  for (int t = 0; t < JACC_NUM_TILES; ++t)
+    if (q.valid[t] && q.ms[t] < b) b = q.ms[t];
+  return b;
+}
+
+}  // namespace jacc
+
+extern "C" jacc_status jacc_costmodel_fit_tables(jacc_costmodel h, int32_t nq, const jacc_tune_table* tables,
+                                                 int32_t epochs, float lr, uintptr_t stream, double* final_mse) {
+  if (!h || nq < 1 || !tables || epochs < 1 || !(lr > 0.f)) return fail(JACC_ERR_INVALID_ARG, "bad fit_tables arguments");
+  std::vector<float> X, Y;
+  for (int32_t q = 0; q < nq; ++q) {
+    const jacc_tune_table& T = tables[q];
+    if (!table_ok(T)) return fail(JACC_ERR_INVALID_ARG, "bad table row " + std::to_string(q));
+    double sum = 0.0;
+    int n = 0;
+    for (int t = 0; t < JACC_NUM_TILES; ++t)
+      if (T.valid[t]) {
+        if (!(T.ms[t] > 0.0) || !std::isfinite(T.ms[t]))
+          return fail(JACC_ERR_INVALID_ARG, "a valid tile needs a finite positive time");
+        sum += std::log(T.ms[t] * 1e3);
+        ++n;
+      }
+    if (n == 0) continue;
+    const double mean = sum / n;
+    for (int t = 0; t < JACC_NUM_TILES; ++t)
+      if (T.valid[t]) {
+        float f[4];
+        jacc_costmodel_features(T.stencil, T.side, T.dtype, t, f);
+        X.insert(X.end(), f, f + 4);
+        Y.push_back(static_cast<float>(std::log(T.ms[t] * 1e3) - mean));
+      }
+  }
+  if (Y.empty()) return fail(JACC_ERR_INVALID_ARG, "no valid (query, tile) pair to train on");
+  const size_t n = Y.size();
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  float* d = nullptr;
+  jacc_status st = cuda_check(cudaMalloc(reinterpret_cast<void**>(&d), sizeof(float) * (5 * n + 1)), "cudaMalloc(fit)");
+  if (st) return st;
+  st = cuda_check(cudaMemcpyAsync(d, X.data(), sizeof(float) * 4 * n, cudaMemcpyHostToDevice, s), "upload features");
+  if (!st) st = cuda_check(cudaMemcpyAsync(d + 4 * n, Y.data(), sizeof(float) * n, cudaMemcpyHostToDevice, s), "upload targets");
+  if (!st) st = jacc_costmodel_train(h, d, d + 4 * n, static_cast<int32_t>(n), epochs, lr, stream, d + 5 * n);
+  float loss = 0.f;
+  if (!st) st = cuda_check(cudaMemcpyAsync(&loss, d + 5 * n, sizeof(float), cudaMemcpyDeviceToHost, s), "read loss");
+  if (!st) st = cuda_check(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  cudaFree(d);
+  if (!st && final_mse) *final_mse = loss;
+  return st;
+}
+
+extern "C" jacc_status jacc_costmodel_evaluate(jacc_costmodel h, int32_t nq, const jacc_tune_table* tables, double margin,
+                                               int32_t topk, uintptr_t stream, jacc_costmodel_eval* out) {
+  if (!h || nq < 1 || !tables || !out || topk < 1 || !(margin >= 0.0))
+    return fail(JACC_ERR_INVALID_ARG, "bad evaluate arguments");
+  for (int32_t q = 0; q < nq; ++q)
+    if (!table_ok(tables[q])) return fail(JACC_ERR_INVALID_ARG, "bad table row " + std::to_string(q));
+  std::vector<float> pred;
+  jacc_status st = predict_tables(h, nq, tables, reinterpret_cast<cudaStream_t>(stream), pred);
+  if (st) return st;
+  for (int32_t q = 0; q < nq; ++q) {
+    const jacc_tune_table& T = tables[q];
+    const std::vector<int> order = ranked(T, &pred[static_cast<size_t>(q) * JACC_NUM_TILES]);
+    jacc_costmodel_eval& e = out[q];
+    if (order.empty()) {
+      e = jacc_costmodel_eval{-1, 1, 0.0, 0.0, 0.0, 0.0};
+      continue;
+    }
+    const float* pq = &pred[static_cast<size_t>(q) * JACC_NUM_TILES];
+    const double best = best_ms(T);
+    e.pick = order[0];
+    e.gap = order.size() > 1 ? static_cast<double>(pq[order[1]]) - static_cast<double>(pq[order[0]]) : 1e300;
+    e.fallback = e.gap < margin ? 1 : 0;
+    e.regret = T.ms[e.pick] / best - 1.0;
+    const size_t k = std::min<size_t>(static_cast<size_t>(topk), order.size());
+    double fastest = 1e300, cost = 0.0;
+    for (size_t i = 0; i < k; ++i) {
+      fastest = std::min(fastest, T.ms[order[i]]);
+      cost += T.ms[order[i]];
+    }
+    e.regret_topk = fastest / best - 1.0;
+    e.search_ms_topk = cost;
+  }
+  return ok();
+}
+
+extern "C" jacc_status jacc_costmodel_fixed_tile(int32_t nq, const jacc_tune_table* tables, int32_t* tile) {
+  if (nq < 1 || !tables || !tile) return fail(JACC_ERR_INVALID_ARG, "bad fixed_tile arguments");
+  int best = -1;
+  double best_mean = 1e300;
+  for (int t = 0; t < JACC_NUM_TILES; ++t) {
+    double sum = 0.0;
+    bool everywhere = true;
+    for (int32_t q = 0; q < nq && everywhere; ++q) {
+      if (!tables[q].valid[t] || !(tables[q].ms[t] > 0.0)) everywhere = false;
+      else sum += std::log(tables[q].ms[t]);
+    }
+    if (everywhere && sum / nq < best_mean) {
+      best_mean = sum / nq;
+      best = t;
+    }
+  }
+  if (best < 0) return fail(JACC_ERR_UNSUPPORTED, "no tile is valid for every query");
+  *tile = best;
+  return ok();
+}
+
+extern "C" jacc_status jacc_costmodel_regret(int32_t nq, const jacc_tune_table* tables, const int32_t* picks,
+                                             double* regret) {
+  if (nq < 1 || !tables || !picks || !regret) return fail(JACC_ERR_INVALID_ARG, "bad regret arguments");
+  for (int32_t q = 0; q < nq; ++q) {
+    const int32_t p = picks[q];
+    if (p < 0 || p >= JACC_NUM_TILES || !tables[q].valid[p])
+      return fail(JACC_ERR_INVALID_ARG, "pick " + std::to_string(p) + " is not a valid tile of query " + std::to_string(q));
+    regret[q] = tables[q].ms[p] / best_ms(tables[q]) - 1.0;
+  }
+  return ok();
+}
+
+extern "C" jacc_status jacc_costmodel_margin(jacc_costmodel h, int32_t nq, const jacc_tune_table* tables, double fraction,
+                                             uintptr_t stream, double* margin) {
+  if (!h || nq < 1 || !tables || !margin || !(fraction >= 0.0 && fraction <= 1.0))
+    return fail(JACC_ERR_INVALID_ARG, "bad margin arguments");
+  std::vector<jacc_costmodel_eval> ev(static_cast<size_t>(nq));
+  jacc_status st = jacc_costmodel_evaluate(h, nq, tables, 0.0, 1, stream, ev.data());
+  if (st) return st;
+  std::vector<double> gaps;
+  for (const auto& e : ev)
+    if (e.pick >= 0) gaps.push_back(e.gap);
+  std::sort(gaps.begin(), gaps.end());
+  // the largest g with #{gap < g} < fraction * nq: the gap of rank floor(fraction * nq)
+  const size_t r = static_cast<size_t>(std::floor(fraction * static_cast<double>(gaps.size())));
+  *margin = (r == 0 || gaps.empty()) ? 0.0 : gaps[std::min(r, gaps.size()) - 1];
+  return ok();
+}
+
 extern "C" jacc_status jacc_costmodel_save(jacc_costmodel h, const char* path) {
   if (!h || !path) return fail(JACC_ERR_INVALID_ARG, "NULL model or path");
   CostModel& m = *reinterpret_cast<CostModel*>(h);

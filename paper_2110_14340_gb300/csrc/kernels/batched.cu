@@ -25,9 +25,10 @@
 // JACC_ERR_TIMEOUT to the status word and every CTA leaves.
 //
 // Loads.  In the staged variant each warp streams its 64-column strip of an
-// item's rows through a ring of 8 rows in shared memory with 16-byte
+// item's rows through a ring of 16 rows in shared memory with 16-byte
 // cp.async.cg copies (L2 only: the same launch writes the fields, and L1 is
-// not coherent), so up to 7 rows per warp are in flight without registers.
+// not coherent), so up to 15 rows per warp are in flight without registers
+// (at HBM latency under load, a shallower ring leaves each warp waiting).
 // A row whose start is not 16-byte aligned (odd nx, odd row) is staged one
 // element to the right.  The register variant marches rows through
 // registers with ld.global.cg, as the single-grid kernels do.
@@ -55,7 +56,7 @@ JD u64 globaltimer_ns() {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kRing = 8;   // staged rows per warp (a power of two)
+constexpr int kRing = 16;  // staged rows per warp (a power of two)
 constexpr int kSlot = 68;  // doubles per staged row: columns x0-2 .. x0+65 (one more when shifted)
 constexpr int kStagedSmem = kWarps * kRing * kSlot * 8;
 
@@ -237,17 +238,24 @@ JD unsigned ld_relaxed_u32(const unsigned* p) {
   return v;
 }
 
+// The item the compute warps run next, with its grid's descriptor and
+// fixed-point scale, so they load nothing but field data.
 struct Mailbox {
   int stop;
-  int s;     // sweep
-  int item;  // entry of the item table
+  int s;  // sweep
+  int F;  // fraction bits of the grid's fixed-point form, -1: native FP64
+  int pad_;
+  JBItem it;
+  JBGrid G;
 };
 
 // Scheduler-side view of one ticket.
 struct Tk {
   long long t;
-  int s, item, self;
+  int s, self, F;
   int dep;  // this lane's counter (lanes 0..4: self, up, down, left, right), -1 if none
+  JBItem it;
+  JBGrid G;
 };
 
 // Decodes ticket t (all lanes of the scheduler warp; grp is the group cursor).
@@ -258,9 +266,11 @@ JD bool decode(const JBatchParams& bp, long long t, int& grp, int base_item, Tk&
   const JBGroup Q = bp.groups[grp];
   const long long lt = t - (long long)(Q.item_begin - base_item) * bp.nsweeps;
   k.s = (int)(lt / Q.nitems);
-  k.item = Q.item_begin + (int)(lt % Q.nitems);
-  const JBItem it = bp.items[k.item];
-  const JBGrid G = bp.grids[it.g];
+  k.it = bp.items[Q.item_begin + (int)(lt % Q.nitems)];
+  const JBItem it = k.it;
+  k.G = bp.grids[it.g];
+  const JBGrid& G = k.G;
+  k.F = bp.maxwords ? fx_frac_bits(bp.maxwords[it.g]) : -1;
   k.self = G.item_base + it.b * G.nc + it.c;
   const int lane = threadIdx.x & 31;
   k.dep = -1;
@@ -301,7 +311,9 @@ JD void publish(Mailbox& mb, int stop, const Tk& k) {
   if ((threadIdx.x & 31) == 0) {
     mb.stop = stop;
     mb.s = k.s;
-    mb.item = k.item;
+    mb.F = k.F;
+    mb.it = k.it;
+    mb.G = k.G;
   }
   __threadfence();  // acquire side of the relaxed dependency loads (every lane)
   __syncwarp();
@@ -356,11 +368,11 @@ __global__ void __launch_bounds__(kCTA, 3) jacc_k_batched(JBatchParams bp) {
     bar_sync(1);
     if (mb.stop) break;
     const int s = mb.s;
-    const JBItem it = bp.items[mb.item];
-    const JBGrid G = bp.grids[it.g];
+    const int F = mb.F;
+    const JBItem it = mb.it;
+    const JBGrid G = mb.G;
     const double* src = G.u[s & 1];
     double* dst = G.u[(s + 1) & 1];
-    const int F = bp.maxwords ? fx_frac_bits(bp.maxwords[it.g]) : -1;
     const int flags = (s == 0 ? JFX_IN_F64 : 0) | (s == bp.nsweeps - 1 ? JFX_OUT_F64 : 0);
     // this warp's unit of the item: a 64-column strip of a slice of its rows
     const int across = G.cols / 64;

@@ -77,6 +77,16 @@ class BatchConfig(C.Structure):
                 ("march", C.c_int32), ("reserved", C.c_int32)]
 
 
+class TuneTable(C.Structure):
+    _fields_ = [("stencil", C.c_int32), ("dtype", C.c_int32), ("side", C.c_double),
+                ("ms", C.c_double * NUM_TILES), ("valid", C.c_int32 * NUM_TILES)]
+
+
+class CostModelEval(C.Structure):
+    _fields_ = [("pick", C.c_int32), ("fallback", C.c_int32), ("gap", C.c_double), ("regret", C.c_double),
+                ("regret_topk", C.c_double), ("search_ms_topk", C.c_double)]
+
+
 class BatchTile(C.Structure):
     _fields_ = [("rows", C.c_int32), ("cols", C.c_int32), ("nitems", C.c_int32), ("group", C.c_int32)]
 
@@ -156,6 +166,11 @@ SIGNATURES = {
     "jacc_costmodel_set_range": ([P, C.c_double, C.c_double, C.c_double], C.c_int32),
     "jacc_costmodel_choose": ([P, P, P, P, C.c_size_t, P, P], C.c_int32),
     "jacc_costmodel_choose_topk": ([P, P, P, P, C.c_size_t, C.c_int32, P], C.c_int32),
+    "jacc_costmodel_fit_tables": ([P, C.c_int32, P, C.c_int32, C.c_float, C.c_size_t, P], C.c_int32),
+    "jacc_costmodel_evaluate": ([P, C.c_int32, P, C.c_double, C.c_int32, C.c_size_t, P], C.c_int32),
+    "jacc_costmodel_fixed_tile": ([C.c_int32, P, P], C.c_int32),
+    "jacc_costmodel_regret": ([C.c_int32, P, P, P], C.c_int32),
+    "jacc_costmodel_margin": ([P, C.c_int32, P, C.c_double, C.c_size_t, P], C.c_int32),
     "jacc_costmodel_save": ([P, C.c_char_p], C.c_int32),
     "jacc_costmodel_load": ([P, C.c_char_p], C.c_int32),
     "jacc_costmodel_release": ([P], C.c_int32),
@@ -707,6 +722,35 @@ def features(stencil, side, dtype, tile):
     return list(out)
 
 
+def tune_tables(tables):
+    """ctypes array of jacc_tune_table rows from dicts (stencil, dtype, side, ms[24], valid[24])."""
+    T = (TuneTable * max(1, len(tables)))()
+    for i, q in enumerate(tables):
+        T[i].stencil, T[i].dtype, T[i].side = int(q["stencil"]), int(q["dtype"]), float(q["side"])
+        for t in range(NUM_TILES):
+            v = bool(q["valid"][t])
+            T[i].valid[t] = 1 if v else 0
+            T[i].ms[t] = float(q["ms"][t]) if v else 0.0
+    return T
+
+
+def fixed_tile(tables):
+    """The best single tile over the tables (the method without the model)."""
+    T = tune_tables(tables)
+    t = C.c_int32(-1)
+    _check(lib().jacc_costmodel_fixed_tile(len(tables), C.cast(T, P), C.byref(t)))
+    return t.value
+
+
+def regret(tables, picks):
+    """Per query: ms[pick] / best ms - 1, by the library."""
+    T = tune_tables(tables)
+    pk = (C.c_int32 * max(1, len(tables)))(*[int(p) for p in picks])
+    out = (C.c_double * max(1, len(tables)))()
+    _check(lib().jacc_costmodel_regret(len(tables), C.cast(T, P), C.cast(pk, P), C.cast(out, P)))
+    return list(out[:len(tables)])
+
+
 def _f32(t, n=None, name="tensor"):
     import torch
     if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
@@ -799,6 +843,31 @@ class CostModel:
         _check(lib().jacc_costmodel_choose_topk(self.handle, C.byref(d.desc), _field(d, u0, "u0"),
                                                 _field(d, u1, "u1"), _stream(stream), int(k), C.byref(t)))
         return t.value
+
+    def fit_tables(self, tables, epochs, lr=1e-3, stream=None):
+        """Train on autotuner tables (list of dict(stencil, dtype, side, ms[24], valid[24])); returns the final MSE."""
+        T = tune_tables(tables)
+        mse = C.c_double(0.0)
+        _check(lib().jacc_costmodel_fit_tables(self.handle, len(tables), C.cast(T, P), int(epochs), float(lr),
+                                               _stream(stream), C.byref(mse)))
+        return mse.value
+
+    def evaluate(self, tables, margin=0.0, topk=1, stream=None):
+        """Per query: dict(pick, fallback, gap, regret, regret_topk, search_ms_topk)."""
+        T = tune_tables(tables)
+        E = (CostModelEval * len(tables))()
+        _check(lib().jacc_costmodel_evaluate(self.handle, len(tables), C.cast(T, P), float(margin), int(topk),
+                                             _stream(stream), C.cast(E, P)))
+        return [dict(pick=e.pick, fallback=bool(e.fallback), gap=e.gap, regret=e.regret, regret_topk=e.regret_topk,
+                     search_ms_topk=e.search_ms_topk) for e in E]
+
+    def margin(self, tables, fraction, stream=None):
+        """The decision margin at which at most `fraction` of these queries fall back."""
+        T = tune_tables(tables)
+        m = C.c_double(0.0)
+        _check(lib().jacc_costmodel_margin(self.handle, len(tables), C.cast(T, P), float(fraction), _stream(stream),
+                                           C.byref(m)))
+        return m.value
 
     def save(self, path):
         _check(lib().jacc_costmodel_save(self.handle, path.encode()))

@@ -89,3 +89,31 @@ def test_region_analysis_matches_oracle_bit_exactly(lib, orc):
         assert st_o == st_j, (loops, refs, arrays)
         if st_o in (0, -2):
             assert out_o == out_j, (loops, refs, arrays)
+
+
+def _table(stencil, dtype, side, ms, valid):
+    return dict(stencil=stencil, dtype=dtype, side=side, ms=ms, valid=valid)
+
+
+def test_costmodel_fixed_tile_and_regret_host_calls(lib):
+    # three queries; tile 2 has the lowest times but is invalid in query 1,
+    # so the best tile valid everywhere is tile 5 (lowest mean ln time)
+    ms = [[10.0] * 24 for _ in range(3)]
+    valid = [[1] * 24 for _ in range(3)]
+    for q in range(3):
+        ms[q][2] = 1.0
+        ms[q][5] = 2.0 + q  # mean ln = ln(2*3*4)/3
+        ms[q][9] = 3.0      # mean ln = ln 3 > ln(24)/3 = 1.059
+    valid[1][2] = 0
+    tables = [_table(7, 64, 300.0 + q, ms[q], valid[q]) for q in range(3)]
+    assert jacc.fixed_tile(tables) == 5
+    r = jacc.regret(tables, [5, 9, 2])
+    assert r == [2.0 / 1.0 - 1.0, 3.0 / 3.0 - 1.0, 1.0 / 1.0 - 1.0]  # query 1's best valid tile is 9 (3.0 < 3.0 + 1)
+    with pytest.raises(jacc.JaccError):
+        jacc.regret(tables, [2, 2, 2])  # tile 2 is not valid for query 1
+    with pytest.raises(jacc.JaccError):
+        jacc.regret(tables, [24, 0, 0])
+    nothing = [_table(5, 32, 100.0, [1.0] * 24, [0] * 24)]
+    with pytest.raises(jacc.JaccError) as e:
+        jacc.fixed_tile(nothing)
+    assert e.value.status == jacc.ERR_UNSUPPORTED

@@ -174,11 +174,95 @@ def test_choose_falls_back_outside_the_training_range():
     jacc.autotune_forget()
 
 
+def _synthetic_tables(seed, nq):
+    """Tables of made-up timings (log-normal around a shape trend), some tiles invalid."""
+    rng = np.random.default_rng(seed)
+    rows = []
+    for q in range(nq):
+        st = [5, 7, 27][q % 3]
+        dt = [32, 64][(q // 3) % 2]
+        side = float(rng.integers(64, 1025))
+        ms = np.exp(rng.normal(0.0, 0.4, 24)) * (side / 256.0) ** (2 if st == 5 else 3) * (dt / 32)
+        valid = (rng.uniform(0, 1, 24) > 0.25).astype(int)
+        valid[q % 24] = 1
+        rows.append(dict(stencil=st, dtype=dt, side=side, ms=[float(m) for m in ms], valid=[int(v) for v in valid]))
+    return rows
+
+
+def test_fit_tables_trains_on_the_centred_log_targets():
+    # the library's pipeline equals training on features and targets built
+    # here from the definition: every valid (query, tile), target ln(1000 ms)
+    # minus the query's mean over its valid tiles
+    tables = _synthetic_tables(21, 30)
+    X, Y = [], []
+    for q in tables:
+        lt = [math.log(q["ms"][t] * 1e3) for t in range(24) if q["valid"][t]]
+        mean = sum(lt) / len(lt)
+        for t in range(24):
+            if q["valid"][t]:
+                X.append(jacc.features(q["stencil"], q["side"], q["dtype"], t))
+                Y.append(math.log(q["ms"][t] * 1e3) - mean)
+    X = np.asarray(X, dtype=np.float32)
+    Y = np.asarray(Y, dtype=np.float32)
+    a = jacc.CostModel(seed=13)
+    b = jacc.CostModel(seed=13)
+    mse = a.fit_tables(tables, epochs=70, lr=1e-3)
+    loss = b.train(torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda(), 70, 1e-3)
+    assert np.array_equal(a.params(), b.params())
+    assert mse == float(loss.item())
+
+
+def test_evaluate_matches_the_oracle_forward_and_regret(orc):
+    tables = _synthetic_tables(22, 40)
+    p = inputs.mlp_init(17)
+    m = jacc.CostModel(init_params=p)
+    ev = m.evaluate(tables, margin=0.05, topk=3)
+    feats = np.array([[jacc.features(q["stencil"], q["side"], q["dtype"], t) for t in range(24)] for q in tables],
+                     dtype=np.float64)
+    pred = orc.mlp_forward(p.astype(np.float64), feats.reshape(-1, 4)).reshape(len(tables), 24)
+    times = np.array([q["ms"] for q in tables])
+    valid = np.array([q["valid"] for q in tables], dtype=bool)
+    times_inf = np.where(valid, times, np.inf)
+    picks = np.array([e["pick"] for e in ev], dtype=np.int32)
+    # regret of the library's picks: the oracle's definition on the same table
+    want = orc.regret(times_inf, picks)
+    assert np.array_equal(np.array([e["regret"] for e in ev]), want)
+    for q in range(len(tables)):
+        pv = np.where(valid[q], pred[q], np.inf)
+        order = np.argsort(pv, kind="stable")
+        gap = pv[order[1]] - pv[order[0]]
+        assert abs(ev[q]["gap"] - gap) <= 1e-4 * max(1.0, abs(pv[order[0]]))
+        assert ev[q]["fallback"] == (ev[q]["gap"] < 0.05)
+        if gap > 1e-3:  # FP32 and FP64 predictions agree on a clear argmin
+            assert picks[q] == order[0]
+            top3 = [t for t in order[:3]]
+            if pv[order[3]] - pv[order[2]] > 1e-3:
+                assert ev[q]["regret_topk"] == orc.regret(times_inf[q:q + 1], np.array([top3[int(np.argmin(times[q][top3]))]], np.int32))[0]
+                assert ev[q]["search_ms_topk"] == pytest.approx(float(np.sum(times[q][top3])), rel=1e-12)
+
+
+def test_margin_caps_the_fallback_fraction():
+    tables = _synthetic_tables(23, 64)
+    m = jacc.CostModel(seed=19)
+    gaps = np.array([e["gap"] for e in m.evaluate(tables)])
+    for f in (0.0, 0.1, 0.25, 0.5, 1.0):
+        g = m.margin(tables, f)
+        assert np.sum(gaps < g) < max(f * len(tables), 1e-9) or (f == 0.0 and g == 0.0)
+        assert g == 0.0 or g in gaps
+    with pytest.raises(jacc.JaccError):
+        m.margin(tables, 1.5)
+
+
+GAIN_SEEDS = (5, 6, 7)
+GAIN_MARGIN = 0.01
+
+
 def test_trained_model_gains_over_the_method_without_it():
     # Reduced workload: 2D sides 256-1024, 3D sides 64-256, four stencil/dtype
     # pairs; timings measured here by the exhaustive autotuner.  The methods
-    # without the model: the library's fixed default tile, and the single tile
-    # that is best on average over the training tables.
+    # without the model: the single tile that is best on average over the
+    # training tables, and the library's built-in default rule (read off
+    # earlier tables of this kind).  Three training seeds.
     pairs = [(5, 64), (7, 32), (7, 64), (27, 32)]
     tr2 = costmodel.train_sides(256, 1024, 8)
     tr3 = costmodel.train_sides(64, 256, 8, step=8)
@@ -189,15 +273,21 @@ def test_trained_model_gains_over_the_method_without_it():
     bufs = costmodel.Buffers(256 ** 3)
     train_t = costmodel.collect(q_train, bufs)
     test_t = costmodel.collect(q_test, bufs)
-    X, Y = costmodel.xy(train_t)
-    m = jacc.CostModel(seed=5)
-    loss, _ = costmodel.fit(m, X, Y, epochs=6000)
-    margin = costmodel.margin_from_training(m, X, Y)
-    res, picks = costmodel.evaluate(m, train_t, test_t, margin)
-    print("cost-model gain test:", res)
-    assert math.isfinite(res["model"]["mean"])
-    assert loss < 0.1  # mean squared error of centred ln(time): a fit within ~30 % per tile
-    # better than the library's fixed default, within noise of the best fixed tile
-    assert res["model"]["mean"] < res["library_default_tile"]["mean"]
-    assert res["model"]["mean"] <= res["fixed_default_tile"]["mean"] + 0.05
-    assert res["model_with_fallback"]["mean"] <= res["model"]["mean"]
+    base = costmodel.baselines(train_t, test_t)
+    fixed = base["fixed_tile"]["mean"]
+    print("cost-model gain test: without the model", base)
+    means = []
+    for seed in GAIN_SEEDS:
+        m = jacc.CostModel(seed=seed)
+        mse = m.fit_tables(train_t, epochs=6000, lr=1e-3)
+        res, _ = costmodel.evaluate(m, train_t, test_t, fallback_fraction=0.25)
+        print(f"seed {seed}: train MSE {mse:.4f}; model {res['model']}; with fallback {res['model_with_fallback']}")
+        assert mse < 0.1  # mean squared error of centred ln(time): a fit within ~30 % per tile
+        # the model beats the best single tile by a margin on the held-out shapes
+        assert res["model"]["mean"] <= fixed - GAIN_MARGIN, (seed, res["model"]["mean"], fixed)
+        # the calibrated fallback fires on a minority and never raises the regret
+        assert res["model_with_fallback"]["fallback_fraction"] <= 0.5
+        assert res["model_with_fallback"]["mean"] <= res["model"]["mean"]
+        means.append(res["model"]["mean"])
+        m.release()
+    assert float(np.mean(means)) <= 0.6 * fixed
