@@ -555,6 +555,20 @@ def profile_case(args):
         print(json.dumps({"profile_case": args.profile_case, "n": n, "sweeps": args.sweeps,
                           "runs": args.warmup + args.steps, "tile": k.info()["tile_id"]}))
         return
+    if args.profile_case == "batched":
+        shapes = inputs.batched_shapes(64, seed=3)
+        hosts = inputs.batched_fields(shapes, seed=4)
+        fields = [(torch.from_numpy(h).to("cuda"), torch.zeros(h.shape, dtype=torch.float64, device="cuda"))
+                  for h in hosts]
+        cfg = dict(item_points=args.item_points, group_bytes=args.group_bytes)
+        bt = jacc.Batch(fields, **cfg)
+        res = torch.zeros(64 * args.sweeps, dtype=torch.float64, device="cuda")
+        for _ in range(args.warmup + args.steps):
+            bt.sweep(args.sweeps, res)
+        bt.status()
+        print(json.dumps({"profile_case": args.profile_case, "sweeps": args.sweeps, "config": bt.config(),
+                          "runs": args.warmup + args.steps}))
+        return
     if args.profile_case == "var19":
         p, fields = inputs.var19_problem_torch(n, n, n, "cuda", seed=7)
         q = torch.empty_like(p)
@@ -589,7 +603,7 @@ def main():
     ap.add_argument("--no-jit", action="store_true", help="use the precompiled kernel instead of the NVRTC variant")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner; use the library's default tile")
     ap.add_argument("--no-secondary", action="store_true", help="skip the other workloads' measurements")
-    ap.add_argument("--profile-case", choices=["box27", "box27-tb2", "var19", "jacobi2d"], default=None,
+    ap.add_argument("--profile-case", choices=["box27", "box27-tb2", "var19", "jacobi2d", "batched"], default=None,
                     help="run only one sweep sequence (27-point FP32 or 19-point on an --n cube; jacobi2d: 5-point FP64 --n squared, graph and cluster launch) for profilers, and exit")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the sweep kernel, if captured for this build")
@@ -597,6 +611,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--n", type=int, default=512, help="grid side (profiling of small cases)")
     ap.add_argument("--sweeps", type=int, default=200)
+    ap.add_argument("--item-points", type=int, default=16384, help="batched profile case: points per item")
+    ap.add_argument("--group-bytes", type=int, default=-1, help="batched profile case: L2 budget per group")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
