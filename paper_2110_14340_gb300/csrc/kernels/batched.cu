@@ -68,56 +68,91 @@ JD void cp_async16(void* smem, const void* gmem) {
 JD void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N> JD void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// Stages the columns [x0-1, x0+64] of row r that lie in the grid.  Element x
-// goes to slot[x - x0 + 2 + sh], sh = (r * nx) & 1: 16-byte chunks start at
-// even element indices, chunk l (columns x0 - sh + 2l, +1) lands at
-// slot[2l + 2].  Lane l copies chunk l, lane 0 also chunk -1 (aligned rows),
-// lane 31 also chunk 32.  The array's last element, whose pair would run past
-// the end of the field, is loaded through a register instead.
-JD void stage_row(double* slot, const double* __restrict__ u, i64 nx, i64 ny, i64 r, i64 x0, int lane) {
-  if (r < 0 || r >= ny) return;
-  const i64 row0 = r * nx;
-  const int sh = (int)(row0 & 1);
-  const i64 clo = x0 >= 1 ? x0 - 1 : 0;
-  const i64 chi = x0 + 64 <= nx - 1 ? x0 + 64 : nx - 1;
-  const i64 n_all = nx * ny;
-  auto chunk = [&](int l) {
-    const i64 cf = x0 - sh + 2 * l;
-    if (cf > chi || cf + 1 < clo) return;
-    const i64 e = row0 + cf;
-    double* d = slot + 2 * l + 2;
-    if (e + 1 < n_all) cp_async16(d, u + e);
-    else d[0] = __ldcg(u + e);
-  };
-  if (lane == 0 && sh == 0) chunk(-1);
-  chunk(lane);
-  if (lane == 31) chunk(32);
+// Staging layout.  Row r's columns [x0-1, x0+64] that lie in the grid are
+// copied into a slot of 68 doubles: element x goes to slot[x - x0 + 2 + sh],
+// sh = (r * nx) & 1, because 16-byte chunks start at even element indices;
+// chunk l (columns x0 - sh + 2l and the next) lands at slot[2l + 2].  Lane l
+// copies chunk l; lanes 0 and 1 also copy chunk -1 and chunk 32 (the halo
+// columns) in the same instruction.  The array's last element, whose pair
+// would run past the end of the field, is copied through a register.  The
+// plan (which chunks a lane copies, for either parity) is fixed per unit, and
+// row addresses advance by nx per row, so staging a row costs a few
+// instructions per lane.
+struct StagePlan {
+  int cfa0, cfa1, cfb0, cfb1;  // first column of the lane's chunks, for sh = 0 and 1
+  bool na0, na1, nb0, nb1;     // whether the chunk is needed
+  int da, db;                  // slot index of each chunk
+};
+
+JD StagePlan stage_plan(int nx, int x0, int lane) {
+  StagePlan P;
+  const int clo = x0 >= 1 ? x0 - 1 : 0;
+  const int chi = x0 + 64 <= nx - 1 ? x0 + 64 : nx - 1;
+  const int la = lane, lb = lane == 0 ? -1 : 32;
+  P.da = 2 * la + 2;
+  P.db = 2 * lb + 2;
+  P.cfa0 = x0 + 2 * la;
+  P.cfa1 = P.cfa0 - 1;
+  P.cfb0 = x0 + 2 * lb;
+  P.cfb1 = P.cfb0 - 1;
+  P.na0 = P.cfa0 <= chi && P.cfa0 + 1 >= clo;
+  P.na1 = P.cfa1 <= chi && P.cfa1 + 1 >= clo;
+  P.nb0 = lane < 2 && P.cfb0 <= chi && P.cfb0 + 1 >= clo;
+  P.nb1 = lane < 2 && P.cfb1 <= chi && P.cfb1 + 1 >= clo;
+  return P;
+}
+
+// Copies one row (row pointer rp = u + r nx, parity sh) into slot sp; `last`
+// marks the field's last row.
+JD void stage_row(const StagePlan& P, double* sp, const double* rp, int sh, bool last, int nx) {
+  const bool na = sh ? P.na1 : P.na0, nb = sh ? P.nb1 : P.nb0;
+  const int ca = sh ? P.cfa1 : P.cfa0, cb = sh ? P.cfb1 : P.cfb0;
+  if (na) {
+    if (!last || ca + 1 < nx) cp_async16(sp + P.da, rp + ca);
+    else sp[P.da] = __ldcg(rp + ca);
+  }
+  if (nb) {
+    if (!last || cb + 1 < nx) cp_async16(sp + P.db, rp + cb);
+    else sp[P.db] = __ldcg(rp + cb);
+  }
 }
 
 // One warp: output rows [ya, yb) of columns [x0, x0 + 64) (lane: x0 + 2 lane
 // and the next column).  Arithmetic and outputs are those of jacobi_fx_march
 // (FX: resident 64-bit fixed point, EDGE: first or last sweep) or of the
-// native jacobi_march, value for value.
+// native jacobi_march, value for value.  Row r lives in slot (r - ya + 1)
+// mod kRing; rows ya-1 .. yb are staged (those inside the grid).
 template <bool FX, bool EDGE>
-JD void staged_march(double* ring, const double* __restrict__ u, double* __restrict__ v, i64 nx, i64 ny, i64 x0,
+JD void staged_march(double* ring, const double* __restrict__ u, double* __restrict__ v, i64 nx64, i64 ny, i64 x064,
                      i64 ya, i64 yb, int F, int flags, u64& rfx, double& rnat) {
   const int lane = threadIdx.x & 31;
-  const i64 xa = x0 + 2 * lane;
+  const int nx = (int)nx64, x0 = (int)x064;  // extents below 2^31
+  const int xa = x0 + 2 * lane;
   const bool inf = EDGE && (flags & JFX_IN_F64);
   const bool outf = EDGE && (flags & JFX_OUT_F64);
   const bool c0 = xa < nx, c1 = xa + 1 < nx;
   const bool in0 = xa >= 1 && xa <= nx - 2, in1 = xa + 1 >= 1 && xa + 1 <= nx - 2;
-  auto slot = [&](i64 r) -> double* { return ring + (int)((r + 1) & (kRing - 1)) * kSlot; };
-  auto shift = [&](i64 r) -> int { return (int)((r * nx) & 1); };
-  auto stage = [&](i64 r) {
-    if (r <= yb) stage_row(slot(r), u, nx, ny, r, x0, lane);
+  const int odd = nx & 1;
+  const StagePlan P = stage_plan(nx, x0, lane);
+  // staging cursor: next row to stage, its offset, parity and ring position
+  i64 rs = ya - 1;
+  i64 offs = (ya - 1) * nx64;
+  int shs = odd ? (int)(rs & 1) : 0;
+  int js = 0;
+  auto stage_next = [&]() {
+    if (rs >= 0 && rs < ny && rs <= yb)
+      stage_row(P, ring + (js & (kRing - 1)) * kSlot, u + offs, shs, rs == ny - 1, nx);
     cp_async_commit();
+    ++rs;
+    offs += nx64;
+    shs ^= odd;
+    ++js;
   };
-  auto own = [&](i64 r, double (&o)[2]) {
+  auto own = [&](const double* sp, int sh, bool inside, double (&o)[2]) {
     o[0] = o[1] = 0.0;
-    if (r < 0 || r >= ny || !c0) return;
-    const double* p = slot(r) + 2 * lane + 2 + shift(r);
-    if (shift(r) == 0 && c1) {
+    if (!inside || !c0) return;
+    const double* p = sp + 2 * lane + 2 + sh;
+    if (sh == 0 && c1) {
       const double2 t = *reinterpret_cast<const double2*>(p);
       o[0] = t.x;
       o[1] = t.y;
@@ -128,40 +163,44 @@ JD void staged_march(double* ring, const double* __restrict__ u, double* __restr
   };
   auto cvt = [&](double raw) -> i64 { return inf ? fx_from(raw, F) : bits_i64(raw); };
 
-  for (int j = 0; j < kRing; ++j) stage(ya - 1 + j);
+#pragma unroll 1
+  for (int j = 0; j < kRing; ++j) stage_next();
   cp_async_wait<kRing - 2>();  // rows ya-1 and ya
   __syncwarp();
+  int shy = odd ? (int)(ya & 1) : 0;  // parity of row y
   double rup[2], rcur[2];
-  own(ya - 1, rup);
-  own(ya, rcur);
+  own(ring + 0 * kSlot, shy ^ odd, ya >= 1, rup);
+  own(ring + 1 * kSlot, shy, true, rcur);
   __syncwarp();
-  stage(ya + kRing - 1);  // into the slot of row ya-1
+  stage_next();  // into the slot of row ya-1
+  double* out = v + ya * nx64 + xa;
+  int jy = 1;  // ring position of row y
+#pragma unroll 1
   for (i64 y = ya; y < yb; ++y) {
     cp_async_wait<kRing - 2>();  // row y+1
     __syncwarp();
+    const double* sy = ring + (jy & (kRing - 1)) * kSlot;
+    const double* sn = ring + ((jy + 1) & (kRing - 1)) * kSlot;
     double rdn[2];
-    own(y + 1, rdn);
-    const double* cs = slot(y) + 2 * lane + 2 + shift(y);
+    own(sn, shy ^ odd, y + 1 < ny, rdn);
+    const double* cs = sy + 2 * lane + 2 + shy;
     const double rl = in0 ? cs[-1] : 0.0;
     const double rr = in1 ? cs[2] : 0.0;
     const bool yint = y >= 1 && y <= ny - 2;
-    double out[2];
+    const bool a0 = yint && in0, a1 = yint && in1;
+    double o0, o1;
     if constexpr (FX) {
-      const i64 up0 = cvt(rup[0]), up1 = cvt(rup[1]);
       const i64 cu0 = cvt(rcur[0]), cu1 = cvt(rcur[1]);
-      const i64 dn0 = cvt(rdn[0]), dn1 = cvt(rdn[1]);
-      const i64 xl = cvt(rl), xr = cvt(rr);
-      const i64 s0 = (up0 + dn0) + (xl + cu1);
-      const i64 s1 = (up1 + dn1) + (cu0 + xr);
+      const i64 s0 = (cvt(rup[0]) + cvt(rdn[0])) + (cvt(rl) + cu1);
+      const i64 s1 = (cvt(rup[1]) + cvt(rdn[1])) + (cu0 + cvt(rr));
       auto bnd = [&](double raw, i64 w) -> double {
         if constexpr (!EDGE) return i64_bits(w);
         if (inf && outf) return raw;
         if (outf) return fx_to(w, F);
         return i64_bits(w);
       };
-      const bool a0 = yint && in0, a1 = yint && in1;
-      out[0] = a0 ? (outf ? fx_to(s0, F + 2) : i64_bits((s0 + 2) >> 2)) : bnd(rcur[0], cu0);
-      out[1] = a1 ? (outf ? fx_to(s1, F + 2) : i64_bits((s1 + 2) >> 2)) : bnd(rcur[1], cu1);
+      o0 = a0 ? (outf ? fx_to(s0, F + 2) : i64_bits((s0 + 2) >> 2)) : bnd(rcur[0], cu0);
+      o1 = a1 ? (outf ? fx_to(s1, F + 2) : i64_bits((s1 + 2) >> 2)) : bnd(rcur[1], cu1);
       const i64 d0 = s0 - cu0 * 4, d1 = s1 - cu1 * 4;
       const u64 ad0 = (u64)(d0 ^ (d0 >> 63)), ad1 = (u64)(d1 ^ (d1 >> 63));
       if (a0 && ad0 > rfx) rfx = ad0;
@@ -170,31 +209,32 @@ JD void staged_march(double* ring, const double* __restrict__ u, double* __restr
       const double s0 = (rup[0] + rdn[0]) + (rl + rcur[1]);
       const double s1 = (rup[1] + rdn[1]) + (rcur[0] + rr);
       const double q0 = 0.25 * s0, q1 = 0.25 * s1;
-      const bool a0 = yint && in0, a1 = yint && in1;
-      out[0] = a0 ? q0 : rcur[0];
-      out[1] = a1 ? q1 : rcur[1];
+      o0 = a0 ? q0 : rcur[0];
+      o1 = a1 ? q1 : rcur[1];
       double e0 = q0 - rcur[0], e1 = q1 - rcur[1];
       e0 = e0 < 0.0 ? -e0 : e0;
       e1 = e1 < 0.0 ? -e1 : e1;
       if (a0 && e0 > rnat) rnat = e0;
       if (a1 && e1 > rnat) rnat = e1;
     }
-    double* o = v + y * nx + xa;
-    if (c1 && shift(y) == 0) {
+    if (c1 && shy == 0) {
       double2 t;
-      t.x = out[0];
-      t.y = out[1];
-      *reinterpret_cast<double2*>(o) = t;
+      t.x = o0;
+      t.y = o1;
+      *reinterpret_cast<double2*>(out) = t;
     } else if (c0) {
-      o[0] = out[0];
-      if (c1) o[1] = out[1];
+      out[0] = o0;
+      if (c1) out[1] = o1;
     }
+    out += nx64;
     rup[0] = rcur[0];
     rup[1] = rcur[1];
     rcur[0] = rdn[0];
     rcur[1] = rdn[1];
+    shy ^= odd;
+    ++jy;
     __syncwarp();
-    stage(y + kRing);  // into the slot of row y
+    stage_next();  // into the slot of row y
   }
   cp_async_wait<0>();  // no copy may land in the ring after the next unit starts with it
   __syncwarp();
