@@ -240,6 +240,113 @@ JD void staged_march(double* ring, const double* __restrict__ u, double* __restr
   __syncwarp();
 }
 
+// The same march for a unit without boundary points: 1 <= x0, x0 + 64 <=
+// nx - 1, 1 <= ya, yb <= ny - 1 (every point interior, every lane's two
+// columns and both halo columns inside the grid), resident fixed point.
+// Rows are counted in 32-bit integers, no point needs a predicate, and two
+// rows are done per iteration so the three row registers rotate without
+// copies.
+template <bool EDGE>
+JD void staged_march_inner(double* ring, const double* __restrict__ u, double* __restrict__ v, i64 nx64, int ny,
+                           int x0, int ya, int yb, int F, int flags, u64& rfx) {
+  const int lane = threadIdx.x & 31;
+  const int nx = (int)nx64;
+  const bool inf = EDGE && (flags & JFX_IN_F64);
+  const bool outf = EDGE && (flags & JFX_OUT_F64);
+  const int odd = nx & 1;
+  // staging: chunk `lane` always; lane 0 also chunk -1 on even-parity rows,
+  // lane 1 also chunk 32
+  const int cfa = x0 + 2 * lane, da = 2 * lane + 2;
+  const int cfb = lane == 0 ? x0 - 2 : x0 + 64, db = lane == 0 ? 0 : 66;
+  int rs = ya - 1, shs = odd & (ya - 1), js = 0;
+  const double* rps = u + (i64)(ya - 1) * nx64;
+  auto stage_next = [&]() {
+    if (rs <= yb) {
+      double* sp = ring + (js & (kRing - 1)) * kSlot;
+      const bool last = rs == ny - 1;
+      const int ca = cfa - shs, cb = cfb - shs;
+      if (!last || ca + 1 < nx) cp_async16(sp + da, rps + ca);
+      else sp[da] = __ldcg(rps + ca);
+      if (lane == 1 || (lane == 0 && shs == 0)) {
+        if (!last || cb + 1 < nx) cp_async16(sp + db, rps + cb);
+        else sp[db] = __ldcg(rps + cb);
+      }
+    }
+    cp_async_commit();
+    ++rs;
+    rps += nx64;
+    shs ^= odd;
+    ++js;
+  };
+  auto own = [&](const double* sp, int sh, double (&o)[2]) {
+    const double* p = sp + 2 * lane + 2 + sh;
+    if (sh == 0) {
+      const double2 t = *reinterpret_cast<const double2*>(p);
+      o[0] = t.x;
+      o[1] = t.y;
+    } else {
+      o[0] = p[0];
+      o[1] = p[1];
+    }
+  };
+  auto cvt = [&](double raw) -> i64 { return inf ? fx_from(raw, F) : bits_i64(raw); };
+#pragma unroll 1
+  for (int j = 0; j < kRing; ++j) stage_next();
+  cp_async_wait<kRing - 2>();  // rows ya-1 and ya
+  __syncwarp();
+  int shy = odd & ya;  // parity of row y
+  double ra[2], rb[2], rc[2];
+  own(ring, shy ^ odd, ra);
+  own(ring + kSlot, shy, rb);
+  __syncwarp();
+  stage_next();
+  double* out = v + (i64)ya * nx64 + x0 + 2 * lane;
+  int jy = 1;
+  // one row: up, cur -> dn (raw words); writes row y
+  auto step = [&](const double (&up)[2], const double (&cur)[2], double (&dn)[2]) {
+    cp_async_wait<kRing - 2>();  // row y+1
+    __syncwarp();
+    const double* sy = ring + (jy & (kRing - 1)) * kSlot;
+    own(ring + ((jy + 1) & (kRing - 1)) * kSlot, shy ^ odd, dn);
+    const double* cs = sy + 2 * lane + 2 + shy;
+    const double rl = cs[-1], rr = cs[2];
+    const i64 cu0 = cvt(cur[0]), cu1 = cvt(cur[1]);
+    const i64 s0 = (cvt(up[0]) + cvt(dn[0])) + (cvt(rl) + cu1);
+    const i64 s1 = (cvt(up[1]) + cvt(dn[1])) + (cu0 + cvt(rr));
+    const double o0 = outf ? fx_to(s0, F + 2) : i64_bits((s0 + 2) >> 2);
+    const double o1 = outf ? fx_to(s1, F + 2) : i64_bits((s1 + 2) >> 2);
+    const i64 d0 = s0 - cu0 * 4, d1 = s1 - cu1 * 4;
+    const u64 ad0 = (u64)(d0 ^ (d0 >> 63)), ad1 = (u64)(d1 ^ (d1 >> 63));
+    const u64 m = ad0 > ad1 ? ad0 : ad1;
+    rfx = m > rfx ? m : rfx;
+    if (shy == 0) {
+      double2 t;
+      t.x = o0;
+      t.y = o1;
+      *reinterpret_cast<double2*>(out) = t;
+    } else {
+      out[0] = o0;
+      out[1] = o1;
+    }
+    out += nx64;
+    shy ^= odd;
+    ++jy;
+    __syncwarp();
+    stage_next();
+  };
+  int y = ya;
+#pragma unroll 1
+  for (; y + 2 < yb; y += 3) {
+    step(ra, rb, rc);
+    step(rb, rc, ra);
+    step(rc, ra, rb);
+  }
+  if (y < yb) step(ra, rb, rc);
+  if (y + 1 < yb) step(rb, rc, ra);
+  cp_async_wait<0>();
+  __syncwarp();
+}
+
 // ---------------------------------------------------------------- register march
 
 template <bool EDGE>
@@ -427,7 +534,11 @@ __global__ void __launch_bounds__(kCTA, 3) jacc_k_batched(JBatchParams bp) {
     double rnat = 0.0;
     if (x0 < G.nx && ya < yb) {
       if constexpr (STAGED) {
-        if (F >= 0) {
+        const bool inner = x0 >= 1 && x0 + 64 <= G.nx - 1 && ya >= 1 && yb <= G.ny - 1;
+        if (F >= 0 && inner) {
+          if (flags) staged_march_inner<true>(ring, src, dst, G.nx, (int)G.ny, (int)x0, (int)ya, (int)yb, F, flags, rfx);
+          else staged_march_inner<false>(ring, src, dst, G.nx, (int)G.ny, (int)x0, (int)ya, (int)yb, F, flags, rfx);
+        } else if (F >= 0) {
           if (flags) staged_march<true, true>(ring, src, dst, G.nx, G.ny, x0, ya, yb, F, flags, rfx, rnat);
           else staged_march<true, false>(ring, src, dst, G.nx, G.ny, x0, ya, yb, F, flags, rfx, rnat);
         } else {
