@@ -618,8 +618,8 @@ jacc_status jacc_costmodel_release(jacc_costmodel m);
  * jacc_batch_tune times, for probe_sweeps sweeps on the batch's own buffers
  * (their contents change), every combination of load path x CTAs per SM in
  * {2, max} x L2 budget in {20 %, 40 %, 60 % of L2, one group} x item size in
- * {4K, 8K, 16K} points, keeps the fastest, then times each group alone at
- * item sizes {2K .. 32K} and gives that group's grids their best tile (kept
+ * {8K, 16K, 32K} points, keeps the fastest, then times each group alone at
+ * item sizes {4K .. 64K} and gives that group's grids their best tile (kept
  * only if the whole batch then runs faster); returns the schedule and its
  * time.  */
 typedef struct {

@@ -417,7 +417,7 @@ extern "C" jacc_status jacc_batch_tune(jacc_batch h, int32_t probe_sweeps, uintp
     for (int p : per_sm) {
       if (p < 1 || p > b.max_ctas_per_sm[march]) continue;
       for (i64 gb : budgets) {
-        for (int pts : {4096, 8192, 16384}) {
+        for (int pts : {8192, 16384, 32768}) {
           jacc_batch_config c = base;
           c.march = march;
           c.ctas_per_sm = p;
@@ -447,7 +447,7 @@ extern "C" jacc_status jacc_batch_tune(jacc_batch h, int32_t probe_sweeps, uintp
       if (b.group_of[g] == q) members.push_back(g);
     int best_pts = 0;
     double best_q = 1e300;
-    for (int pts : {2048, 4096, 8192, 16384, 32768}) {
+    for (int pts : {4096, 8192, 16384, 32768, 65536}) {
       for (int g : members) {
         int rows = 0, cols = 0;
         grid_tile(b.grids[g], jacc_batch_tile{0, 0, 0, 0}, pts, &rows, &cols);

@@ -121,7 +121,9 @@ JD void stage_row(const StagePlan& P, double* sp, const double* rp, int sh, bool
 // and the next column).  Arithmetic and outputs are those of jacobi_fx_march
 // (FX: resident 64-bit fixed point, EDGE: first or last sweep) or of the
 // native jacobi_march, value for value.  Row r lives in slot (r - ya + 1)
-// mod kRing; rows ya-1 .. yb are staged (those inside the grid).
+// mod kRing; rows ya-1 .. yb are staged (those inside the grid).  The
+// kernel runs fixed-point units through staged_march_fx below and uses this
+// one for the native FP64 path (grids with a non-finite or tiny maximum).
 template <bool FX, bool EDGE>
 JD void staged_march(double* ring, const double* __restrict__ u, double* __restrict__ v, i64 nx64, i64 ny, i64 x064,
                      i64 ya, i64 yb, int F, int flags, u64& rfx, double& rnat) {
@@ -240,109 +242,110 @@ JD void staged_march(double* ring, const double* __restrict__ u, double* __restr
   __syncwarp();
 }
 
-// The same march for a unit without boundary points: 1 <= x0, x0 + 64 <=
-// nx - 1, 1 <= ya, yb <= ny - 1 (every point interior, every lane's two
-// columns and both halo columns inside the grid), resident fixed point.
-// Rows are counted in 32-bit integers, no point needs a predicate, and two
-// rows are done per iteration so the three row registers rotate without
-// copies.
+// The fixed-point march of any unit, fast: rows are counted in 32-bit
+// integers, the per-lane facts (columns inside the grid, interior columns,
+// the staging plan) are fixed per unit, a boundary row is a uniform test per
+// row, and three rows are done per iteration so the row registers rotate
+// without copies.  Outputs and
+// residual are those of jacobi_fx_march, value for value.
 template <bool EDGE>
-JD void staged_march_inner(double* ring, const double* __restrict__ u, double* __restrict__ v, i64 nx64, int ny,
-                           int x0, int ya, int yb, int F, int flags, u64& rfx) {
+JD void staged_march_fx(double* ring, const double* __restrict__ u, double* __restrict__ v, i64 nx64, int ny, int x0,
+                        int ya, int yb, int F, int flags, u64& rfx) {
   const int lane = threadIdx.x & 31;
   const int nx = (int)nx64;
+  const int xa = x0 + 2 * lane;
   const bool inf = EDGE && (flags & JFX_IN_F64);
   const bool outf = EDGE && (flags & JFX_OUT_F64);
+  const bool c0 = xa < nx, c1 = xa + 1 < nx;
+  const bool in0 = xa >= 1 && xa <= nx - 2, in1 = xa + 1 <= nx - 2;
   const int odd = nx & 1;
-  // staging: chunk `lane` always; lane 0 also chunk -1 on even-parity rows,
-  // lane 1 also chunk 32
-  const int cfa = x0 + 2 * lane, da = 2 * lane + 2;
-  const int cfb = lane == 0 ? x0 - 2 : x0 + 64, db = lane == 0 ? 0 : 66;
+  const StagePlan P = stage_plan(nx, x0, lane);
   int rs = ya - 1, shs = odd & (ya - 1), js = 0;
   const double* rps = u + (i64)(ya - 1) * nx64;
   auto stage_next = [&]() {
-    if (rs <= yb) {
-      double* sp = ring + (js & (kRing - 1)) * kSlot;
-      const bool last = rs == ny - 1;
-      const int ca = cfa - shs, cb = cfb - shs;
-      if (!last || ca + 1 < nx) cp_async16(sp + da, rps + ca);
-      else sp[da] = __ldcg(rps + ca);
-      if (lane == 1 || (lane == 0 && shs == 0)) {
-        if (!last || cb + 1 < nx) cp_async16(sp + db, rps + cb);
-        else sp[db] = __ldcg(rps + cb);
-      }
-    }
+    if (rs >= 0 && rs <= yb && rs < ny) stage_row(P, ring + (js & (kRing - 1)) * kSlot, rps, shs, rs == ny - 1, nx);
     cp_async_commit();
     ++rs;
     rps += nx64;
     shs ^= odd;
     ++js;
   };
-  auto own = [&](const double* sp, int sh, double (&o)[2]) {
+  auto own = [&](const double* sp, int sh, bool inside, double (&o)[2]) {
+    o[0] = o[1] = 0.0;
+    if (!inside) return;
     const double* p = sp + 2 * lane + 2 + sh;
-    if (sh == 0) {
+    if (sh == 0 && c1) {
       const double2 t = *reinterpret_cast<const double2*>(p);
       o[0] = t.x;
       o[1] = t.y;
-    } else {
+    } else if (c0) {
       o[0] = p[0];
-      o[1] = p[1];
+      if (c1) o[1] = p[1];
     }
   };
   auto cvt = [&](double raw) -> i64 { return inf ? fx_from(raw, F) : bits_i64(raw); };
+  auto bnd = [&](double raw, i64 w) -> double {
+    if constexpr (!EDGE) return i64_bits(w);
+    if (inf && outf) return raw;
+    if (outf) return fx_to(w, F);
+    return i64_bits(w);
+  };
 #pragma unroll 1
   for (int j = 0; j < kRing; ++j) stage_next();
   cp_async_wait<kRing - 2>();  // rows ya-1 and ya
   __syncwarp();
   int shy = odd & ya;  // parity of row y
   double ra[2], rb[2], rc[2];
-  own(ring, shy ^ odd, ra);
-  own(ring + kSlot, shy, rb);
+  own(ring, shy ^ odd, ya >= 1, ra);
+  own(ring + kSlot, shy, true, rb);
   __syncwarp();
   stage_next();
-  double* out = v + (i64)ya * nx64 + x0 + 2 * lane;
-  int jy = 1;
+  double* out = v + (i64)ya * nx64 + xa;
+  int jy = 1, y = ya;
   // one row: up, cur -> dn (raw words); writes row y
   auto step = [&](const double (&up)[2], const double (&cur)[2], double (&dn)[2]) {
     cp_async_wait<kRing - 2>();  // row y+1
     __syncwarp();
     const double* sy = ring + (jy & (kRing - 1)) * kSlot;
-    own(ring + ((jy + 1) & (kRing - 1)) * kSlot, shy ^ odd, dn);
+    own(ring + ((jy + 1) & (kRing - 1)) * kSlot, shy ^ odd, y + 1 < ny, dn);
     const double* cs = sy + 2 * lane + 2 + shy;
-    const double rl = cs[-1], rr = cs[2];
+    const double rl = in0 ? cs[-1] : 0.0;
+    const double rr = in1 ? cs[2] : 0.0;
+    const bool yint = y >= 1 && y <= ny - 2;
+    const bool a0 = yint && in0, a1 = yint && in1;
     const i64 cu0 = cvt(cur[0]), cu1 = cvt(cur[1]);
     const i64 s0 = (cvt(up[0]) + cvt(dn[0])) + (cvt(rl) + cu1);
     const i64 s1 = (cvt(up[1]) + cvt(dn[1])) + (cu0 + cvt(rr));
-    const double o0 = outf ? fx_to(s0, F + 2) : i64_bits((s0 + 2) >> 2);
-    const double o1 = outf ? fx_to(s1, F + 2) : i64_bits((s1 + 2) >> 2);
+    const double o0 = a0 ? (outf ? fx_to(s0, F + 2) : i64_bits((s0 + 2) >> 2)) : bnd(cur[0], cu0);
+    const double o1 = a1 ? (outf ? fx_to(s1, F + 2) : i64_bits((s1 + 2) >> 2)) : bnd(cur[1], cu1);
     const i64 d0 = s0 - cu0 * 4, d1 = s1 - cu1 * 4;
-    const u64 ad0 = (u64)(d0 ^ (d0 >> 63)), ad1 = (u64)(d1 ^ (d1 >> 63));
+    const u64 ad0 = a0 ? (u64)(d0 ^ (d0 >> 63)) : 0ull, ad1 = a1 ? (u64)(d1 ^ (d1 >> 63)) : 0ull;
     const u64 m = ad0 > ad1 ? ad0 : ad1;
     rfx = m > rfx ? m : rfx;
-    if (shy == 0) {
+    if (shy == 0 && c1) {
       double2 t;
       t.x = o0;
       t.y = o1;
       *reinterpret_cast<double2*>(out) = t;
-    } else {
+    } else if (c0) {
       out[0] = o0;
-      out[1] = o1;
+      if (c1) out[1] = o1;
     }
     out += nx64;
     shy ^= odd;
     ++jy;
+    ++y;
     __syncwarp();
     stage_next();
   };
-  int y = ya;
 #pragma unroll 1
-  for (; y + 2 < yb; y += 3) {
+  while (y + 2 < yb) {
     step(ra, rb, rc);
     step(rb, rc, ra);
     step(rc, ra, rb);
   }
   if (y < yb) step(ra, rb, rc);
-  if (y + 1 < yb) step(rb, rc, ra);
+  if (y < yb) step(rb, rc, ra);
   cp_async_wait<0>();
   __syncwarp();
 }
@@ -534,13 +537,9 @@ __global__ void __launch_bounds__(kCTA, 3) jacc_k_batched(JBatchParams bp) {
     double rnat = 0.0;
     if (x0 < G.nx && ya < yb) {
       if constexpr (STAGED) {
-        const bool inner = x0 >= 1 && x0 + 64 <= G.nx - 1 && ya >= 1 && yb <= G.ny - 1;
-        if (F >= 0 && inner) {
-          if (flags) staged_march_inner<true>(ring, src, dst, G.nx, (int)G.ny, (int)x0, (int)ya, (int)yb, F, flags, rfx);
-          else staged_march_inner<false>(ring, src, dst, G.nx, (int)G.ny, (int)x0, (int)ya, (int)yb, F, flags, rfx);
-        } else if (F >= 0) {
-          if (flags) staged_march<true, true>(ring, src, dst, G.nx, G.ny, x0, ya, yb, F, flags, rfx, rnat);
-          else staged_march<true, false>(ring, src, dst, G.nx, G.ny, x0, ya, yb, F, flags, rfx, rnat);
+        if (F >= 0) {
+          if (flags) staged_march_fx<true>(ring, src, dst, G.nx, (int)G.ny, (int)x0, (int)ya, (int)yb, F, flags, rfx);
+          else staged_march_fx<false>(ring, src, dst, G.nx, (int)G.ny, (int)x0, (int)ya, (int)yb, F, flags, rfx);
         } else {
           staged_march<false, false>(ring, src, dst, G.nx, G.ny, x0, ya, yb, F, flags, rfx, rnat);
         }
