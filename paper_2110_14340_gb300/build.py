@@ -63,7 +63,8 @@ def _jobs():
             jobs.append((obj, KERNEL_HEADERS + [os.path.join(KDIR, "inst.cu")],
                          [NVCC] + cu_flags + [f"-DJACC_INST_STENCIL={st}", f"-DJACC_INST_DTYPE={dt}", "-c",
                                               os.path.join(KDIR, "inst.cu"), "-o", obj]))
-    for name in ("aux.cu", "static_scratch.cu", "batched.cu", "mlp.cu", "jacobi_cluster.cu", "until.cu", "var19.cu"):
+    for name in ("aux.cu", "static_scratch.cu", "batched.cu", "mlp.cu", "jacobi_cluster.cu", "until.cu", "var19.cu",
+                 "box27_tb2.cu"):
         obj = os.path.join(BUILD, name.replace(".cu", ".o"))
         jobs.append((obj, KERNEL_HEADERS + HOST_HEADERS + [os.path.join(KDIR, name)],
                      [NVCC] + cu_flags + ["-c", os.path.join(KDIR, name), "-o", obj]))

@@ -59,6 +59,7 @@ struct Kernel {
   const void* func_last = nullptr;  // constant-folded FP64 last sweep that converts only on store (or null)
   cudaLibrary_t lib = nullptr;  // NVRTC module, if jit
   dim3 grid, block;
+  int smem = 0;                 // dynamic shared memory per CTA of `func`
   int tblock = 1;
   int cluster_nc = 0;           // JACC_SPEC_CLUSTER: CTAs of the cluster-resident sweep launch
   int refcount = 0;
@@ -67,6 +68,14 @@ struct Kernel {
   std::map<UntilKey, UntilGraph> until_graphs;
   std::map<std::string, SweepGraph> coeff_graphs;  // jacc_sweep_coeffs graphs, keyed by all pointers
 };
+
+// The two-sweep staged 27-point FP32 kernel (temporal blocking, T = 2;
+// rows of 16-byte multiples).
+const void* box27_tb2_kernel();
+int box27_tb2_smem();
+dim3 box27_tb2_grid(long long nx, long long ny, long long nz);
+dim3 box27_tb2_block();
+cudaError_t box27_tb2_setup();
 
 // The variable-coefficient 19-point kernel (one fixed tile).
 void var19_geometry(long long nx, long long ny, long long nz, dim3* grid, dim3* block);

@@ -354,6 +354,16 @@ extern "C" jacc_status jacc_specialize(const jacc_kernel_desc* desc, jacc_kernel
   if (desc->stencil == 19) {
     var19_geometry(desc->nx, desc->ny, desc->nz, &k->grid, &k->block);
     k->func = k->func_out = nullptr;  // launched by jacc_sweep_coeffs only
+  } else if (desc->tblock == 2 && desc->nx % 4 == 0) {
+    // two sweeps per launch, staged: 320 threads over a 128 x 16 output tile,
+    // 64-plane chunks (box27_tb2.cu)
+    k->tblock = 2;
+    st = cuda_check(box27_tb2_setup(), "cudaFuncSetAttribute(two-sweep 27-point kernel)");
+    if (st) return st;
+    k->func = k->func_out = box27_tb2_kernel();
+    k->block = box27_tb2_block();
+    k->grid = box27_tb2_grid(desc->nx, desc->ny, desc->nz);
+    k->smem = box27_tb2_smem();
   } else if (desc->tblock > 1) {
     // temporally blocked 27-point kernel: 32 x 16 threads over a 128 x 16 region,
     // output tile 120 x (16 - 2T), 64-plane chunks
@@ -489,7 +499,7 @@ cudaError_t launch_sweep_kernel(const Kernel& k, const void* u, void* v, double*
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = k.grid;
   cfg.blockDim = k.block;
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = static_cast<size_t>(k.smem);
   cfg.stream = s;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;

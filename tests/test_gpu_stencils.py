@@ -443,3 +443,41 @@ def test_box27_temporal_blocking_small_periodic_and_errors(orc):
     with pytest.raises(jacc.JaccError) as e:
         jacc.Kernel(jacc.STENCIL_27PT, jacc.F64, 12, 7, 5, coeffs=(0.5, 0.05, 0.01, 0.005), tblock=2)
     assert e.value.status == jacc.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("shape", [(70, 37, 248), (5, 7, 12), (33, 20, 520), (3, 3, 4)])
+def test_box27_two_sweep_kernel_bit_identical_to_single_sweeps(orc, shape):
+    # the staged two-sweep kernel (rows of a multiple of 4 floats) forms each
+    # sweep with the single-sweep staged kernel's arithmetic in the same order:
+    # after 2k sweeps its field equals 2k single staged sweeps bit for bit
+    nz, ny, nx = shape
+    u = inputs.box27_field(nx, ny, nz, seed=14)
+    wt = tuple(float(w) for w in W)
+    k2 = jacc.Kernel(jacc.STENCIL_27PT, jacc.F32, nx, ny, nz, coeffs=wt, tblock=2)
+    k1 = jacc.Kernel(jacc.STENCIL_27PT, jacc.F32, nx, ny, nz, coeffs=wt, tile_id=3)
+    g2, s2 = run(k2, u, 6)
+    g1, s1 = run(k1, u, 6)
+    assert np.array_equal(g2.view(np.int32), g1.view(np.int32))
+    o, osum = orc.box27_run(u, W, 6)
+    assert nerr(g2, o) <= TOL32
+    A = float(np.sum(np.abs(o.astype(np.float64))))
+    for i in range(6):
+        if (i + 1) % 2:
+            assert np.isnan(s2[i])
+        else:
+            assert abs(s2[i] - osum[i]) <= 1e-6 * A and abs(s2[i] - s1[i]) <= 1e-6 * A
+    assert k2.status() == 0
+
+
+def test_box27_two_sweep_kernel_wait_timeout_is_reported_and_recoverable(orc):
+    nz, ny, nx = 40, 20, 256
+    u = inputs.box27_field(nx, ny, nz, seed=15)
+    k = jacc.Kernel(jacc.STENCIL_27PT, jacc.F32, nx, ny, nz, coeffs=tuple(float(w) for w in W), tblock=2)
+    k.set_wait(timeout_ms=20, stall_plane=3)
+    run(k, u, 2, graph=False)
+    assert k.status() == jacc.ERR_TIMEOUT
+    k.set_wait()
+    g, _ = run(k, u, 4)
+    o, _ = orc.box27_run(u, W, 4)
+    assert nerr(g, o) <= TOL32
+    assert k.status() == 0
