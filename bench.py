@@ -526,7 +526,7 @@ def secondary(dev):
     out["var19_f32_512x512x1024_x20"] = {
         "ms_per_sweep": ms19, "GLUP/s": lup19 / ms19 / 1e6,
         "GB/s_56B_per_update": lup19 * 56 / ms19 / 1e6,
-        "frac_of_measured_hbm": lup19 * 56 / ms19 / 1e6 / 6775.9,
+        "frac_of_measured_hbm": lup19 * 56 / ms19 / 1e6 / peaks()[0],
         "residual_first_last": [float(r19[0]), float(r19[-1])]}
     k19.release()
     del p, q, fields

@@ -254,7 +254,10 @@ def test_margin_caps_the_fallback_fraction():
 
 
 GAIN_SEEDS = (5, 6, 7)
-GAIN_MARGIN = 0.01
+# the model's mean regret must be at least 5 points below the best single
+# tile's on every seed (measured on this workload: 15-18 points below, the
+# best single tile at about 19 %)
+GAIN_MARGIN = 0.05
 
 
 def test_trained_model_gains_over_the_method_without_it():
