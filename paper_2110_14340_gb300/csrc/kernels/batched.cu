@@ -369,19 +369,24 @@ JD void register_units(const JBGrid& G, const double* src, double* dst, i64 x0, 
 
 // ---------------------------------------------------------------- the persistent kernel
 //
-// A CTA is 8 compute warps and one scheduler warp.  The scheduler takes the
-// next ticket, loads its item and grid and polls its five dependency
-// counters (one lane each, relaxed loads in parallel) while the compute
-// warps work on the current item; when they are done (named barrier 2) it
-// publishes the next item at once if it is ready (named barrier 1), and only
-// then makes the finished item visible (fence, release store of its
-// counter).  It signals the finished item before it blocks on anything, so
-// the smallest unfinished ticket is always some CTA's current item.
+// A CTA is 8 compute warps and one scheduler warp, which hand items over
+// through two mailbox slots on mbarriers: the scheduler fills slot i & 1
+// with the CTA's i-th item and arrives on the slot's `ready` barrier; each
+// compute warp runs its unit of item i, arrives on the slot's `done` barrier
+// and goes straight on to item i + 1 once that is published, so warps that
+// finish early do not wait for the slowest one.  The scheduler resolves item
+// i + 1 (ticket, item, grid, and the five dependency counters polled by five
+// lanes with relaxed loads in parallel) while item i runs.  It signals a
+// finished item (fence, release store of its counter) as soon as the item's
+// `done` barrier completes — also from inside its wait for the next item's
+// dependencies — so it never blocks while it holds a finished, unsignalled
+// item: the smallest unfinished ticket is always some CTA's item in progress
+// or a published item whose dependencies are all signalled, and the launch
+// cannot deadlock.  A slot is refilled only after every compute warp has
+// finished the item it held two steps before, so no warp can miss a phase.
 
 constexpr int kCTA = kThreads + 32;  // compute warps + the scheduler warp
 
-JD void bar_sync(int id) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kCTA) : "memory"); }
-JD void bar_arrive(int id) { asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(kCTA) : "memory"); }
 JD unsigned ld_relaxed_u32(const unsigned* p) {
   unsigned v;
   asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -397,6 +402,12 @@ struct Mailbox {
   int pad_;
   JBItem it;
   JBGrid G;
+};
+
+struct BatchShared {
+  Mailbox mb[2];
+  u64 ready[2];  // count 1: the scheduler filled the slot
+  u64 done[2];   // count kWarps: every compute warp finished the slot's item
 };
 
 // Scheduler-side view of one ticket.
@@ -438,13 +449,33 @@ JD bool deps_ready(const JBatchParams& bp, const Tk& k) {
   return __all_sync(0xffffffffu, ok);
 }
 
-// Polls until ready; false if the batch is abandoned (timeout here or elsewhere).
-JD bool deps_wait(const JBatchParams& bp, const Tk& k) {
-  if (deps_ready(bp, k)) return true;
+// What the scheduler keeps of an item after publishing it: enough to signal it.
+struct Sig {
+  long long t;
+  int s, self;
+};
+
+JD Sig sig_of(const Tk& k) { return Sig{k.t, k.s, k.self}; }
+
+JD void signal_done(const JBatchParams& bp, const Sig& k) {
+  if ((threadIdx.x & 31) == 0 && k.t != bp.stall_ticket) {
+    __threadfence();
+    st_release_u32(bp.done + k.self, (unsigned)(k.s + 1));
+  }
+  __syncwarp();
+}
+
+// Polls the dependencies of `nxt` until they are ready; meanwhile signals
+// `cur` (the CTA's item i) as soon as its done barrier completes.  False if
+// the batch is abandoned (this wait ran out, or another CTA's did).
+JD bool deps_wait_serving(const JBatchParams& bp, const Tk& nxt, const Sig& cur, BatchShared& sh, int i, bool& sig) {
   const u64 t0 = globaltimer_ns();
   for (;;) {
-    __nanosleep(64);
-    if (deps_ready(bp, k)) return true;
+    if (deps_ready(bp, nxt)) return true;
+    if (!sig && mbar_try(&sh.done[i & 1], (u32)((i >> 1) & 1))) {
+      signal_done(bp, cur);
+      sig = true;
+    }
     int bad = 0;
     if ((threadIdx.x & 31) == 0) {
       bad = ld_relaxed_i32(bp.status) != 0;
@@ -454,10 +485,13 @@ JD bool deps_wait(const JBatchParams& bp, const Tk& k) {
       }
     }
     if (__shfl_sync(0xffffffffu, bad, 0)) return false;
+    __nanosleep(64);
   }
 }
 
-JD void publish(Mailbox& mb, int stop, const Tk& k) {
+// Fills slot i & 1 and marks it ready (all lanes of the scheduler warp).
+JD void publish(BatchShared& sh, int i, int stop, const Tk& k) {
+  Mailbox& mb = sh.mb[i & 1];
   if ((threadIdx.x & 31) == 0) {
     mb.stop = stop;
     mb.s = k.s;
@@ -467,62 +501,75 @@ JD void publish(Mailbox& mb, int stop, const Tk& k) {
   }
   __threadfence();  // acquire side of the relaxed dependency loads (every lane)
   __syncwarp();
-  bar_sync(1);
-}
-
-JD void signal_done(const JBatchParams& bp, const Tk& k) {
-  if ((threadIdx.x & 31) == 0 && k.t != bp.stall_ticket) {
-    __threadfence();
-    st_release_u32(bp.done + k.self, (unsigned)(k.s + 1));
-  }
+  if ((threadIdx.x & 31) == 0) mbar_arrive(&sh.ready[i & 1]);
 }
 
 template <int STAGED>
 __global__ void __launch_bounds__(kCTA, 3) jacc_k_batched(JBatchParams bp) {
   extern __shared__ __align__(16) double s_ring[];
-  __shared__ Mailbox mb;
+  __shared__ __align__(16) BatchShared sh;
   const int warp = threadIdx.x >> 5;
   const int base_item = bp.groups[0].item_begin;
+  if (threadIdx.x == 0) {
+    mbar_init(&sh.ready[0], 1);
+    mbar_init(&sh.ready[1], 1);
+    mbar_init(&sh.done[0], kWarps);
+    mbar_init(&sh.done[1], kWarps);
+    mbar_init_fence();
+  }
+  __syncthreads();
   if (warp == kWarps) {
     // ------------------------------------------------------------ scheduler warp
     int grp = 0;
-    Tk cur;
-    long long t = 0;
-    if ((threadIdx.x & 31) == 0) t = (long long)atomicAdd(bp.ticket, 1ull);
-    t = __shfl_sync(0xffffffffu, t, 0);
-    bool live = decode(bp, t, grp, base_item, cur) && deps_wait(bp, cur);
-    publish(mb, live ? 0 : 1, cur);
-    while (live) {
+    Sig cur;
+    bool live;
+    {
+      Tk first;
+      long long t = 0;
+      if ((threadIdx.x & 31) == 0) t = (long long)atomicAdd(bp.ticket, 1ull);
+      t = __shfl_sync(0xffffffffu, t, 0);
+      bool none_pending = true;  // no item of this CTA is running yet
+      live = decode(bp, t, grp, base_item, first) && deps_wait_serving(bp, first, sig_of(first), sh, 0, none_pending);
+      publish(sh, 0, live ? 0 : 1, first);
+      cur = sig_of(first);
+    }
+    for (int i = 0; live; ++i) {
+      // item i runs; resolve item i + 1, serving item i's completion meanwhile
       Tk nxt;
       long long tn = 0;
       if ((threadIdx.x & 31) == 0) tn = (long long)atomicAdd(bp.ticket, 1ull);
       tn = __shfl_sync(0xffffffffu, tn, 0);
+      bool sig = false;
       const bool has = decode(bp, tn, grp, base_item, nxt);
-      const bool ready = has && deps_ready(bp, nxt);
-      bar_sync(2);  // the compute warps are done with cur
-      if (ready) {
-        publish(mb, 0, nxt);
+      const bool ok = has && deps_wait_serving(bp, nxt, cur, sh, i, sig);
+      publish(sh, i + 1, ok ? 0 : 1, nxt);  // slot (i+1) & 1 held item i-1, finished before cur was signalled
+      if (!sig) {
+        if (!mbar_wait(&sh.done[i & 1], (u32)((i >> 1) & 1), (i64)bp.timeout_ns)) {
+          if ((threadIdx.x & 31) == 0) atomicCAS(bp.status, 0, JACC_ERR_TIMEOUT);
+          break;
+        }
         signal_done(bp, cur);
-      } else {
-        signal_done(bp, cur);
-        live = has && deps_wait(bp, nxt);
-        publish(mb, live ? 0 : 1, nxt);
       }
-      cur = nxt;
+      cur = sig_of(nxt);
+      live = ok;
     }
     return;
   }
   // -------------------------------------------------------------- compute warps
   double* ring = s_ring + warp * kRing * kSlot;
-  for (;;) {
-    bar_sync(1);
+  for (int i = 0;; ++i) {
+    if (!mbar_wait(&sh.ready[i & 1], (u32)((i >> 1) & 1), (i64)bp.timeout_ns)) {
+      if ((threadIdx.x & 31) == 0) atomicCAS(bp.status, 0, JACC_ERR_TIMEOUT);
+      break;
+    }
+    const Mailbox& mb = sh.mb[i & 1];
     if (mb.stop) break;
     const int s = mb.s;
     const int F = mb.F;
     const JBItem it = mb.it;
     const JBGrid G = mb.G;
-    const double* src = G.u[s & 1];
-    double* dst = G.u[(s + 1) & 1];
+    const double* src = (s & 1) ? G.u[1] : G.u[0];
+    double* dst = (s & 1) ? G.u[0] : G.u[1];
     const int flags = (s == 0 ? JFX_IN_F64 : 0) | (s == bp.nsweeps - 1 ? JFX_OUT_F64 : 0);
     // this warp's unit of the item: a 64-column strip of a slice of its rows
     const int across = G.cols / 64;
@@ -553,7 +600,8 @@ __global__ void __launch_bounds__(kCTA, 3) jacc_k_batched(JBatchParams bp) {
     const u64 bits = warp_max_u64(F >= 0 ? dbits(fx_to_u(rfx, F + 2)) : dbits(rnat));
     if ((threadIdx.x & 31) == 0 && bp.resid)
       atomicMax(reinterpret_cast<unsigned long long*>(bp.resid + (i64)it.g * bp.nsweeps + s), (unsigned long long)bits);
-    bar_arrive(2);
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(&sh.done[i & 1]);
   }
 }
 
