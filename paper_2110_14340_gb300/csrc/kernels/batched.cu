@@ -320,8 +320,7 @@ JD void staged_march_fx(double* ring, const double* __restrict__ u, double* __re
     const double o1 = a1 ? (outf ? fx_to(s1, F + 2) : i64_bits((s1 + 2) >> 2)) : bnd(cur[1], cu1);
     const i64 d0 = s0 - cu0 * 4, d1 = s1 - cu1 * 4;
     const u64 ad0 = a0 ? (u64)(d0 ^ (d0 >> 63)) : 0ull, ad1 = a1 ? (u64)(d1 ^ (d1 >> 63)) : 0ull;
-    const u64 m = ad0 > ad1 ? ad0 : ad1;
-    rfx = m > rfx ? m : rfx;
+    rfx = max(rfx, max(ad0, ad1));
     if (shy == 0 && c1) {
       double2 t;
       t.x = o0;
