@@ -382,6 +382,25 @@ def measure_e2e(step_host, a, b, resid, u_host, args, ws):
     return e2e
 
 
+def region_analysis_c_us(n=256, calls=200000):
+    """Microseconds per jacc_region_analyze call of the n x n 5-point interior
+    nest, timed by a plain C program (tests/c/region_timing.c) linked with
+    libjacc.so: no Python in the loop.  None if it cannot be built here."""
+    from paper_2110_14340_gb300 import build
+    libdir = os.path.dirname(build.LIB)
+    with tempfile.TemporaryDirectory() as d:
+        exe = os.path.join(d, "region_timing")
+        try:
+            subprocess.run(["gcc", "-O2", "-std=c11", os.path.join(ROOT, "tests", "c", "region_timing.c"), "-o", exe,
+                            "-I" + os.path.join(ROOT, "include"), "-L" + libdir, "-ljacc", "-Wl,-rpath," + libdir,
+                            "-L/usr/local/cuda/lib64", "-lcudart", "-Wl,-rpath,/usr/local/cuda/lib64"],
+                           check=True, capture_output=True, text=True, timeout=120)
+            r = subprocess.run([exe, str(n), str(calls)], capture_output=True, text=True, timeout=120, check=True)
+            return float(r.stdout.splitlines()[1].split()[1])
+        except Exception:
+            return None
+
+
 def _time_ms(fn, reps=3):
     """Best of `reps` CUDA-event timings of fn() on the current stream (after one warm-up call)."""
     import torch
@@ -433,7 +452,8 @@ def secondary(dev):
                                 "tile": k.info()["tile_id"], "cluster_ms": msc,
                                 "cluster_us_per_sweep": 1e3 * msc / 100,
                                 "cluster_GLUP/s": 254 * 254 * 100 / msc / 1e6,
-                                "region_analysis_us_via_python": ra_us}
+                                "region_analysis_us_via_python": ra_us,
+                                "region_analysis_us_from_c": region_analysis_c_us()}
     k.release()
     kc.release()
     # 64 batched grids x 500 sweeps: one persistent launch vs 64 plain graph launches

@@ -11,6 +11,7 @@ from paper_2110_14340_gb300 import inputs
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "tests", "c", "heat_c_client.c")
+TIMING_SRC = os.path.join(ROOT, "tests", "c", "region_timing.c")
 
 
 @pytest.fixture(scope="module")
@@ -29,6 +30,25 @@ def client(tmp_path_factory):
 
 def test_c_client_compiles_and_links(client):
     assert os.access(client, os.X_OK)
+
+
+def test_region_analysis_from_c(tmp_path):
+    # host-only: the 5-point interior nest of a 256 x 256 grid analysed from
+    # plain C, with the hulls of the golden fixture and a time per call
+    from paper_2110_14340_gb300 import build
+    lib = build.build()
+    libdir = os.path.dirname(lib)
+    exe = str(tmp_path / "region_timing")
+    subprocess.run(["gcc", "-O2", "-std=c11", "-Wall", "-Wextra", "-Werror", TIMING_SRC, "-o", exe,
+                    "-I" + os.path.join(ROOT, "include"), "-L" + libdir, "-ljacc", "-Wl,-rpath," + libdir,
+                    "-L/usr/local/cuda/lib64", "-lcudart", "-Wl,-rpath,/usr/local/cuda/lib64"],
+                   check=True, capture_output=True, text=True)
+    r = subprocess.run([exe, "256", "20000"], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    lines = r.stdout.splitlines()
+    assert lines[0] == "write [1,254]x[1,254] linear [257,65278]; read [0,255]x[0,255] linear [1,65534]"
+    us = float(lines[1].split()[1])
+    assert 0.0 < us < 1000.0
 
 
 @pytest.mark.gpu
