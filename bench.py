@@ -603,7 +603,7 @@ def profile_case(args):
     w = tuple(float(x) for x in inputs.box27_weights())
     a = inputs.uniform_torch(6, n ** 3, "cuda", torch.float32).mul_(2).sub_(1).view(n, n, n)
     b = torch.empty_like(a)
-    T = 2 if args.profile_case == "box27-tb2" else 0
+    T = {"box27-tb2": 2, "box27-tb3": 3}.get(args.profile_case, 0)
     k = jacc.Kernel(27, 32, n, n, n, coeffs=w, tile_id=3 if args.tile < 0 else args.tile, tblock=T)
     res = torch.zeros(args.sweeps, dtype=torch.float64, device="cuda")
     for _ in range(args.warmup + args.steps):
@@ -623,7 +623,7 @@ def main():
     ap.add_argument("--no-jit", action="store_true", help="use the precompiled kernel instead of the NVRTC variant")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner; use the library's default tile")
     ap.add_argument("--no-secondary", action="store_true", help="skip the other workloads' measurements")
-    ap.add_argument("--profile-case", choices=["box27", "box27-tb2", "var19", "jacobi2d", "batched"], default=None,
+    ap.add_argument("--profile-case", choices=["box27", "box27-tb2", "box27-tb3", "var19", "jacobi2d", "batched"], default=None,
                     help="run only one sweep sequence (27-point FP32 or 19-point on an --n cube; jacobi2d: 5-point FP64 --n squared, graph and cluster launch) for profilers, and exit")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the sweep kernel, if captured for this build")

@@ -219,8 +219,12 @@ jacc_status jacc_region_boxes_affine(int32_t nloops, const jacc_loop_affine* loo
  * to the launch-per-sweep sequence; jacc_launch still runs the tile kernel.
  * JACC_ERR_UNSUPPORTED if the grid does not fit a cluster the device can run.
  *
- * tblock (27PT only): temporal-blocking depth T >= 1.  Each launch then
- * performs T sweeps; jacc_sweep accounts for this.
+ * tblock (27PT FP32 only, nx a multiple of 4, T <= 3): temporal-blocking
+ * depth T >= 1.  Each launch then performs T sweeps and reads and writes
+ * the field once (8/T bytes per point-sweep); jacc_sweep accounts for this.
+ * T = 2 runs a staged two-sweep kernel whose fields are bit-identical to two
+ * single sweeps of the staged 16-byte-vector tiles; T = 3 a register-based
+ * kernel (equal within FP32 rounding).  UNSUPPORTED otherwise.
  *
  * The handle is owned by the library and stays valid until jacc_release or
  * jacc_shutdown.  Identical descriptors share one compiled kernel. */

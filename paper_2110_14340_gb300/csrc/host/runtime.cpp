@@ -354,7 +354,7 @@ extern "C" jacc_status jacc_specialize(const jacc_kernel_desc* desc, jacc_kernel
   if (desc->stencil == 19) {
     var19_geometry(desc->nx, desc->ny, desc->nz, &k->grid, &k->block);
     k->func = k->func_out = nullptr;  // launched by jacc_sweep_coeffs only
-  } else if (desc->tblock == 2 && desc->nx % 4 == 0) {
+  } else if (desc->tblock == 2) {
     // two sweeps per launch, staged: 320 threads over a 128 x 16 output tile,
     // 64-plane chunks (box27_tb2.cu)
     k->tblock = 2;
