@@ -162,13 +162,13 @@ template <class T> struct RT<T, JM_FIXED> { typedef u64 type; };
 
 // ---------------------------------------------------------------- block reductions
 
+// Maximum of a 64-bit word over the (converged) warp: the maximum of the high
+// halves, then the maximum of the low halves of the lanes that hold it; two
+// redux.sync operations instead of five shuffle rounds.
 JD u64 warp_max_u64(u64 v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    u64 w = __shfl_xor_sync(0xffffffffu, v, o);
-    v = w > v ? w : v;
-  }
-  return v;
+  const u32 hi = __reduce_max_sync(0xffffffffu, (u32)(v >> 32));
+  const u32 lo = __reduce_max_sync(0xffffffffu, (u32)(v >> 32) == hi ? (u32)v : 0u);
+  return ((u64)hi << 32) | lo;
 }
 JD double warp_sum_f64(double v) {
 #pragma unroll

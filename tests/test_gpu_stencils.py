@@ -108,7 +108,8 @@ def run_both(k, u, nsweeps):
 @pytest.mark.parametrize("shape,nsweeps,arith", [
     ((256, 256), 100, jacc.ARITH_AUTO), ((130, 37), 7, jacc.ARITH_AUTO), ((3, 3), 1, jacc.ARITH_AUTO),
     ((17, 255), 2, jacc.ARITH_AUTO), ((64, 41), 1, jacc.ARITH_AUTO), ((101, 37), 5, jacc.ARITH_NATIVE),
-    ((320, 300), 3, jacc.ARITH_AUTO)])
+    ((320, 300), 3, jacc.ARITH_AUTO), ((64, 41), 1100, jacc.ARITH_AUTO), ((40, 52), 513, jacc.ARITH_NATIVE),
+    ((256, 256), 1025, jacc.ARITH_AUTO)])
 def test_jacobi2d_cluster_resident_bit_identical_to_per_sweep(orc, shape, nsweeps, arith):
     # the whole sequence in one cluster launch: result buffer, the other
     # buffer (sweep n-1 in the internal form) and residuals equal the
