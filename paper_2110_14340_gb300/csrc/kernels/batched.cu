@@ -24,14 +24,16 @@
 // deadlock.  Waits are bounded by %globaltimer; a wait that gives up writes
 // JACC_ERR_TIMEOUT to the status word and every CTA leaves.
 //
-// Loads.  In the staged variant each warp streams its 64-column strip of an
-// item's rows through a ring of 16 rows in shared memory with 16-byte
-// cp.async.cg copies (L2 only: the same launch writes the fields, and L1 is
-// not coherent), so up to 15 rows per warp are in flight without registers
-// (at HBM latency under load, a shallower ring leaves each warp waiting).
-// A row whose start is not 16-byte aligned (odd nx, odd row) is staged one
-// element to the right.  The register variant marches rows through
-// registers with ld.global.cg, as the single-grid kernels do.
+// Loads.  In the staged variant each warp streams its strip of an item's
+// rows through a ring in shared memory: fixed-point units (every grid whose
+// maximum allows it) fetch each row with one bulk copy issued by one lane
+// and completed on the row slot's mbarrier, 8 rows in flight per warp, and
+// intermediate sweeps give each lane 4 columns of a 128-column strip; the
+// native FP64 path stages 64-column strips with 16-byte cp.async.cg copies
+// (L2 only: the same launch writes the fields, and L1 is not coherent), 16
+// rows in flight.  A row whose start is not 16-byte aligned (odd nx, odd
+// row) is staged one element to the right.  The register variant marches
+// rows through registers with ld.global.cg, as the single-grid kernels do.
 #include <cuda_runtime.h>
 
 #include "../host/jacc_internal.h"
@@ -122,7 +124,7 @@ JD void stage_row(const StagePlan& P, double* sp, const double* rp, int sh, bool
 // (FX: resident 64-bit fixed point, EDGE: first or last sweep) or of the
 // native jacobi_march, value for value.  Row r lives in slot (r - ya + 1)
 // mod kRing; rows ya-1 .. yb are staged (those inside the grid).  The
-// kernel runs fixed-point units through staged_march_fx below and uses this
+// kernel runs fixed-point units through bulk_march_fx below and uses this
 // one for the native FP64 path (grids with a non-finite or tiny maximum).
 template <bool FX, bool EDGE>
 JD void staged_march(double* ring, const double* __restrict__ u, double* __restrict__ v, i64 nx64, i64 ny, i64 x064,
@@ -242,45 +244,114 @@ JD void staged_march(double* ring, const double* __restrict__ u, double* __restr
   __syncwarp();
 }
 
-// The fixed-point march of any unit, fast: rows are counted in 32-bit
-// integers, the per-lane facts (columns inside the grid, interior columns,
-// the staging plan) are fixed per unit, a boundary row is a uniform test per
-// row, and three rows are done per iteration so the row registers rotate
-// without copies.  Outputs and
-// residual are those of jacobi_fx_march, value for value.
-template <bool EDGE>
-JD void staged_march_fx(double* ring, const double* __restrict__ u, double* __restrict__ v, i64 nx64, int ny, int x0,
-                        int ya, int yb, int F, int flags, u64& rfx) {
+// ---------------------------------------------------------------- bulk-copy march
+//
+// The fixed-point march of the staged variant.  A warp's unit is W = 32 CPL
+// columns (CPL = 4 for items at least 128 columns wide, else 2); lane l owns
+// columns x0 + CPL l .. x0 + CPL l + CPL - 1.  Rows stream through a ring of
+// kRingB slots of W + 4 doubles, each slot with its own mbarrier: lane 0
+// fetches row r with ONE bulk copy (cp.async.bulk) of the 16-byte-aligned
+// span that covers columns [max(x0 - 1, 0), min(x0 + W, nx - 1)], counted in
+// bytes on the slot's barrier.  Element x of row r lands at
+// slot[x - x0 + 2 + sh], sh = (r nx) & 1, which puts the span's even start on
+// an even slot index.  The field's last element, whose pair would run past
+// the end of the field, goes through a register.  A row outside the grid or
+// past the unit's halo row is not fetched, but lane 0 still arrives on its
+// slot's barrier, so every slot completes one phase per staged row and the
+// warp's running row count `gq` (kept across units) gives each wait its
+// slot and parity.  Staging a row costs a few instructions on one lane, and
+// the row loop handles CPL columns per lane, so the per-row bookkeeping is
+// spread over 2 CPL updates.  Outputs and residual are those of
+// jacobi_fx_march, value for value.  False if a wait ran out (after a
+// bounded wait for the copies still in flight).
+constexpr int kRingB = 8;  // staged rows per warp in the bulk-copy march (a power of two)
+static_assert(kRingB * (128 + 4) <= kRing * kSlot, "the bulk-copy ring fits the staged ring");
+
+JD void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+template <int CPL, bool EDGE>
+JD bool bulk_march_fx(double* ring, u64* bars, u32& gq, const double* __restrict__ u, double* __restrict__ v,
+                      i64 nx64, int ny, int x0, int ya, int yb, int F, int flags, u64 timeout_ns, u64& rfx) {
+  constexpr int W = 32 * CPL, SLOT = W + 4;
   const int lane = threadIdx.x & 31;
   const int nx = (int)nx64;
-  const int xa = x0 + 2 * lane;
+  const i64 ntot = nx64 * ny;
+  const int xl = x0 + CPL * lane;  // the lane's first column
   const bool inf = EDGE && (flags & JFX_IN_F64);
   const bool outf = EDGE && (flags & JFX_OUT_F64);
-  const bool c0 = xa < nx, c1 = xa + 1 < nx;
-  const bool in0 = xa >= 1 && xa <= nx - 2, in1 = xa + 1 <= nx - 2;
+  bool cin[CPL], cint[CPL];  // column inside the grid; interior column
+  bool call = true, iall = true;
+#pragma unroll
+  for (int e = 0; e < CPL; ++e) {
+    cin[e] = xl + e < nx;
+    cint[e] = xl + e >= 1 && xl + e <= nx - 2;
+    call = call && cin[e];
+    iall = iall && cint[e];
+  }
+  const bool ufast = __all_sync(0xffffffffu, iall);  // no boundary column in the unit
   const int odd = nx & 1;
-  const StagePlan P = stage_plan(nx, x0, lane);
-  int rs = ya - 1, shs = odd & (ya - 1), js = 0;
-  const double* rps = u + (i64)(ya - 1) * nx64;
+  const int clo = x0 >= 1 ? x0 - 1 : 0;
+  const int chi = x0 + W <= nx - 1 ? x0 + W : nx - 1;
+  const u32 g0 = gq;  // running count of row ya - 1
+  int rs = ya - 1;    // next row to stage
+  __syncwarp();
+  if (lane == 0) fence_proxy_async_smem();  // the ring's earlier generic-proxy use precedes these copies
   auto stage_next = [&]() {
-    if (rs >= 0 && rs <= yb && rs < ny) stage_row(P, ring + (js & (kRing - 1)) * kSlot, rps, shs, rs == ny - 1, nx);
-    cp_async_commit();
+    if (lane == 0) {
+      const int j = (int)(gq & (kRingB - 1));
+      u64* bar = bars + j;
+      double* slot = ring + j * SLOT;
+      i64 es = 0, ee = 0, base = 0;
+      if (rs >= 0 && rs <= yb && rs < ny) {
+        const i64 rb = (i64)rs * nx64;
+        base = rb + x0 - 2 - (rb & 1);  // the element at slot[0]
+        es = (rb + clo) & ~1ll;
+        ee = (rb + chi + 2) & ~1ll;
+        if (ee > ntot) {  // the span ends at the field's odd last element
+          ee = ntot - 1;
+          slot[ntot - 1 - base] = __ldcg(u + ntot - 1);
+        }
+      }
+      if (ee > es) {
+        const u32 bytes = (u32)(ee - es) * 8u;
+        mbar_expect_tx(bar, bytes);
+        bulk_g2s(slot + (es - base), u + es, bytes, bar);
+      } else {
+        mbar_arrive(bar);
+      }
+    }
     ++rs;
-    rps += nx64;
-    shs ^= odd;
-    ++js;
+    ++gq;
   };
-  auto own = [&](const double* sp, int sh, bool inside, double (&o)[2]) {
-    o[0] = o[1] = 0.0;
-    if (!inside) return;
-    const double* p = sp + 2 * lane + 2 + sh;
-    if (sh == 0 && c1) {
-      const double2 t = *reinterpret_cast<const double2*>(p);
-      o[0] = t.x;
-      o[1] = t.y;
-    } else if (c0) {
+  auto slot_of = [&](int r) -> const double* { return ring + ((g0 + (u32)(r - ya + 1)) & (kRingB - 1)) * SLOT; };
+  auto wait_row = [&](int r) -> bool {
+    const u32 q = g0 + (u32)(r - ya + 1);
+    return mbar_wait(bars + (q & (kRingB - 1)), (q / kRingB) & 1u, (i64)timeout_ns);
+  };
+  // the lane's CPL raw words of a staged row (zero outside the grid's rows)
+  auto own = [&](const double* sp, int sh, bool inside, double (&o)[CPL]) {
+    if (!inside) {
+#pragma unroll
+      for (int e = 0; e < CPL; ++e) o[e] = 0.0;
+      return;
+    }
+    const double* p = sp + CPL * lane + 2 + sh;
+    if (sh == 0) {
+#pragma unroll
+      for (int e = 0; e < CPL; e += 2) {
+        const double2 t = *reinterpret_cast<const double2*>(p + e);
+        o[e] = t.x;
+        o[e + 1] = t.y;
+      }
+    } else {
       o[0] = p[0];
-      if (c1) o[1] = p[1];
+#pragma unroll
+      for (int e = 1; e + 1 < CPL; e += 2) {
+        const double2 t = *reinterpret_cast<const double2*>(p + e);
+        o[e] = t.x;
+        o[e + 1] = t.y;
+      }
+      o[CPL - 1] = p[CPL - 1];
     }
   };
   auto cvt = [&](double raw) -> i64 { return inf ? fx_from(raw, F) : bits_i64(raw); };
@@ -290,63 +361,93 @@ JD void staged_march_fx(double* ring, const double* __restrict__ u, double* __re
     if (outf) return fx_to(w, F);
     return i64_bits(w);
   };
+  // bounded wait for the copies still in flight (the last kRingB staged rows)
+  auto drain = [&]() {
+    for (u32 q = gq - kRingB; q != gq; ++q) mbar_wait(bars + (q & (kRingB - 1)), (q / kRingB) & 1u, 1000000);
+  };
+
 #pragma unroll 1
-  for (int j = 0; j < kRing; ++j) stage_next();
-  cp_async_wait<kRing - 2>();  // rows ya-1 and ya
-  __syncwarp();
+  for (int j = 0; j < kRingB; ++j) stage_next();
+  if (!wait_row(ya - 1) || !wait_row(ya)) {
+    drain();
+    return false;
+  }
   int shy = odd & ya;  // parity of row y
-  double ra[2], rb[2], rc[2];
-  own(ring, shy ^ odd, ya >= 1, ra);
-  own(ring + kSlot, shy, true, rb);
+  double ra[CPL], rb[CPL], rc[CPL];
+  own(slot_of(ya - 1), shy ^ odd, ya >= 1, ra);
+  own(slot_of(ya), shy, true, rb);
   __syncwarp();
   stage_next();
-  double* out = v + (i64)ya * nx64 + xa;
-  int jy = 1, y = ya;
+  double* out = v + (i64)ya * nx64 + xl;
+  int y = ya;
+  bool ok = true;
   // one row: up, cur -> dn (raw words); writes row y
-  auto step = [&](const double (&up)[2], const double (&cur)[2], double (&dn)[2]) {
-    cp_async_wait<kRing - 2>();  // row y+1
-    __syncwarp();
-    const double* sy = ring + (jy & (kRing - 1)) * kSlot;
-    own(ring + ((jy + 1) & (kRing - 1)) * kSlot, shy ^ odd, y + 1 < ny, dn);
-    const double* cs = sy + 2 * lane + 2 + shy;
-    const double rl = in0 ? cs[-1] : 0.0;
-    const double rr = in1 ? cs[2] : 0.0;
+  auto step = [&](const double (&up)[CPL], const double (&cur)[CPL], double (&dn)[CPL]) {
+    if (!ok || !wait_row(y + 1)) {
+      ok = false;
+      return;
+    }
+    own(slot_of(y + 1), shy ^ odd, y + 1 < ny, dn);
+    const double* cs = slot_of(y) + CPL * lane + 2 + shy;
+    const double rl = cs[-1], rr = cs[CPL];  // columns left and right of the lane's (any value outside)
     const bool yint = y >= 1 && y <= ny - 2;
-    const bool a0 = yint && in0, a1 = yint && in1;
-    const i64 cu0 = cvt(cur[0]), cu1 = cvt(cur[1]);
-    const i64 s0 = (cvt(up[0]) + cvt(dn[0])) + (cvt(rl) + cu1);
-    const i64 s1 = (cvt(up[1]) + cvt(dn[1])) + (cu0 + cvt(rr));
-    const double o0 = a0 ? (outf ? fx_to(s0, F + 2) : i64_bits((s0 + 2) >> 2)) : bnd(cur[0], cu0);
-    const double o1 = a1 ? (outf ? fx_to(s1, F + 2) : i64_bits((s1 + 2) >> 2)) : bnd(cur[1], cu1);
-    const i64 d0 = s0 - cu0 * 4, d1 = s1 - cu1 * 4;
-    const u64 ad0 = a0 ? (u64)(d0 ^ (d0 >> 63)) : 0ull, ad1 = a1 ? (u64)(d1 ^ (d1 >> 63)) : 0ull;
-    rfx = max(rfx, max(ad0, ad1));
-    if (shy == 0 && c1) {
-      double2 t;
-      t.x = o0;
-      t.y = o1;
-      *reinterpret_cast<double2*>(out) = t;
-    } else if (c0) {
-      out[0] = o0;
-      if (c1) out[1] = o1;
+    i64 c[CPL], sm[CPL];
+#pragma unroll
+    for (int e = 0; e < CPL; ++e) c[e] = cvt(cur[e]);
+#pragma unroll
+    for (int e = 0; e < CPL; ++e) {
+      const i64 w = e == 0 ? cvt(rl) : c[e - 1];
+      const i64 z = e == CPL - 1 ? cvt(rr) : c[e + 1];
+      sm[e] = (cvt(up[e]) + cvt(dn[e])) + (w + z);
+    }
+    double o[CPL];
+    if (!EDGE && ufast && yint) {
+#pragma unroll
+      for (int e = 0; e < CPL; ++e) {
+        o[e] = i64_bits((sm[e] + 2) >> 2);
+        const i64 d = sm[e] - c[e] * 4;
+        const u64 ad = (u64)(d ^ (d >> 63));  // |d| (one less if negative)
+        rfx = ad > rfx ? ad : rfx;
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < CPL; ++e) {
+        const bool a = yint && cint[e];
+        o[e] = a ? (outf ? fx_to(sm[e], F + 2) : i64_bits((sm[e] + 2) >> 2)) : bnd(cur[e], c[e]);
+        const i64 d = sm[e] - c[e] * 4;
+        const u64 ad = a ? (u64)(d ^ (d >> 63)) : 0ull;
+        rfx = ad > rfx ? ad : rfx;
+      }
+    }
+    if (call && shy == 0) {
+#pragma unroll
+      for (int e = 0; e < CPL; e += 2) {
+        double2 t;
+        t.x = o[e];
+        t.y = o[e + 1];
+        *reinterpret_cast<double2*>(out + e) = t;
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < CPL; ++e)
+        if (cin[e]) out[e] = o[e];
     }
     out += nx64;
     shy ^= odd;
-    ++jy;
     ++y;
     __syncwarp();
-    stage_next();
+    stage_next();  // into the slot of the row just finished
   };
 #pragma unroll 1
-  while (y + 2 < yb) {
+  while (ok && y + 2 < yb) {
     step(ra, rb, rc);
     step(rb, rc, ra);
     step(rc, ra, rb);
   }
   if (y < yb) step(ra, rb, rc);
   if (y < yb) step(rb, rc, ra);
-  cp_async_wait<0>();
-  __syncwarp();
+  if (!ok) drain();
+  return ok;
 }
 
 // ---------------------------------------------------------------- register march
@@ -405,8 +506,9 @@ struct Mailbox {
 
 struct BatchShared {
   Mailbox mb[2];
-  u64 ready[2];  // count 1: the scheduler filled the slot
-  u64 done[2];   // count kWarps: every compute warp finished the slot's item
+  u64 ready[2];              // count 1: the scheduler filled the slot
+  u64 done[2];               // count kWarps: every compute warp finished the slot's item
+  u64 rows[kWarps][kRingB];  // count 1 + bytes: a compute warp's staged row (bulk-copy march)
 };
 
 // Scheduler-side view of one ticket.
@@ -504,7 +606,7 @@ JD void publish(BatchShared& sh, int i, int stop, const Tk& k) {
 }
 
 template <int STAGED>
-__global__ void __launch_bounds__(kCTA, 3) jacc_k_batched(JBatchParams bp) {
+__global__ void __launch_bounds__(kCTA, STAGED ? 2 : 3) jacc_k_batched(JBatchParams bp) {
   extern __shared__ __align__(16) double s_ring[];
   __shared__ __align__(16) BatchShared sh;
   const int warp = threadIdx.x >> 5;
@@ -514,6 +616,8 @@ __global__ void __launch_bounds__(kCTA, 3) jacc_k_batched(JBatchParams bp) {
     mbar_init(&sh.ready[1], 1);
     mbar_init(&sh.done[0], kWarps);
     mbar_init(&sh.done[1], kWarps);
+    for (int w = 0; w < kWarps; ++w)
+      for (int j = 0; j < kRingB; ++j) mbar_init(&sh.rows[w][j], 1);
     mbar_init_fence();
   }
   __syncthreads();
@@ -556,6 +660,7 @@ __global__ void __launch_bounds__(kCTA, 3) jacc_k_batched(JBatchParams bp) {
   }
   // -------------------------------------------------------------- compute warps
   double* ring = s_ring + warp * kRing * kSlot;
+  u32 gq = 0;  // rows this warp has staged through its bulk-copy ring
   for (int i = 0;; ++i) {
     if (!mbar_wait(&sh.ready[i & 1], (u32)((i >> 1) & 1), (i64)bp.timeout_ns)) {
       if ((threadIdx.x & 31) == 0) atomicCAS(bp.status, 0, JACC_ERR_TIMEOUT);
@@ -570,10 +675,13 @@ __global__ void __launch_bounds__(kCTA, 3) jacc_k_batched(JBatchParams bp) {
     const double* src = (s & 1) ? G.u[1] : G.u[0];
     double* dst = (s & 1) ? G.u[0] : G.u[1];
     const int flags = (s == 0 ? JFX_IN_F64 : 0) | (s == bp.nsweeps - 1 ? JFX_OUT_F64 : 0);
-    // this warp's unit of the item: a 64-column strip of a slice of its rows
-    const int across = G.cols / 64;
+    // this warp's unit of the item: a strip of Wu columns (128 in the
+    // bulk-copy march of intermediate sweeps of items at least 128 wide, else
+    // 64) of a slice of its rows
+    const int Wu = (STAGED && F >= 0 && G.cols >= 128 && !flags) ? 128 : 64;
+    const int across = G.cols / Wu;
     const int slices = kWarps / across;
-    const i64 x0 = (i64)it.c * G.cols + 64 * (warp % across);
+    const i64 x0 = (i64)it.c * G.cols + Wu * (warp % across);
     const i64 r0 = (i64)it.b * G.rows;
     const i64 r1 = r0 + G.rows < G.ny ? r0 + G.rows : G.ny;
     const i64 h = (r1 - r0 + slices - 1) / slices;
@@ -581,11 +689,20 @@ __global__ void __launch_bounds__(kCTA, 3) jacc_k_batched(JBatchParams bp) {
     const i64 yb = ya + h < r1 ? ya + h : r1;
     u64 rfx = 0;
     double rnat = 0.0;
-    if (x0 < G.nx && ya < yb) {
+    // after a wait anywhere ran out the batch is abandoned: items still
+    // handed out are passed through without work
+    if (x0 < G.nx && ya < yb && ld_relaxed_i32(bp.status) == 0) {
       if constexpr (STAGED) {
         if (F >= 0) {
-          if (flags) staged_march_fx<true>(ring, src, dst, G.nx, (int)G.ny, (int)x0, (int)ya, (int)yb, F, flags, rfx);
-          else staged_march_fx<false>(ring, src, dst, G.nx, (int)G.ny, (int)x0, (int)ya, (int)yb, F, flags, rfx);
+          const int nyi = (int)G.ny, x0i = (int)x0, yai = (int)ya, ybi = (int)yb;
+          const u64 tmo = bp.timeout_ns;
+          bool ok;
+          if (Wu == 128)
+            ok = bulk_march_fx<4, false>(ring, sh.rows[warp], gq, src, dst, G.nx, nyi, x0i, yai, ybi, F, flags, tmo, rfx);
+          else
+            ok = flags ? bulk_march_fx<2, true>(ring, sh.rows[warp], gq, src, dst, G.nx, nyi, x0i, yai, ybi, F, flags, tmo, rfx)
+                       : bulk_march_fx<2, false>(ring, sh.rows[warp], gq, src, dst, G.nx, nyi, x0i, yai, ybi, F, flags, tmo, rfx);
+          if (!ok && (threadIdx.x & 31) == 0) atomicCAS(bp.status, 0, JACC_ERR_TIMEOUT);
         } else {
           staged_march<false, false>(ring, src, dst, G.nx, G.ny, x0, ya, yb, F, flags, rfx, rnat);
         }
