@@ -612,11 +612,17 @@ jacc_status jacc_costmodel_release(jacc_costmodel m);
  * fit), item order within a group (0: grid by grid, largest grid first;
  * 1: round-robin over the group's grids), the L2 budget per group in bytes
  * of both fields (0 = 40 % of the device's L2; -1 = one group), and the
- * load path (march 0: each warp stages its rows in shared memory with
- * cp.async, 8 rows deep; 1: rows marched through registers).  timeout_ms
- * bounds every device wait (0 = 2000 ms).  test_stall_ticket is a
- * fault-injection hook for tests: that ticket never reports completion, so
- * the waits behind it time out; -1 = off.  jacc_batch_set_tiles overrides
+ * load path (march 0: each warp stages its rows in shared memory, one bulk
+ * copy per row completed on the row slot's mbarrier, 8 rows in flight, or
+ * 16-byte cp.async copies for grids on the native FP64 path; 1: rows
+ * marched through registers).  timeout_ms bounds every device wait (0 =
+ * 2000 ms).  test_stall_ticket and test_stall_row are fault-injection hooks
+ * for tests: that ticket never reports completion, so the waits behind it
+ * time out (-1 = off); the first compute warp of CTA 0 never fetches the
+ * test_stall_row-th row it stages in the bulk-copy march, so its wait for
+ * that row times out (0 = off).  Either way the launch ends early with
+ * JACC_ERR_TIMEOUT in the status that jacc_batch_status reports, and the
+ * fields hold partial results.  jacc_batch_set_tiles overrides
  * the tile of each grid (rows, cols; 0 = from item_points) and
  * jacc_batch_get_tiles reports every grid's tile, item count and group.
  * jacc_batch_tune times, for probe_sweeps sweeps on the batch's own buffers
@@ -640,7 +646,7 @@ typedef struct {
   int64_t test_stall_ticket; /* fault injection for tests; -1 = off               */
   int64_t group_bytes;       /* L2 budget per group; 0 = 40 % of L2, -1 = one     */
   int32_t march;             /* 0 staged in shared memory, 1 registers            */
-  int32_t reserved;          /* 0                                                 */
+  int32_t test_stall_row;    /* fault injection for tests; 0 = off                */
 } jacc_batch_config;
 
 typedef struct {

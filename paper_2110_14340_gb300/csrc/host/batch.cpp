@@ -64,7 +64,7 @@ static void config_defaults(jacc_batch_config* c) {
   c->test_stall_ticket = -1;
   c->group_bytes = 0;
   c->march = 0;
-  c->reserved = 0;
+  c->test_stall_row = 0;
 }
 
 static bool valid_cols(int c) { return c == 64 || c == 128 || c == 256 || c == 512; }
@@ -93,6 +93,7 @@ static jacc_status plan(Batch& b, const jacc_batch_config& in) {
   if (c.order != 0 && c.order != 1) return fail(JACC_ERR_INVALID_ARG, "batch order must be 0 or 1");
   if (c.march != 0 && c.march != 1) return fail(JACC_ERR_INVALID_ARG, "batch march must be 0 or 1");
   if (c.ctas_per_sm < 0) return fail(JACC_ERR_INVALID_ARG, "ctas_per_sm < 0");
+  if (c.test_stall_row < 0) return fail(JACC_ERR_INVALID_ARG, "test_stall_row < 0");
   const int ng = static_cast<int>(b.grids.size());
   std::vector<JBGrid> hg(ng);
   int next_item = 0;
@@ -227,6 +228,7 @@ static jacc_status enqueue(Batch& b, int32_t nsweeps, double* resid, cudaStream_
   bp.resid = resid;
   bp.timeout_ns = static_cast<u64>(b.cfg.timeout_ms) * 1000000ull;
   bp.stall_ticket = b.cfg.test_stall_ticket;
+  bp.stall_row = b.cfg.test_stall_row;
   return cuda_check(launch_batched(bp, b.nctas, s), "batched persistent launch");
 }
 
@@ -424,6 +426,7 @@ extern "C" jacc_status jacc_batch_tune(jacc_batch h, int32_t probe_sweeps, uintp
           c.group_bytes = gb;
           c.item_points = pts;
           c.test_stall_ticket = -1;
+          c.test_stall_row = 0;
           st = replan(c);
           double t = 1e300;
           if (!st) st = time_run(b, probe_sweeps, s, 0, static_cast<int>(b.hgroups.size()), 2, e0, e1, &t);

@@ -263,7 +263,8 @@ JD void staged_march(double* ring, const double* __restrict__ u, double* __restr
 // the row loop handles CPL columns per lane, so the per-row bookkeeping is
 // spread over 2 CPL updates.  Outputs and residual are those of
 // jacobi_fx_march, value for value.  False if a wait ran out (after a
-// bounded wait for the copies still in flight).
+// bounded wait for the copies still in flight).  stall > 0 is a test hook:
+// the warp never stages its stall-th row (counted by gq from 1).
 constexpr int kRingB = 8;  // staged rows per warp in the bulk-copy march (a power of two)
 static_assert(kRingB * (128 + 4) <= kRing * kSlot, "the bulk-copy ring fits the staged ring");
 
@@ -271,7 +272,7 @@ JD void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;"
 
 template <int CPL, bool EDGE>
 JD bool bulk_march_fx(double* ring, u64* bars, u32& gq, const double* __restrict__ u, double* __restrict__ v,
-                      i64 nx64, int ny, int x0, int ya, int yb, int F, int flags, u64 timeout_ns, u64& rfx) {
+                      i64 nx64, int ny, int x0, int ya, int yb, int F, int flags, u64 timeout_ns, int stall, u64& rfx) {
   constexpr int W = 32 * CPL, SLOT = W + 4;
   const int lane = threadIdx.x & 31;
   const int nx = (int)nx64;
@@ -297,7 +298,9 @@ JD bool bulk_march_fx(double* ring, u64* bars, u32& gq, const double* __restrict
   __syncwarp();
   if (lane == 0) fence_proxy_async_smem();  // the ring's earlier generic-proxy use precedes these copies
   auto stage_next = [&]() {
-    if (lane == 0) {
+    // the test hook: the stall-th staged row is neither fetched nor arrived
+    // on, so the wait for it runs out
+    if (lane == 0 && (stall == 0 || gq + 1 != (u32)stall)) {
       const int j = (int)(gq & (kRingB - 1));
       u64* bar = bars + j;
       double* slot = ring + j * SLOT;
@@ -696,12 +699,15 @@ __global__ void __launch_bounds__(kCTA, STAGED ? 2 : 3) jacc_k_batched(JBatchPar
         if (F >= 0) {
           const int nyi = (int)G.ny, x0i = (int)x0, yai = (int)ya, ybi = (int)yb;
           const u64 tmo = bp.timeout_ns;
+          const int stall = (blockIdx.x == 0 && warp == 0) ? bp.stall_row : 0;
+          u64* bars = sh.rows[warp];
           bool ok;
           if (Wu == 128)
-            ok = bulk_march_fx<4, false>(ring, sh.rows[warp], gq, src, dst, G.nx, nyi, x0i, yai, ybi, F, flags, tmo, rfx);
+            ok = bulk_march_fx<4, false>(ring, bars, gq, src, dst, G.nx, nyi, x0i, yai, ybi, F, flags, tmo, stall, rfx);
+          else if (flags)
+            ok = bulk_march_fx<2, true>(ring, bars, gq, src, dst, G.nx, nyi, x0i, yai, ybi, F, flags, tmo, stall, rfx);
           else
-            ok = flags ? bulk_march_fx<2, true>(ring, sh.rows[warp], gq, src, dst, G.nx, nyi, x0i, yai, ybi, F, flags, tmo, rfx)
-                       : bulk_march_fx<2, false>(ring, sh.rows[warp], gq, src, dst, G.nx, nyi, x0i, yai, ybi, F, flags, tmo, rfx);
+            ok = bulk_march_fx<2, false>(ring, bars, gq, src, dst, G.nx, nyi, x0i, yai, ybi, F, flags, tmo, stall, rfx);
           if (!ok && (threadIdx.x & 31) == 0) atomicCAS(bp.status, 0, JACC_ERR_TIMEOUT);
         } else {
           staged_march<false, false>(ring, src, dst, G.nx, G.ny, x0, ya, yb, F, flags, rfx, rnat);

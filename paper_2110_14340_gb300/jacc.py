@@ -74,7 +74,7 @@ class Grid(C.Structure):
 class BatchConfig(C.Structure):
     _fields_ = [("item_points", C.c_int32), ("ctas_per_sm", C.c_int32), ("order", C.c_int32),
                 ("timeout_ms", C.c_int32), ("test_stall_ticket", C.c_int64), ("group_bytes", C.c_int64),
-                ("march", C.c_int32), ("reserved", C.c_int32)]
+                ("march", C.c_int32), ("test_stall_row", C.c_int32)]
 
 
 class TuneTable(C.Structure):
@@ -594,14 +594,16 @@ class Sched:
 
 def _cfg_dict(c):
     return dict(item_points=c.item_points, ctas_per_sm=c.ctas_per_sm, order=c.order, timeout_ms=c.timeout_ms,
-                test_stall_ticket=c.test_stall_ticket, group_bytes=c.group_bytes, march=c.march)
+                test_stall_ticket=c.test_stall_ticket, group_bytes=c.group_bytes, march=c.march,
+                test_stall_row=c.test_stall_row)
 
 
-def _cfg_struct(item_points=0, ctas_per_sm=0, order=0, timeout_ms=0, test_stall_ticket=-1, group_bytes=0, march=0):
+def _cfg_struct(item_points=0, ctas_per_sm=0, order=0, timeout_ms=0, test_stall_ticket=-1, group_bytes=0, march=0,
+                test_stall_row=0):
     c = BatchConfig()
     c.item_points, c.ctas_per_sm, c.order = item_points, ctas_per_sm, order
     c.timeout_ms, c.test_stall_ticket = timeout_ms, test_stall_ticket
-    c.group_bytes, c.march, c.reserved = group_bytes, march, 0
+    c.group_bytes, c.march, c.test_stall_row = group_bytes, march, test_stall_row
     return c
 
 

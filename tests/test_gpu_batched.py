@@ -3,8 +3,9 @@
 Each grid must match its own single-grid oracle run; every schedule (load
 path, item size, per-grid tiles, group budget, order, CTAs per SM) gives the
 same bits (the fixed-point arithmetic is exact per point, and the native
-path evaluates each point the same way); a stalled ticket makes the bounded
-waits time out with JACC_ERR_TIMEOUT and leaves the context usable.
+path evaluates each point the same way); a stalled ticket, or a staged row
+that is never fetched, makes the bounded waits time out with
+JACC_ERR_TIMEOUT and leaves the context usable.
 Widths below one 64-column strip, odd widths (rows that start off a 16-byte
 boundary) and fields with an odd number of points (whose last element is
 staged through a register) are included.
@@ -180,6 +181,26 @@ def test_stalled_ticket_times_out_and_context_survives(march):
     b.status()
     x = torch.ones(4, device="cuda") * 2
     assert float(x.sum().item()) == 8.0
+
+
+def test_stalled_row_copy_times_out_and_context_survives(orc):
+    # the first compute warp of CTA 0 never fetches its 3rd staged row: its
+    # bounded wait for that row's barrier runs out, the launch ends early
+    # with JACC_ERR_TIMEOUT, and the next launch is correct
+    hosts, fields = make(SHAPES[:3], seed=7)
+    b = jacc.Batch(fields, item_points=1024, timeout_ms=20, test_stall_row=3, march=0)
+    b.sweep(4, graph=False)
+    with pytest.raises(jacc.JaccError) as e:
+        b.status()
+    assert e.value.status == jacc.ERR_TIMEOUT
+    b.configure(item_points=1024, timeout_ms=2000, test_stall_row=0, march=0)
+    reset(fields, hosts)
+    fb = b.sweep(6)
+    b.status()
+    got = results(fields, fb)
+    for g in range(3):
+        o, _ = orc.jacobi2d_run(hosts[g], 6)
+        assert nerr(got[g], o) <= TOL64, g
 
 
 def test_tuner_returns_a_valid_schedule():
