@@ -60,7 +60,10 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kRing = 16;  // staged rows per warp (a power of two)
 constexpr int kSlot = 68;  // doubles per staged row: columns x0-2 .. x0+65 (one more when shifted)
-constexpr int kStagedSmem = kWarps * kRing * kSlot * 8;
+constexpr int kRingB = 8;  // staged rows per warp in the bulk-copy march
+constexpr int kSlotB = 128 + 4;  // doubles per bulk-staged row of a 128-column strip
+constexpr int kRingWords = kRing * kSlot > kRingB * kSlotB ? kRing * kSlot : kRingB * kSlotB;  // per warp
+constexpr int kStagedSmem = kWarps * kRingWords * 8;
 
 // ---------------------------------------------------------------- staged march
 
@@ -265,9 +268,6 @@ JD void staged_march(double* ring, const double* __restrict__ u, double* __restr
 // jacobi_fx_march, value for value.  False if a wait ran out (after a
 // bounded wait for the copies still in flight).  stall > 0 is a test hook:
 // the warp never stages its stall-th row (counted by gq from 1).
-constexpr int kRingB = 8;  // staged rows per warp in the bulk-copy march (a power of two)
-static_assert(kRingB * (128 + 4) <= kRing * kSlot, "the bulk-copy ring fits the staged ring");
-
 JD void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 template <int CPL, bool EDGE>
@@ -297,11 +297,12 @@ JD bool bulk_march_fx(double* ring, u64* bars, u32& gq, const double* __restrict
   int rs = ya - 1;    // next row to stage
   __syncwarp();
   if (lane == 0) fence_proxy_async_smem();  // the ring's earlier generic-proxy use precedes these copies
+  // the test hook: the stall-th staged row is neither fetched nor arrived
+  // on, so the wait for it runs out (no row has this count otherwise)
+  const u32 stall_q = stall > 0 ? (u32)(stall - 1) : 0xffffffffu;
   auto stage_next = [&]() {
-    // the test hook: the stall-th staged row is neither fetched nor arrived
-    // on, so the wait for it runs out
-    if (lane == 0 && (stall == 0 || gq + 1 != (u32)stall)) {
-      const int j = (int)(gq & (kRingB - 1));
+    if (lane == 0 && gq != stall_q) {
+      const int j = (int)(gq % kRingB);
       u64* bar = bars + j;
       double* slot = ring + j * SLOT;
       i64 es = 0, ee = 0, base = 0;
@@ -326,10 +327,10 @@ JD bool bulk_march_fx(double* ring, u64* bars, u32& gq, const double* __restrict
     ++rs;
     ++gq;
   };
-  auto slot_of = [&](int r) -> const double* { return ring + ((g0 + (u32)(r - ya + 1)) & (kRingB - 1)) * SLOT; };
+  auto slot_of = [&](int r) -> const double* { return ring + ((g0 + (u32)(r - ya + 1)) % kRingB) * SLOT; };
   auto wait_row = [&](int r) -> bool {
     const u32 q = g0 + (u32)(r - ya + 1);
-    return mbar_wait(bars + (q & (kRingB - 1)), (q / kRingB) & 1u, (i64)timeout_ns);
+    return mbar_wait(bars + (q % kRingB), (q / kRingB) & 1u, (i64)timeout_ns);
   };
   // the lane's CPL raw words of a staged row (zero outside the grid's rows)
   auto own = [&](const double* sp, int sh, bool inside, double (&o)[CPL]) {
@@ -366,7 +367,7 @@ JD bool bulk_march_fx(double* ring, u64* bars, u32& gq, const double* __restrict
   };
   // bounded wait for the copies still in flight (the last kRingB staged rows)
   auto drain = [&]() {
-    for (u32 q = gq - kRingB; q != gq; ++q) mbar_wait(bars + (q & (kRingB - 1)), (q / kRingB) & 1u, 1000000);
+    for (u32 q = gq - kRingB; q != gq; ++q) mbar_wait(bars + (q % kRingB), (q / kRingB) & 1u, 1000000);
   };
 
 #pragma unroll 1
@@ -662,7 +663,7 @@ __global__ void __launch_bounds__(kCTA, STAGED ? 2 : 3) jacc_k_batched(JBatchPar
     return;
   }
   // -------------------------------------------------------------- compute warps
-  double* ring = s_ring + warp * kRing * kSlot;
+  double* ring = s_ring + warp * kRingWords;
   u32 gq = 0;  // rows this warp has staged through its bulk-copy ring
   for (int i = 0;; ++i) {
     if (!mbar_wait(&sh.ready[i & 1], (u32)((i >> 1) & 1), (i64)bp.timeout_ns)) {
