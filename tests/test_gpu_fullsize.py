@@ -123,10 +123,12 @@ def test_batched_64_grids_500_sweeps(orc):
     bt.release()
 
 
-def _box27_kernel(n, T, shape=None):
+def _box27_kernel(n, T, shape=None, jit=False):
+    """T = 0: single sweeps (jit: the constant-folded NVRTC variant); T = 2: two per launch."""
     w = inputs.box27_weights()
     nz, ny, nx = shape or (n, n, n)
-    return jacc.Kernel(jacc.STENCIL_27PT, jacc.F32, nx, ny, nz, coeffs=tuple(float(x) for x in w), tblock=T)
+    return jacc.Kernel(jacc.STENCIL_27PT, jacc.F32, nx, ny, nz, coeffs=tuple(float(x) for x in w), tblock=T,
+                       jit=jit)
 
 
 def _wrap_block(t, corner, m, halo):
@@ -141,11 +143,11 @@ def _wrap_block(t, corner, m, halo):
     return t[np.ix_(idx[0], idx[1], idx[2])]
 
 
-@pytest.mark.parametrize("T", [0, 2])
-def test_box27_1024_100_sweeps(orc, T):
+@pytest.mark.parametrize("T,jit", [(0, False), (0, True), (2, False)])
+def test_box27_1024_100_sweeps(orc, T, jit):
     n, ns, m = 1024, 100, 8
     w = inputs.box27_weights()
-    k = _box27_kernel(n, T)
+    k = _box27_kernel(n, T, jit=jit)
     a = inputs.uniform_torch(6, n ** 3, "cuda", torch.float32).mul_(2).sub_(1).view(n, n, n)
     corners = [(0, 0, 0), (1020, 3, 1019), (517, 1000, 260), (97, 511, 700)]
     blocks = [_wrap_block(a, c, m, ns).cpu().numpy() for c in corners]
@@ -163,7 +165,7 @@ def test_box27_1024_100_sweeps(orc, T):
             oc = o[ns:ns + m, ns:ns + m, ns:ns + m]
             gc = _wrap_block(g, c, m, 0).cpu().numpy()
             e = nerr(gc, oc)
-            print(f"27-point 1024^3 x 100 T={T}: block at {c}: normwise error {e:.3e}")
+            print(f"27-point 1024^3 x 100 T={T} jit={jit}: block at {c}: normwise error {e:.3e}")
             assert e <= TOL32, c
     # sums after every sweep (T > 0: after every T-th; the others are NaN)
     W = float(w.astype(np.float64) @ np.array([1, 6, 12, 8], dtype=np.float64))
@@ -195,8 +197,8 @@ def test_box27_512_100_sweeps_elementwise_plain_and_blocked(orc):
     with orc.threads():
         o, osum = orc.box27_run(u, w, ns)
     A = float(np.sum(np.abs(o.astype(np.float64))))
-    for T in (0, 2):
-        k = _box27_kernel(n, T)
+    for T, jit in ((0, False), (0, True), (2, False)):
+        k = _box27_kernel(n, T, jit=jit)
         a = torch.from_numpy(u).cuda()
         b = torch.empty_like(a)
         res = torch.zeros(ns, dtype=torch.float64, device="cuda")
@@ -204,7 +206,7 @@ def test_box27_512_100_sweeps_elementwise_plain_and_blocked(orc):
         torch.cuda.synchronize()
         g = (a if fb == 0 else b).cpu().numpy()
         e = nerr(g, o)
-        print(f"27-point 512^3 x 100 T={T}: normwise error {e:.3e}")
+        print(f"27-point 512^3 x 100 T={T} jit={jit}: normwise error {e:.3e}")
         assert e <= TOL32
         r = res.cpu().numpy()
         for i in range(ns):
