@@ -611,7 +611,8 @@ def profile_case(args):
     a = inputs.uniform_torch(6, n ** 3, "cuda", torch.float32).mul_(2).sub_(1).view(n, n, n)
     b = torch.empty_like(a)
     T = {"box27-tb2": 2, "box27-tb3": 3}.get(args.profile_case, 0)
-    k = jacc.Kernel(27, 32, n, n, n, coeffs=w, tile_id=3 if args.tile < 0 else args.tile, tblock=T)
+    k = jacc.Kernel(27, 32, n, n, n, coeffs=w, tile_id=3 if args.tile < 0 else args.tile, tblock=T,
+                    jit=args.profile_case == "box27-jit")
     res = torch.zeros(args.sweeps, dtype=torch.float64, device="cuda")
     for _ in range(args.warmup + args.steps):
         jacc.sweep(k, a, b, args.sweeps, res)
@@ -630,7 +631,8 @@ def main():
     ap.add_argument("--no-jit", action="store_true", help="use the precompiled kernel instead of the NVRTC variant")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner; use the library's default tile")
     ap.add_argument("--no-secondary", action="store_true", help="skip the other workloads' measurements")
-    ap.add_argument("--profile-case", choices=["box27", "box27-tb2", "box27-tb3", "var19", "jacobi2d", "batched"], default=None,
+    ap.add_argument("--profile-case", choices=["box27", "box27-jit", "box27-tb2", "box27-tb3", "var19", "jacobi2d",
+                                               "batched"], default=None,
                     help="run only one sweep sequence (27-point FP32 or 19-point on an --n cube; jacobi2d: 5-point FP64 --n squared, graph and cluster launch) for profilers, and exit")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the sweep kernel, if captured for this build")
