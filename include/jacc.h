@@ -618,8 +618,9 @@ jacc_status jacc_costmodel_release(jacc_costmodel m);
  * marched through registers).  timeout_ms bounds every device wait (0 =
  * 2000 ms).  test_stall_ticket and test_stall_row are fault-injection hooks
  * for tests: that ticket never reports completion, so the waits behind it
- * time out (-1 = off); the first compute warp of CTA 0 never fetches the
- * test_stall_row-th row it stages in the bulk-copy march, so its wait for
+ * time out (-1 = off); the first compute warp of the CTA that runs the
+ * first ticket never fetches the test_stall_row-th row it stages in the
+ * bulk-copy march (counted from that item), so its wait for
  * that row times out (0 = off).  Either way the launch ends early with
  * JACC_ERR_TIMEOUT in the status that jacc_batch_status reports, and the
  * fields hold partial results.  jacc_batch_set_tiles overrides

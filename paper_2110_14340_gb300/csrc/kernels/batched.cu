@@ -503,7 +503,7 @@ struct Mailbox {
   int stop;
   int s;  // sweep
   int F;  // fraction bits of the grid's fixed-point form, -1: native FP64
-  int pad_;
+  int first;  // the item is the launch's first ticket (the row-stall test hook's warp)
   JBItem it;
   JBGrid G;
 };
@@ -599,6 +599,7 @@ JD void publish(BatchShared& sh, int i, int stop, const Tk& k) {
   Mailbox& mb = sh.mb[i & 1];
   if ((threadIdx.x & 31) == 0) {
     mb.stop = stop;
+    mb.first = k.t == 0;
     mb.s = k.s;
     mb.F = k.F;
     mb.it = k.it;
@@ -665,6 +666,7 @@ __global__ void __launch_bounds__(kCTA, STAGED ? 2 : 3) jacc_k_batched(JBatchPar
   // -------------------------------------------------------------- compute warps
   double* ring = s_ring + warp * kRingWords;
   u32 gq = 0;  // rows this warp has staged through its bulk-copy ring
+  bool stall_armed = false;
   for (int i = 0;; ++i) {
     if (!mbar_wait(&sh.ready[i & 1], (u32)((i >> 1) & 1), (i64)bp.timeout_ns)) {
       if ((threadIdx.x & 31) == 0) atomicCAS(bp.status, 0, JACC_ERR_TIMEOUT);
@@ -676,6 +678,9 @@ __global__ void __launch_bounds__(kCTA, STAGED ? 2 : 3) jacc_k_batched(JBatchPar
     const int F = mb.F;
     const JBItem it = mb.it;
     const JBGrid G = mb.G;
+    // the row-stall test hook acts in warp 0 of the CTA that runs the first
+    // ticket (its first item), which counts its staged rows from there on
+    if (mb.first && warp == 0) stall_armed = true;
     const double* src = (s & 1) ? G.u[1] : G.u[0];
     double* dst = (s & 1) ? G.u[0] : G.u[1];
     const int flags = (s == 0 ? JFX_IN_F64 : 0) | (s == bp.nsweeps - 1 ? JFX_OUT_F64 : 0);
@@ -700,7 +705,7 @@ __global__ void __launch_bounds__(kCTA, STAGED ? 2 : 3) jacc_k_batched(JBatchPar
         if (F >= 0) {
           const int nyi = (int)G.ny, x0i = (int)x0, yai = (int)ya, ybi = (int)yb;
           const u64 tmo = bp.timeout_ns;
-          const int stall = (blockIdx.x == 0 && warp == 0) ? bp.stall_row : 0;
+          const int stall = stall_armed ? bp.stall_row : 0;
           u64* bars = sh.rows[warp];
           bool ok;
           if (Wu == 128)

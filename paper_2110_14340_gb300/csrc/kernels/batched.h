@@ -47,7 +47,7 @@ struct JBatchParams {
   unsigned long long* ticket;
   int* status;               // 0, or JACC_ERR_TIMEOUT after a wait gave up
   int staged;                // 1: rows staged in shared memory; 0: register march
-  int stall_row;             // fault-injection hook: warp 0 of CTA 0 never fetches this staged row (1-based; 0: none)
+  int stall_row;             // fault-injection hook: warp 0 of the first ticket's CTA never fetches this staged row (1-based; 0: none)
   double* resid;             // [ngrids][nsweeps] or null
   u64 timeout_ns;
   long long stall_ticket;    // fault-injection hook: this ticket never signals (-1: none)

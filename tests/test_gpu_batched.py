@@ -184,7 +184,7 @@ def test_stalled_ticket_times_out_and_context_survives(march):
 
 
 def test_stalled_row_copy_times_out_and_context_survives(orc):
-    # the first compute warp of CTA 0 never fetches its 3rd staged row: its
+    # warp 0 of the CTA running the first ticket never fetches its 3rd staged row: its
     # bounded wait for that row's barrier runs out, the launch ends early
     # with JACC_ERR_TIMEOUT, and the next launch is correct
     hosts, fields = make(SHAPES[:3], seed=7)
