@@ -209,8 +209,11 @@ jacc_status jacc_region_boxes_affine(int32_t nloops, const jacc_loop_affine* loo
  *
  * flags: JACC_SPEC_JIT compiles a variant with the extents and coefficients
  * folded in as constants (NVRTC, sm_103a; cached in memory and, if the
- * environment variable JACC_CACHE_DIR names a directory, on disk).  Without
- * it the handle uses a precompiled kernel that takes them as arguments.
+ * environment variable JACC_CACHE_DIR names a directory, on disk); for the
+ * 3D tiles with 16-byte columns and the long march it marches 40 planes per
+ * CTA instead of the table's 64 (jacc_kernel_info reports the grid).
+ * Without it the handle uses a precompiled kernel that takes them as
+ * arguments.
  * JACC_SPEC_CLUSTER (5PT FP64 only; no counterpart in the paper): jacc_sweep
  * runs the whole sequence in one launch of one thread-block cluster (16 or 8
  * CTAs) that keeps both fields in its distributed shared memory; it suits
