@@ -43,9 +43,9 @@ def set_size(n, sweeps):
     WORKLOAD = f"heat3d 7-point FP64 {n}^3, r=0.125, zero Dirichlet, {sweeps} sweeps per CUDA graph"
 BYTES_PER_LUP = 16  # one FP64 read + one FP64 write per interior point
 # DRAM bytes (read + write) per update of the intermediate-sweep kernel, from
-# an ncu capture of the same kernel on a 384^3 grid (875.6 MB for 382^3
+# an ncu capture of the same kernel on a 384^3 grid (882.8 MB for 382^3
 # updates); scaled to a launch by its updates.
-DRAM_BYTES_PER_LUP = 15.708
+DRAM_BYTES_PER_LUP = 15.837
 METRIC = "stencil GLUP/s"
 WORKLOAD = "heat3d 7-point FP64 512^3, r=0.125, zero Dirichlet, 200 sweeps per CUDA graph"
 
@@ -311,7 +311,7 @@ def run_gpu(args):
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": args.traffic if args.traffic is not None else DRAM_BYTES_PER_LUP * LUP_PER_SWEEP,
             "traffic_source": "command line" if args.traffic is not None else
-            "ncu dram read+write bytes of a 382^3 launch of the same kernel, 15.708 B per update, x updates per launch",
+            "ncu dram read+write bytes of a 382^3 launch of the same kernel, 15.837 B per update, x updates per launch",
             "peak_kind": peak_kind,
             "per_unit": f"16 B per interior point per sweep (8 B read + 8 B write), {N - 2}^3 points per launch"}
 
