@@ -362,7 +362,7 @@ jacc_status jacc_sweep_host(jacc_kernel k, const void* u_host, void* result_host
  * caller-owned, read-only during the call and not overlapping u0 or u1
  * (nfields must be 12).  Graphs (JACC_SWEEP_GRAPH) are cached by every
  * pointer of the call.  The 19-point kernel has one tile (32 x 4 threads,
- * 16-byte columns, input planes staged by bulk copies, 64-plane march); nx
+ * 16-byte columns, input planes staged by bulk copies, 40-plane march); nx
  * must be a multiple of 4.  jacc_launch and jacc_sweep reject 19PT handles. */
 jacc_status jacc_sweep_coeffs(jacc_kernel k, void* u0, void* u1, int32_t nsweeps, const void* const* fields,
                               int32_t nfields, double* resid_dev, uint32_t flags, uintptr_t stream,

@@ -321,7 +321,7 @@ extern "C" jacc_status jacc_specialize(const jacc_kernel_desc* desc, jacc_kernel
   if (st) return st;
   int tile = desc->tile_id;
   if (desc->stencil == 19) {
-    tile = 3;  // the kernel's one configuration: 32 x 4 threads, 16-byte columns, 64-plane march
+    tile = 3;  // the kernel's one configuration: 32 x 4 threads, 16-byte columns, 40-plane march
   } else if (tile < 0) {
     tile = tuned_tile(*desc);
     if (tile < 0 || !tile_valid(*desc, tile)) tile = default_tile(*desc);
