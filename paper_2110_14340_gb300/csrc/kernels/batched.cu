@@ -250,7 +250,9 @@ JD void staged_march(double* ring, const double* __restrict__ u, double* __restr
 // ---------------------------------------------------------------- bulk-copy march
 //
 // The fixed-point march of the staged variant.  A warp's unit is W = 32 CPL
-// columns (CPL = 4 for items at least 128 columns wide, else 2); lane l owns
+// columns (CPL = 4 in intermediate sweeps of items at least 128 columns
+// wide; 2 in narrower items and in the converting first and last sweeps,
+// whose conversions need the registers); lane l owns
 // columns x0 + CPL l .. x0 + CPL l + CPL - 1.  Rows stream through a ring of
 // kRingB slots of W + 4 doubles, each slot with its own mbarrier: lane 0
 // fetches row r with ONE bulk copy (cp.async.bulk) of the 16-byte-aligned
