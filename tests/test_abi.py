@@ -117,3 +117,43 @@ def test_costmodel_fixed_tile_and_regret_host_calls(lib):
     with pytest.raises(jacc.JaccError) as e:
         jacc.fixed_tile(nothing)
     assert e.value.status == jacc.ERR_UNSUPPORTED
+
+
+# ctypes structures of the binding and the C types of include/jacc.h they mirror
+ABI_STRUCTS = [("Loop", "jacc_loop"), ("Ref", "jacc_ref"), ("Array", "jacc_array"), ("Region", "jacc_region"),
+               ("KernelDesc", "jacc_kernel_desc"), ("KernelInfo", "jacc_kernel_info_t"), ("Grid", "jacc_grid"),
+               ("BatchConfig", "jacc_batch_config"), ("TuneTable", "jacc_tune_table"),
+               ("CostModelEval", "jacc_costmodel_eval"), ("BatchTile", "jacc_batch_tile"),
+               ("TuneResult", "jacc_tune_result"), ("LoopAffine", "jacc_loop_affine"), ("Box", "jacc_box"),
+               ("Tile", "jacc_tile")]
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    # a C program compiled against include/jacc.h prints the size of every
+    # struct the binding mirrors and the offset of each of its fields (a field
+    # the header lacks fails the compile); the ctypes layout must agree
+    import ctypes
+    import os
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "jacc.h"', "int main(void) {"]
+    for py, c in ABI_STRUCTS:
+        cls = getattr(jacc, py)
+        lines.append(f'  printf("{py} size %zu\\n", sizeof({c}));')
+        for name, _ in cls._fields_:
+            lines.append(f'  printf("{py} {name} %zu\\n", offsetof({c}, {name}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "abi_layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = str(tmp_path / "abi_layout")
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Werror", str(src), "-o", exe, "-I" + os.path.join(root, "include")],
+                   check=True, capture_output=True, text=True)
+    got = {}
+    for ln in subprocess.run([exe], check=True, capture_output=True, text=True).stdout.splitlines():
+        cls, key, val = ln.split()
+        got[(cls, key)] = int(val)
+    for py, _ in ABI_STRUCTS:
+        cls = getattr(jacc, py)
+        assert got[(py, "size")] == ctypes.sizeof(cls), py
+        for name, _ in cls._fields_:
+            assert got[(py, name)] == getattr(cls, name).offset, (py, name)
