@@ -157,3 +157,20 @@ def test_binding_structs_match_the_header_layout(tmp_path):
         assert got[(py, "size")] == ctypes.sizeof(cls), py
         for name, _ in cls._fields_:
             assert got[(py, name)] == getattr(cls, name).offset, (py, name)
+
+
+def test_binding_signatures_match_the_header_prototypes():
+    # every function include/jacc.h declares has a binding entry with as many
+    # arguments as its prototype
+    import os
+    import re
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    with open(os.path.join(root, "include", "jacc.h")) as f:
+        h = re.sub(r"/\*.*?\*/", "", f.read(), flags=re.S)
+    decls = re.findall(r"\b(jacc_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", h)
+    assert len(decls) >= 50
+    for name, args in decls:
+        a = args.strip()
+        n = 0 if a in ("", "void") else a.count(",") + 1
+        assert name in jacc.SIGNATURES, name
+        assert len(jacc.SIGNATURES[name][0]) == n, name
