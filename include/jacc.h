@@ -211,7 +211,8 @@ jacc_status jacc_region_boxes_affine(int32_t nloops, const jacc_loop_affine* loo
  * folded in as constants (NVRTC, sm_103a; cached in memory and, if the
  * environment variable JACC_CACHE_DIR names a directory, on disk); for the
  * 3D tiles with 16-byte columns and the long march it marches 40 planes per
- * CTA instead of the table's 64 (jacc_kernel_info reports the grid).
+ * CTA (27PT: 32) instead of the table's 64 (jacc_kernel_info reports the
+ * grid).
  * Without it the handle uses a precompiled kernel that takes them as
  * arguments.
  * JACC_SPEC_CLUSTER (5PT FP64 only; no counterpart in the paper): jacc_sweep

@@ -224,15 +224,16 @@ static std::string key_of(const jacc_kernel_desc& d, int tile) {
 }
 
 // Planes per CTA of a 3D kernel.  The constant-folded variants of the staged
-// tiles with the long march take 40 planes instead of the table's 64: with
-// the extents folded their kernels need fewer registers and more CTAs fit,
-// and shallower chunks then balance better (heat 512^3 FP64: 396.8 against
-// 392.1 GLUP/s; 27-point 1024^3 FP32: 131.5 against 144.7 ms for 100
-// sweeps), while the precompiled kernels stay at 64 (there 40 was no
-// faster).
+// tiles with the long march take fewer planes than the table's 64: with the
+// extents folded their kernels need fewer registers and more CTAs fit, and
+// shallower chunks then balance better.  Measured with tile 3: heat 512^3
+// FP64 best at 40 planes (396.8 against 392.1 GLUP/s at 64), 27-point 1024^3
+// FP32 best at 24-32 (128.6 ms for 100 sweeps at 32 against 144.7 at 64).
+// The precompiled kernels stay at 64.
 static int plane_chunk(const jacc_kernel_desc& d, int tile) {
   const TileCfg& c = kTiles[tile];
-  if ((d.flags & JACC_SPEC_JIT) && d.stencil != 5 && staged_tile(d, tile) && c.zc == 64) return 40;
+  if ((d.flags & JACC_SPEC_JIT) && d.stencil != 5 && staged_tile(d, tile) && c.zc == 64)
+    return d.stencil == 27 ? 32 : 40;
   return c.zc;
 }
 
