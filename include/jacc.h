@@ -611,8 +611,9 @@ jacc_status jacc_costmodel_release(jacc_costmodel m);
  * every schedule gives the same bits.
  *
  * Schedule (jacc_batch_config): target points per item (tile columns: the
- * fewest 64-column strips, at most 8, that cover a row; rows = max(warps per
- * strip, item_points / columns)), persistent CTAs per SM (0 = as many as
+ * fewest 64-column strips that cover a row, at most 2 for the staged march
+ * and 8 for the register march; rows = max(warps per strip, item_points /
+ * columns)), persistent CTAs per SM (0 = as many as
  * fit), item order within a group (0: grid by grid, largest grid first;
  * 1: round-robin over the group's grids), the L2 budget per group in bytes
  * of both fields (0 = 40 % of the device's L2; -1 = one group), and the
